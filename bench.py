@@ -1,0 +1,376 @@
+"""Throughput benchmark of the elastic-solid D2Q9 LBM step on GB300.
+
+Workload (one benchmark step = one full shot): the 2048 x 1024 half-space --
+free surface on the top row, 64-cell absorbing layers on the left, right and
+bottom, homogeneous Poisson solid (nu = 0.25), vertical Ricker x Gaussian force
+10 cells below the surface, 256 surface receivers -- advanced 4000 time steps
+in FP32 from rest, receivers recorded every step.  Metric: MLUPS (million
+lattice-cell updates per second) = cells x time steps / time.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+One JSON line is printed by rank 0.  Timing: CUDA events on the library's
+stream, a barrier and a synchronise on both sides of the K timed shots, the
+maximum over ranks; L2 is flushed (a 256 MiB write) before every shot.  With N
+GPUs each rank runs its own shot (independent replicas, weak scaling).
+``--impl reference`` times the FP64 CPU oracle on the host cores instead, on
+bounded samples of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "D2Q9 elastic-LBM MLUPS & % HBM roofline: plain vs batched/FP16-store/adjoint"
+UNIT = "MLUPS"
+# Algorithmic bytes per cell update of the FP32 step without per-cell material:
+# 9 populations read + 9 written (4 B each) + displacement read + written (2 x 2 x 4 B).
+BYTES_PER_CELL = {"f32": 9 * 4 * 2 + 2 * 4 * 2, "f64": 9 * 8 * 2 + 2 * 8 * 2}
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """Samples SM clocks and throttle reasons with nvidia-smi while running."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+        self.t = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.QUERY}", "--format=csv,noheader,nounits",
+                 "-lms", "200", "-i", str(self.gpu)],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            if self.t is not None:
+                self.t.join(timeout=2)
+
+    def summary(self):
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax = float(parts[2])
+            except ValueError:
+                continue
+            for name, val in zip(names, parts[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _dist():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def cpu_oracle_sample(nsteps_sample: int, nthreads: int):
+    """Times the FP64 CPU oracle on ``nsteps_sample`` steps of the half-space
+    workload, starting from rest at step 40 (the source is firing).  Returns
+    (MLUPS, seconds)."""
+    import oracle
+    from paper_2009_06404_gb300 import workloads as wl
+    w = wl.halfspace()
+    prob = oracle.Problem(nx=w.nx, ny=w.ny, tau=w.tau, bc_top=w.bc[0], bc_bottom=w.bc[1],
+                          bc_left=w.bc[2], bc_right=w.bc[3], sponge=tuple(w.sponge),
+                          sponge_amax=w.sponge_amax, fs_order=w.fs_order, rho0=w.rho0, lam=w.lam, mu=w.mu,
+                          sources=w.sources, receivers=w.receivers, nthreads=nthreads)
+    st = oracle.State(prob, n=40)
+    t = time.perf_counter()
+    oracle.run(prob, nsteps_sample, st)
+    dt = time.perf_counter() - t
+    return w.cells * nsteps_sample / dt / 1e6, dt
+
+
+def run_reference(args):
+    world, rank, _ = _dist()
+    if rank != 0:
+        return 0
+    import oracle
+    oracle.build()
+    nthreads = os.cpu_count() or 1
+    sample = args.ref_sample_steps
+    for _ in range(args.warmup):
+        cpu_oracle_sample(sample, nthreads)
+    vals, secs = [], []
+    for _ in range(args.steps):
+        v, dt = cpu_oracle_sample(sample, nthreads)
+        vals.append(v)
+        secs.append(dt)
+    from paper_2009_06404_gb300 import workloads as wl
+    w = wl.halfspace()
+    total = w.cells * sample * args.steps / sum(secs) / 1e6
+    desc = (f"FP64 oracle, {sample} time steps of the {w.nx}x{w.ny} half-space per step, "
+            f"OpenMP over rows, {nthreads} threads")
+    line = {
+        "impl": "reference", "metric": METRIC, "value": total, "unit": UNIT,
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * sum(secs) / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "halfspace_2048x1024_fp32_4000steps", "nx": w.nx, "ny": w.ny,
+                   "time_steps_per_step": sample, "note": "bounded sample of the workload"},
+        "cpu_baseline": {"value": total, "unit": UNIT, "cores": nthreads, "kind": "oracle",
+                         "sample": desc},
+        "e2e": {"value": total, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_gpu(args):
+    import torch
+    import paper_2009_06404_gb300 as pkg
+    from paper_2009_06404_gb300 import workloads as wl
+    from paper_2009_06404_gb300 import build as _build
+
+    world, rank, local = _dist()
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA device")
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    if not _build.up_to_date():
+        if rank == 0:
+            _build.build()
+        if dist is not None:
+            dist.barrier()
+    pkg.load_library()
+
+    storage = args.storage
+    w = wl.halfspace(nsteps=args.time_steps, storage=storage)
+    stream = torch.cuda.current_stream()
+    sim = pkg.from_workload(w, max_steps_traced=w.nsteps, stream=stream)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+
+    def shot(ev_pair=None):
+        sim.reset()
+        if ev_pair is not None:
+            ev_pair[0].record(stream)
+        sim.step(w.nsteps)
+        if ev_pair is not None:
+            ev_pair[1].record(stream)
+
+    def barrier():
+        torch.cuda.synchronize()
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    # --------------------------------------------------- device-resident timing
+    for _ in range(args.warmup):
+        flush.fill_(1)
+        shot()
+    barrier()
+    launches0 = sim.kernel_launches
+    step_events = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                   for _ in range(args.steps)]
+    t_start = torch.cuda.Event(enable_timing=True)
+    t_stop = torch.cuda.Event(enable_timing=True)
+    gpu_index = local
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES")
+    if vis:
+        try:
+            gpu_index = int(vis.split(",")[local])
+        except ValueError:
+            pass
+    with ClockSampler(gpu_index) as clk:
+        barrier()
+        elapsed = 0.0
+        kernel_ms = 0.0
+        for k in range(args.steps):
+            flush.fill_(k & 0xFF)  # L2 flush, outside the shot's events
+            e0, e1 = step_events[k]
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            shot((e0, e1))
+            b.record(stream)
+            torch.cuda.synchronize()
+            elapsed += a.elapsed_time(b)
+            kernel_ms += e0.elapsed_time(e1)
+        barrier()
+    sim.sync()
+    gpu_launches = sim.kernel_launches - launches0
+    t = torch.tensor([elapsed], dtype=torch.float64, device="cuda")
+    if dist is not None:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    elapsed_max = float(t.item())
+    cells_steps = w.cells * w.nsteps
+    value = world * cells_steps * args.steps / (elapsed_max / 1e3) / 1e6
+
+    # --------------------------------------------------- end to end (host buffers)
+    rho0, lam, mu = (np.ascontiguousarray(a) for a in (w.rho0, w.lam, w.mu))
+    src = np.ascontiguousarray(w.sources)
+    rec = np.ascontiguousarray(w.receivers)
+    tr_host = torch.empty((w.nsteps, len(rec), 4), dtype=torch.float64).pin_memory()
+    u_host = [torch.empty((w.ny, w.nx), dtype=torch.float64).pin_memory() for _ in range(2)]
+    h2d = rho0.nbytes + lam.nbytes + mu.nbytes + src.nbytes + rec.nbytes
+    d2h = tr_host.numel() * 8 + sum(u.numel() * 8 for u in u_host)
+
+    def e2e_shot():
+        sim.set_material(rho0, lam, mu)
+        sim.set_sources(src)
+        sim.set_receivers(rec)
+        sim.reset()
+        sim.step(w.nsteps)
+        sim.read_traces(out=tr_host.numpy())
+        f = sim.L.lbm_elastic_read_fields(sim.h, u_host[0].data_ptr(), u_host[1].data_ptr(),
+                                          None, None, None, None, None, None, 0)
+        sim._check(f)
+
+    for _ in range(max(1, args.warmup // 2)):
+        flush.fill_(3)
+        e2e_shot()
+    barrier()
+    e2e_ms = 0.0
+    for k in range(args.steps):
+        flush.fill_(k & 0xFF)
+        torch.cuda.synchronize()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        e2e_shot()
+        b.record(stream)
+        torch.cuda.synchronize()
+        e2e_ms += a.elapsed_time(b)
+    t = torch.tensor([e2e_ms], dtype=torch.float64, device="cuda")
+    if dist is not None:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    e2e_value = world * cells_steps * args.steps / (float(t.item()) / 1e3) / 1e6
+
+    # --------------------------------------------------- roofline of the step kernel
+    peak, peak_kind = _peaks()
+    avg_launch_s = kernel_ms / 1e3 / (args.steps * w.nsteps)
+    bytes_launch = BYTES_PER_CELL[storage] * w.cells
+    achieved = bytes_launch / avg_launch_s / 1e9
+    traffic = None
+    prof = os.path.join(ROOT, "profiles", "traffic.json")
+    if os.path.exists(prof):
+        try:
+            with open(prof) as f:
+                d = json.load(f)
+            key = f"step_{storage}_{w.nx}x{w.ny}"
+            if key in d and d[key].get("kernel_hash") == _build.source_hash():
+                traffic = d[key]["dram_bytes_per_launch"]
+        except Exception:
+            traffic = None
+
+    if rank != 0:
+        if dist is not None:
+            dist.destroy_process_group()
+        return 0
+
+    cpu = None
+    if world == 1 and not args.no_cpu_baseline:
+        import oracle
+        oracle.build()
+        nthreads = os.cpu_count() or 1
+        v, dt = cpu_oracle_sample(args.cpu_sample_steps, nthreads)
+        cpu = {"value": v, "unit": UNIT, "cores": nthreads, "kind": "oracle",
+               "sample": f"{args.cpu_sample_steps} time steps of the {w.nx}x{w.ny} half-space "
+                         f"(FP64 oracle, OpenMP over rows), {dt:.1f} s"}
+
+    clocks = clk.summary()
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": elapsed_max / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32" if storage == "f32" else storage, "data": "synthetic",
+        "config": {"workload": "halfspace_2048x1024_fp32_4000steps", "nx": w.nx, "ny": w.ny,
+                   "time_steps_per_step": w.nsteps, "storage": storage,
+                   "free_surface": "top", "absorbing_layers": "left,right,bottom x64",
+                   "receivers": len(w.receivers), "parallelism": f"replicas x{world}",
+                   "l2": "flushed before every timed shot (256 MiB write)"},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": traffic,
+                     "peak_kind": peak_kind, "kernel": "step_kernel",
+                     "bytes_per_cell": BYTES_PER_CELL[storage],
+                     "avg_launch_us": avg_launch_s * 1e6},
+        "cpu_baseline": cpu,
+        "e2e": {"value": e2e_value, "unit": UNIT,
+                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
+        "clocks": clocks,
+        "gpu_launches": int(gpu_launches),
+    }
+    print(json.dumps(line), flush=True)
+    sim.close()
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
+    ap.add_argument("--storage", default="f32", choices=["f32", "f64"])
+    ap.add_argument("--time-steps", type=int, default=4000)
+    ap.add_argument("--cpu-sample-steps", type=int, default=100)
+    ap.add_argument("--ref-sample-steps", type=int, default=10)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        raise SystemExit("--warmup must be >= 3")
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gpu(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

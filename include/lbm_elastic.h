@@ -1,0 +1,222 @@
+/*
+ * lbm_elastic.h -- C ABI of the GB300 (sm_103a) library for the
+ * single-relaxation-time D2Q9 lattice Boltzmann method for wave propagation
+ * in isotropic linear elastic solids (Escande, Kolluru, Cleon, Sagaut,
+ * arXiv 2009.06404).
+ *
+ * One time step (Sec. 2, Eq. 18, with Eqs. 9-15) per cell:
+ *   1. pull streaming  f_i(x) = f*_i(x - c_i), with the wall rules below;
+ *   2. moments         rho = sum f, m = sum f c, P = sum f c c;
+ *   3. density gradient by centred differences (Eq. 10);
+ *   4. source          S = (mu - lambda)/rho0 grad rho + F - A j   (Eqs. 9, 44),
+ *                      physical flux j = (m + (S_elastic + F)/2) / (1 + A/2);
+ *   5. equilibrium     f^eq = w (rho + c.j/b^2 + P^n:(cc - b^2 I)/(2 b^4)),
+ *                      P^n = P - rho b^2 I                       (Eqs. 14-15);
+ *   6. BGK + forcing   f* = f - (f - f^eq)/tau + (1 - 1/(2 tau)) w c.S/b^2 (Eqs. 11, 18);
+ *   7. displacement    u += j / rho0 (Delta t = 1), receivers record (u, j/rho0).
+ * Lattice units: Delta x = Delta t = 1, b^2 = 1/3 (the S-wave speed).
+ *
+ * Boundaries (Sec. 6): periodic (must pair top/bottom or left/right), rigid
+ * wall by half-way bounce-back (Eq. 36), free surface by anti-bounce-back with
+ * rho_air and the tangential stress extrapolated to the wall, the normal and
+ * shear stress set to zero (Eqs. 37-42), and absorbing layers
+ * A(x) = A_max (d/L)^2 on any side (Sec. 6.4, Eq. 44).  Body force: sum over sources of
+ * amplitude * dir * exp(-|x-x_s|^2/(2 sigma^2)) * ricker(n) inside r_cut
+ * (Sec. 5), evaluated at t = n for step n.
+ *
+ * Grid layout seen by callers: row-major [ny][nx], x fastest; row y = 0 is the
+ * TOP row.  Population order: c_0 = (0,0); c_1..4 = (1,0),(0,1),(-1,0),(0,-1);
+ * c_5..8 = (1,1),(-1,1),(-1,-1),(1,-1).  Populations are deviations from a
+ * rest state with zero density (the step is linear-affine, so this is exact).
+ *
+ * Memory ownership: the caller owns ALL device memory.  It passes one device
+ * workspace of lbm_elastic_workspace_bytes() bytes to lbm_elastic_create and
+ * keeps it alive until lbm_elastic_destroy.  The library never calls
+ * cudaMalloc/cudaFree; the handle itself holds only host memory.
+ *
+ * Streams: every call enqueues its device work on the stream given at create
+ * (0 = the legacy default stream).  lbm_elastic_step is asynchronous.  Calls
+ * that return data to the host synchronise that stream.
+ *
+ * Errors: every function returns an lbm_status; nothing is thrown across the
+ * ABI.  Argument errors are reported synchronously.  A non-finite value met by
+ * the step kernel (an unstable run, Sec. 4) sets a device flag that the next
+ * synchronising call reports as LBM_ERR_NONFINITE.  lbm_elastic_last_error
+ * gives a message for the last failing call on a handle.
+ *
+ * Threads: one handle must not be used by two host threads at once.
+ */
+#ifndef LBM_ELASTIC_H
+#define LBM_ELASTIC_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define LBM_ELASTIC_ABI_VERSION 1
+
+typedef struct lbm_elastic lbm_elastic_t;
+
+typedef enum {
+  LBM_OK = 0,
+  /* set_material: mu/rho0 differs from b^2 = 1/3 somewhere.  The lattice fixes
+   * v_S = b (Sec. 2, after Eq. 12); Lambda = (mu - lambda)/(rho0 b^2) (Eq. 32)
+   * is still used as given.  Not an error. */
+  LBM_WARN_VS_NOT_B = 1,
+  LBM_ERR_ARG = -1,         /* invalid argument, size or pointer            */
+  LBM_ERR_UNSUPPORTED = -2, /* a valid request this build does not support  */
+  LBM_ERR_WORKSPACE = -3,   /* workspace too small or misaligned            */
+  LBM_ERR_CUDA = -4,        /* a CUDA runtime call failed                   */
+  LBM_ERR_NONFINITE = -5,   /* NaN/Inf met by a step (unstable run)         */
+  LBM_ERR_TIMEOUT = -6,     /* a bounded device wait gave up                */
+  LBM_ERR_CAPACITY = -7     /* more sources/receivers than reserved at create */
+} lbm_status;
+
+/* Storage type of the populations.  F64 computes in FP64; the others compute
+ * in FP32. */
+typedef enum { LBM_F64 = 0, LBM_F32 = 1, LBM_F16 = 2, LBM_BF16 = 3 } lbm_storage;
+
+/* Boundary kinds (Sec. 6). */
+typedef enum { LBM_BC_PERIODIC = 0, LBM_BC_FREE = 1, LBM_BC_RIGID = 2 } lbm_bc;
+
+typedef struct {
+  int nx, ny;            /* grid size; both >= 3                              */
+  int storage;           /* lbm_storage                                       */
+  int u_fp64;            /* 1: accumulate the displacement in FP64            */
+  double tau;            /* BGK relaxation time (> 0.5), Eq. 18               */
+  int bc_top, bc_bottom, bc_left, bc_right;             /* lbm_bc             */
+  int sponge_top, sponge_bottom, sponge_left, sponge_right; /* layer cells, >= 0 */
+  double sponge_amax;    /* A_max of every layer; <= 0 selects 12.8 / L       */
+  int free_surface_order; /* extrapolation of rho_air and the tangential stress
+                           * to a free surface: 1 = linear, 1.5 x_b - 0.5 x_in
+                           * as printed (Eq. 39; it has growing modes: up to
+                           * x1.046 per step at tau = 1), 0 = constant, the
+                           * boundary cell's own values (neutrally stable).
+                           * The density-gradient ghost follows the same
+                           * order: 2 rho_b - rho_in, or rho_b.               */
+  int material_per_cell; /* 0: material given per row (ny values); 1: per cell */
+  int max_sources;       /* capacity reserved in the workspace (>= 0)         */
+  int max_receivers;     /* capacity reserved in the workspace (>= 0)         */
+  int max_steps_traced;  /* receiver samples kept: steps [0, max) after reset */
+} lbm_elastic_config;
+
+/* One Ricker x Gaussian body-force source (Sec. 5).  Position in cells (may be
+ * fractional), sigma and r_cut in cells, force direction (used as given, not
+ * normalised), amplitude, Ricker peak frequency f_peak (1/steps) and delay t0
+ * (steps): r(t) = (1 - 2 pi^2 f^2 (t-t0)^2) exp(-pi^2 f^2 (t-t0)^2). */
+typedef struct {
+  double x, y, sigma, dir_x, dir_y, amplitude, f_peak, t0, r_cut;
+} lbm_source;
+
+/* Bytes of device workspace a configuration needs (0 for an invalid one).
+ * The workspace must start on a 256-byte boundary. */
+size_t lbm_elastic_workspace_bytes(const lbm_elastic_config *cfg);
+
+/* Creates a handle over a caller-owned device workspace and resets the state
+ * to rest (f* = 0, u = 0, step 0).  The material defaults to a homogeneous
+ * Poisson solid with rho0 = 1 (lambda = mu = 1/3); no sources; no receivers.
+ * cuda_stream is a cudaStream_t (NULL for the default stream).  Synchronous. */
+lbm_status lbm_elastic_create(const lbm_elastic_config *cfg, void *d_workspace,
+                              size_t workspace_bytes, void *cuda_stream,
+                              lbm_elastic_t **out);
+
+/* Material (Sec. 2, Eqs. 9 and 32): rho0, lambda and mu, FP64, each with ny
+ * entries (material_per_cell = 0, one value per row) or nx*ny entries
+ * ([ny][nx]).  Pointers are device pointers if on_device, else host pointers.
+ * The kernel forms Lambda = (mu - lambda)/(rho0 b^2) and 1/rho0.  Returns
+ * LBM_WARN_VS_NOT_B (still applied) if |mu/(rho0 b^2) - 1| > 1e-9 anywhere,
+ * LBM_ERR_ARG if some rho0 <= 0 or a value is not finite.  Synchronous. */
+lbm_status lbm_elastic_set_material(lbm_elastic_t *h, const double *rho0,
+                                    const double *lambda, const double *mu,
+                                    int on_device);
+
+/* Replaces the source list (host array of n <= max_sources entries; n = 0
+ * removes every source).  sigma > 0, r_cut >= 0 required. */
+lbm_status lbm_elastic_set_sources(lbm_elastic_t *h, const lbm_source *src, int n);
+
+/* Replaces the receivers: host array xy[2n] of cell coordinates (x, y), n <=
+ * max_receivers, each inside the grid.  Clears the recorded traces; steps
+ * taken afterwards are recorded from trace slot 0. */
+lbm_status lbm_elastic_set_receivers(lbm_elastic_t *h, const int *xy, int n);
+
+/* Back to rest: f* = 0, u = 0, step index 0, traces cleared, error flag
+ * cleared.  Material, sources and receivers are kept.  Asynchronous. */
+lbm_status lbm_elastic_reset(lbm_elastic_t *h);
+
+/* Advances nsteps >= 0 time steps (asynchronous; nsteps = 0 is a no-op).  Each
+ * step also records the receivers while fewer than max_steps_traced steps
+ * have been recorded since the last reset / set_receivers / set_state. */
+lbm_status lbm_elastic_step(lbm_elastic_t *h, int nsteps);
+
+/* Index n of the next step (number of steps taken since reset or the step
+ * given to set_state). */
+long long lbm_elastic_step_index(const lbm_elastic_t *h);
+
+/* Fields of the current state, FP64, each [ny][nx]: displacement u, velocity
+ * v = j/rho0 with j the physical flux that the next step will use (with the
+ * half-force shift), density rho and second moment P = -sigma (Sec. 2) of the
+ * streamed populations.  Any pointer may be NULL to skip that field.  Device
+ * pointers if on_device, else host pointers.  Synchronises; returns
+ * LBM_ERR_NONFINITE if a step met a non-finite value. */
+lbm_status lbm_elastic_read_fields(lbm_elastic_t *h, double *ux, double *uy,
+                                   double *vx, double *vy, double *rho,
+                                   double *pxx, double *pxy, double *pyy,
+                                   int on_device);
+
+/* Number of steps recorded in the trace buffer so far. */
+int lbm_elastic_traces_recorded(const lbm_elastic_t *h);
+
+/* Copies the recorded traces, FP64 [T][R][4] with T = traces_recorded and R =
+ * the receiver count; the four values are (u_x, u_y, v_x, v_y) after each
+ * step.  Synchronises. */
+lbm_status lbm_elastic_read_traces(lbm_elastic_t *h, double *out, int on_device);
+
+/* Sets the state from FP64 arrays: post-collision populations f9 [9][ny][nx]
+ * (the state a step streams from) and displacement u2 [2][ny][nx] (NULL: zero).
+ * The step index becomes `step`; traces are cleared.  Values are rounded to
+ * the storage type.  Synchronous. */
+lbm_status lbm_elastic_set_state(lbm_elastic_t *h, const double *f9,
+                                 const double *u2, long long step, int on_device);
+
+/* Reads the state as FP64 arrays (either pointer may be NULL).  Synchronises. */
+lbm_status lbm_elastic_get_state(lbm_elastic_t *h, double *f9, double *u2,
+                                 int on_device);
+
+/* Checkpoint in the storage type: lbm_elastic_checkpoint_bytes() bytes holding
+ * the populations, the displacement and the step index.  save/load copy to or
+ * from a caller buffer (device if on_device).  load clears the traces.  A
+ * checkpoint only loads into a handle of the same configuration. */
+size_t lbm_elastic_checkpoint_bytes(const lbm_elastic_t *h);
+lbm_status lbm_elastic_save(lbm_elastic_t *h, void *buf, int on_device);
+lbm_status lbm_elastic_load(lbm_elastic_t *h, const void *buf, int on_device);
+
+/* Deterministic FP64 sums over the grid of the current post-collision state:
+ * out[0..6] = sum rho, sum m_x, sum m_y, sum P_xx, sum P_xy, sum P_yy,
+ * sum (u_x^2 + u_y^2).  Fixed summation order (per-block partials in the
+ * workspace, then one block), so repeated calls give identical bits.
+ * Synchronises. */
+lbm_status lbm_elastic_moment_sums(lbm_elastic_t *h, double out[7]);
+
+/* Waits for the handle's stream; reports LBM_ERR_NONFINITE / LBM_ERR_CUDA. */
+lbm_status lbm_elastic_sync(lbm_elastic_t *h);
+
+/* Releases the handle (host memory only; the workspace stays the caller's). */
+lbm_status lbm_elastic_destroy(lbm_elastic_t *h);
+
+/* Message of the last failing call on h ("" if none).  Valid until the next
+ * call on h.  With h == NULL: the last failure of lbm_elastic_create. */
+const char *lbm_elastic_last_error(const lbm_elastic_t *h);
+
+/* Static name of a status code. */
+const char *lbm_elastic_status_string(int status);
+
+/* Number of kernel launches this handle has issued (for launch accounting). */
+long long lbm_elastic_kernel_launches(const lbm_elastic_t *h);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LBM_ELASTIC_H */

@@ -63,7 +63,7 @@ class _Problem(ctypes.Structure):
         ("bc_left", ctypes.c_int), ("bc_right", ctypes.c_int),
         ("sp_top", ctypes.c_int), ("sp_bottom", ctypes.c_int),
         ("sp_left", ctypes.c_int), ("sp_right", ctypes.c_int),
-        ("sp_amax", ctypes.c_double),
+        ("sp_amax", ctypes.c_double), ("fs_order", ctypes.c_int),
         ("rho0", ctypes.c_void_p), ("lam", ctypes.c_void_p), ("mu", ctypes.c_void_p),
         ("nsrc", ctypes.c_int), ("src", ctypes.c_void_p),
         ("nrec", ctypes.c_int), ("rec", ctypes.c_void_p),
@@ -113,6 +113,7 @@ class Problem:
     bc_right: str = "periodic"
     sponge: Sequence[int] = (0, 0, 0, 0)  # top, bottom, left, right
     sponge_amax: float = 0.0
+    fs_order: int = 1                    # free-surface extrapolation: 1 linear, 0 constant
     rho0: Optional[np.ndarray] = None    # [ny][nx] or [ny] (expanded)
     lam: Optional[np.ndarray] = None
     mu: Optional[np.ndarray] = None
@@ -139,7 +140,7 @@ class Problem:
         s = _Problem(self.nx, self.ny, float(self.tau),
                      BC[self.bc_top], BC[self.bc_bottom], BC[self.bc_left], BC[self.bc_right],
                      *[int(v) for v in self.sponge], float(self.sponge_amax),
-                     rho0.ctypes.data, lam.ctypes.data, mu.ctypes.data,
+                     int(self.fs_order), rho0.ctypes.data, lam.ctypes.data, mu.ctypes.data,
                      src.shape[0], src.ctypes.data if src.size else None,
                      rec.shape[0], rec.ctypes.data if rec.size else None,
                      int(self.nthreads))

@@ -36,13 +36,18 @@
  *     (d = 0 on the first interior cell); corners take the largest value.
  *     A_max <= 0 selects 12.8/L for each layer.
  *   - Free surface: "t + Delta x" in the ABB formula is read as t + Delta t;
- *     rho_air = 1.5 rho_b - 0.5 rho_in and the tangential diagonal stress is
- *     extrapolated the same way, the other stress components of P_air are zero
- *     (P_air n = 0).  rho and P of the post-collision populations equal those of
- *     the pre-collision ones (the collision conserves both), so they are taken
- *     from f* at time t.
- *   - grad(rho) at a wall uses a ghost value: free surface 2 rho_b - rho_in,
- *     rigid wall rho_b; periodic axes wrap.
+ *     the other stress components of P_air are zero (P_air n = 0) and the
+ *     tangential diagonal stress is kept.  rho and P of the post-collision
+ *     populations equal those of the pre-collision ones (the collision conserves
+ *     both), so they are taken from f* at time t.  Two extrapolations to the
+ *     wall: fs_order = 1 is the paper's linear one, rho_air = 1.5 rho_b -
+ *     0.5 rho_in and the same for the tangential stress (Eq. 39); fs_order = 0
+ *     takes the boundary cell's own rho and stress.  The linear one has growing
+ *     modes at every tangential wavenumber (|eig| up to 1.046 per step at
+ *     tau = 1, 1.009 at tau = 0.55), the constant one none.
+ *   - grad(rho) at a wall uses a ghost value: free surface 2 rho_b - rho_in
+ *     (fs_order = 1) or rho_b (fs_order = 0), rigid wall rho_b; periodic axes
+ *     wrap.
  *   - A diagonal link that leaves the domain through both a horizontal and a
  *     vertical wall takes the rule of the horizontal (top/bottom) wall.
  *   - Source: g(x) = exp(-|x - x_s|^2 / (2 sigma^2)) for |x - x_s| <= r_cut,
@@ -86,6 +91,7 @@ typedef struct {
   int bc_top, bc_bottom, bc_left, bc_right;
   int sp_top, sp_bottom, sp_left, sp_right;
   double sp_amax;
+  int fs_order; /* free-surface extrapolation: 1 linear (Eq. 39), 0 constant */
   const double *rho0, *lam, *mu; /* [ny][nx] each */
   int nsrc;
   const double *src; /* 9 per source: x y sigma dir_x dir_y amplitude f_peak t0 r_cut */
@@ -180,11 +186,21 @@ static double wall_value(const double *fs, const oracle_problem *p, int bc,
     cell_moments(fs, p, x, y, &rb, &mxb, &myb, &pxxb, &pxyb, &pyyb);
     cell_moments(fs, p, x - nxo, y - nyo, &ri, &mxi, &myi, &pxxi, &pxyi,
                  &pyyi);
-    rho_air = 1.5 * rb - 0.5 * ri;
-    if (nyo != 0) /* horizontal wall: the tangential stress is P_xx */
-      pxx_air = 1.5 * pxxb - 0.5 * pxxi;
-    else /* vertical wall: the tangential stress is P_yy */
-      pyy_air = 1.5 * pyyb - 0.5 * pyyi;
+    if (p->fs_order == 1) {
+      /* linear extrapolation to the wall half a cell out (Eq. 39) */
+      rho_air = 1.5 * rb - 0.5 * ri;
+      if (nyo != 0) /* horizontal wall: the tangential stress is P_xx */
+        pxx_air = 1.5 * pxxb - 0.5 * pxxi;
+      else /* vertical wall: the tangential stress is P_yy */
+        pyy_air = 1.5 * pyyb - 0.5 * pyyi;
+    } else {
+      /* constant extrapolation: the values of the boundary cell */
+      rho_air = rb;
+      if (nyo != 0)
+        pxx_air = pxxb;
+      else
+        pyy_air = pyyb;
+    }
     pnxx = pxx_air - bb * rho_air;
     pnyy = pyy_air - bb * rho_air;
     pnxy = 0.0;
@@ -233,7 +249,7 @@ static double rho_ghost(const double *rho, const oracle_problem *p, int x,
     int yb = y < 0 ? 0 : p->ny - 1, yin = y < 0 ? 1 : p->ny - 2;
     int bc = y < 0 ? p->bc_top : p->bc_bottom;
     if (bc == BC_PERIODIC) return rho[(size_t)((y + p->ny) % p->ny) * p->nx + x];
-    if (bc == BC_FREE)
+    if (bc == BC_FREE && p->fs_order == 1)
       return 2.0 * rho[(size_t)yb * p->nx + x] - rho[(size_t)yin * p->nx + x];
     return rho[(size_t)yb * p->nx + x];
   }
@@ -241,7 +257,7 @@ static double rho_ghost(const double *rho, const oracle_problem *p, int x,
     int xb = x < 0 ? 0 : p->nx - 1, xin = x < 0 ? 1 : p->nx - 2;
     int bc = x < 0 ? p->bc_left : p->bc_right;
     if (bc == BC_PERIODIC) return rho[(size_t)y * p->nx + (x + p->nx) % p->nx];
-    if (bc == BC_FREE)
+    if (bc == BC_FREE && p->fs_order == 1)
       return 2.0 * rho[(size_t)y * p->nx + xb] - rho[(size_t)y * p->nx + xin];
     return rho[(size_t)y * p->nx + xb];
   }

@@ -1,0 +1,817 @@
+// Host side of the C ABI declared in include/lbm_elastic.h, plus the small
+// set-up, conversion and reduction kernels.  All device memory comes from the
+// caller's workspace; this file never allocates device memory.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "lbm_elastic.h"
+#include "lbm_kernels.cuh"
+
+using namespace lbm;
+
+namespace {
+
+constexpr size_t kAlign = 256;
+constexpr int kRedBlocks = 304;   // 2 x 152 SMs; fixed so sums are reproducible
+constexpr int kRedThreads = 256;
+constexpr int kStageCells = 1 << 18;
+constexpr unsigned kMagic = 0x4c424d45u;  // checkpoint header tag
+
+size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+struct Layout {
+  int pitch = 0;
+  long long plane = 0;
+  size_t tsize = 0, usize = 0, csize = 0;
+  size_t f[2] = {0, 0}, u = 0, lam = 0, irho = 0, src = 0, rec_ptr = 0, rec_xy = 0,
+         rec_id = 0, traces = 0, partials = 0, flags = 0, stage = 0, total = 0;
+  int rec_tiles_x = 0, rec_tiles = 0, stage_rows = 0;
+  long long mat_count = 0;
+};
+
+bool config_ok(const lbm_elastic_config *c, std::string *why) {
+  auto bad = [&](const char *m) {
+    if (why) *why = m;
+    return false;
+  };
+  if (!c) return bad("config is NULL");
+  if (c->nx < 3 || c->ny < 3) return bad("nx and ny must be >= 3");
+  if ((long long)c->nx * c->ny > (1LL << 33) || c->ny > 500000) return bad("grid too large");
+  if (c->storage < LBM_F64 || c->storage > LBM_BF16) return bad("unknown storage type");
+  if (!(c->tau > 0.5) || !std::isfinite(c->tau)) return bad("tau must be finite and > 0.5");
+  const int bcs[4] = {c->bc_top, c->bc_bottom, c->bc_left, c->bc_right};
+  for (int b : bcs)
+    if (b < LBM_BC_PERIODIC || b > LBM_BC_RIGID) return bad("unknown boundary kind");
+  if ((c->bc_top == LBM_BC_PERIODIC) != (c->bc_bottom == LBM_BC_PERIODIC))
+    return bad("periodic top/bottom must be paired");
+  if ((c->bc_left == LBM_BC_PERIODIC) != (c->bc_right == LBM_BC_PERIODIC))
+    return bad("periodic left/right must be paired");
+  const int sp[4] = {c->sponge_top, c->sponge_bottom, c->sponge_left, c->sponge_right};
+  for (int s : sp)
+    if (s < 0) return bad("sponge thickness must be >= 0");
+  if (c->sponge_top + c->sponge_bottom > c->ny || c->sponge_left + c->sponge_right > c->nx)
+    return bad("absorbing layers larger than the grid");
+  if (!std::isfinite(c->sponge_amax)) return bad("sponge_amax must be finite");
+  if (c->free_surface_order != 0 && c->free_surface_order != 1)
+    return bad("free_surface_order must be 0 or 1");
+  if (c->max_sources < 0 || c->max_receivers < 0 || c->max_steps_traced < 0)
+    return bad("capacities must be >= 0");
+  if (c->storage == LBM_F16 || c->storage == LBM_BF16)
+    return bad("FP16/BF16 storage is not built in this library version");
+  return true;
+}
+
+Layout make_layout(const lbm_elastic_config *c) {
+  Layout L;
+  L.tsize = c->storage == LBM_F64 ? 8 : (c->storage == LBM_F32 ? 4 : 2);
+  L.csize = c->storage == LBM_F64 ? 8 : 4;
+  L.usize = (c->storage == LBM_F64 || c->u_fp64) ? 8 : 4;
+  const int per_line = (int)(128 / L.tsize);
+  L.pitch = (c->nx + per_line - 1) / per_line * per_line;
+  L.plane = (long long)L.pitch * c->ny;
+  L.rec_tiles_x = (c->nx + kRecTileX - 1) / kRecTileX;
+  L.rec_tiles = L.rec_tiles_x * ((c->ny + kRecTileY - 1) / kRecTileY);
+  L.mat_count = c->material_per_cell ? L.plane : c->ny;
+  L.stage_rows = kStageCells / c->nx;
+  if (L.stage_rows < 1) L.stage_rows = 1;
+  if (L.stage_rows > c->ny) L.stage_rows = c->ny;
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    size_t o = off;
+    off = align_up(off + bytes, kAlign);
+    return o;
+  };
+  L.f[0] = take(9 * (size_t)L.plane * L.tsize);
+  L.f[1] = take(9 * (size_t)L.plane * L.tsize);
+  L.u = take(2 * (size_t)L.plane * L.usize);
+  L.lam = take((size_t)L.mat_count * L.csize);
+  L.irho = take((size_t)L.mat_count * L.csize);
+  L.src = take((size_t)c->max_sources * sizeof(SourceDev) + 8);
+  L.rec_ptr = take(((size_t)L.rec_tiles + 1) * sizeof(int));
+  L.rec_xy = take((size_t)c->max_receivers * 2 * sizeof(int) + 8);
+  L.rec_id = take((size_t)c->max_receivers * sizeof(int) + 8);
+  L.traces = take((size_t)c->max_steps_traced * c->max_receivers * 4 * sizeof(double) + 8);
+  L.partials = take((size_t)(kRedBlocks + 1) * 8 * sizeof(double));
+  L.flags = take(64);
+  size_t stage = (size_t)L.stage_rows * c->nx * 11 * sizeof(double);
+  size_t mat_stage = (size_t)3 * c->ny * sizeof(double);
+  L.stage = take(stage > mat_stage ? stage : mat_stage);
+  L.total = off;
+  return L;
+}
+
+// ------------------------------------------------------------ small kernels
+
+// Lambda = (mu - lambda)/(rho0 b^2) and 1/rho0 (Eqs. 9 and 32) from FP64
+// material arrays; flags: 1 = some Lambda != 0, 2 = mu/(rho0 b^2) != 1,
+// 4 = invalid value.
+template <class C>
+__global__ void material_kernel(const double *rho0, const double *lam, const double *mu,
+                                long long count, int per_cell, int nx, int pitch, long long off,
+                                C *lam_out, C *irho_out, int *flags) {
+  for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < count;
+       k += (long long)gridDim.x * blockDim.x) {
+    const double r = rho0[k], l = lam[k], m = mu[k];
+    long long dst = off + k;
+    if (per_cell) {
+      const long long g = off + k;  // dense index of the cell
+      dst = (g / nx) * pitch + g % nx;
+    }
+    int fl = 0;
+    if (!(r > 0.0) || !isfinite(r) || !isfinite(l) || !isfinite(m)) {
+      fl |= 4;
+      lam_out[dst] = C(0);
+      irho_out[dst] = C(1);
+    } else {
+      const double L = (m - l) / (r * (1.0 / 3.0));
+      lam_out[dst] = C(L);
+      irho_out[dst] = C(1.0 / r);
+      if (C(L) != C(0)) fl |= 1;
+      if (fabs(m / (r * (1.0 / 3.0)) - 1.0) > 1e-9) fl |= 2;
+    }
+    if (fl) atomicOr(flags, fl);
+  }
+}
+
+template <class C>
+__global__ void fill_kernel(C *p, long long n, C v) {
+  for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n;
+       k += (long long)gridDim.x * blockDim.x)
+    p[k] = v;
+}
+
+// State <-> dense FP64 rows [row0, row0 + nrows).  dst/src planes are
+// [nplanes][rows][nx] with a plane stride of dplane elements.
+template <class T>
+__global__ void to_f64_kernel(const T *s, long long splane, int pitch, int nx, int row0,
+                              int nrows, int nplanes, double *d, long long dplane) {
+  const long long n = (long long)nrows * nx;
+  for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n * nplanes;
+       k += (long long)gridDim.x * blockDim.x) {
+    const int pl = (int)(k / n);
+    const long long r = k % n;
+    const long long y = row0 + r / nx, x = r % nx;
+    d[pl * dplane + r] = (double)s[pl * splane + y * pitch + x];
+  }
+}
+
+template <class T>
+__global__ void from_f64_kernel(T *s, long long splane, int pitch, int nx, int row0, int nrows,
+                                int nplanes, const double *d, long long dplane) {
+  const long long n = (long long)nrows * nx;
+  for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n * nplanes;
+       k += (long long)gridDim.x * blockDim.x) {
+    const int pl = (int)(k / n);
+    const long long r = k % n;
+    const long long y = row0 + r / nx, x = r % nx;
+    s[pl * splane + y * pitch + x] = T(d ? d[pl * dplane + r] : 0.0);
+  }
+}
+
+// Deterministic FP64 block reduction of seven per-cell sums.
+__device__ void block_reduce7(double *v, double *out) {
+  __shared__ double sm[kRedThreads / 32][7];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+  for (int k = 0; k < 7; ++k) {
+    double t = v[k];
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
+    if (lane == 0) sm[w][k] = t;
+  }
+  __syncthreads();
+  if (threadIdx.x < 7) {
+    double t = 0.0;
+    for (int i = 0; i < kRedThreads / 32; ++i) t += sm[i][threadIdx.x];
+    out[threadIdx.x] = t;
+  }
+}
+
+template <class T, class U>
+__global__ void __launch_bounds__(kRedThreads)
+    moments_partial_kernel(const T *f, const U *u, long long plane, int pitch, int nx, int ny,
+                           double *partials) {
+  double v[7] = {0, 0, 0, 0, 0, 0, 0};
+  const long long n = (long long)nx * ny;
+  for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n;
+       k += (long long)gridDim.x * blockDim.x) {
+    const long long c = (k / nx) * pitch + k % nx;
+    double q[9];
+#pragma unroll
+    for (int i = 0; i < 9; ++i) q[i] = (double)f[i * plane + c];
+    v[0] += q[0] + q[1] + q[2] + q[3] + q[4] + q[5] + q[6] + q[7] + q[8];
+    v[1] += q[1] - q[3] + q[5] - q[6] - q[7] + q[8];
+    v[2] += q[2] - q[4] + q[5] + q[6] - q[7] - q[8];
+    v[3] += q[1] + q[3] + q[5] + q[6] + q[7] + q[8];
+    v[4] += q[5] - q[6] + q[7] - q[8];
+    v[5] += q[2] + q[4] + q[5] + q[6] + q[7] + q[8];
+    const double ux = (double)u[c], uy = (double)u[plane + c];
+    v[6] += ux * ux + uy * uy;
+  }
+  block_reduce7(v, partials + 8 * blockIdx.x);
+}
+
+__global__ void __launch_bounds__(kRedThreads) moments_final_kernel(const double *partials,
+                                                                    int nblocks, double *out) {
+  double v[7] = {0, 0, 0, 0, 0, 0, 0};
+  for (int b = threadIdx.x; b < nblocks; b += blockDim.x)
+#pragma unroll
+    for (int k = 0; k < 7; ++k) v[k] += partials[8 * b + k];
+  block_reduce7(v, out);
+}
+
+}  // namespace
+
+// ------------------------------------------------------------ the handle
+
+struct lbm_elastic {
+  lbm_elastic_config cfg;
+  Layout L;
+  char *ws = nullptr;
+  cudaStream_t stream = nullptr;
+  int cur = 0;                 // buffer holding the latest post-collision state
+  long long step = 0;
+  int traced = 0;
+  int nsrc = 0, nrec = 0;
+  bool lambda_nonzero = false;
+  long long launches = 0;
+  std::vector<SourceDev> src_host;
+  std::string err;
+};
+
+namespace {
+
+std::string g_create_error;
+
+lbm_status fail(lbm_elastic_t *h, lbm_status s, const std::string &msg) {
+  if (h) h->err = msg;
+  else g_create_error = msg;
+  return s;
+}
+
+lbm_status cuda_fail(lbm_elastic_t *h, cudaError_t e, const char *what) {
+  return fail(h, LBM_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define LBM_CUDA(h, call)                                  \
+  do {                                                     \
+    cudaError_t e_ = (call);                               \
+    if (e_ != cudaSuccess) return cuda_fail((h), e_, #call); \
+  } while (0)
+
+template <class X> X *at(lbm_elastic_t *h, size_t off) { return (X *)(h->ws + off); }
+
+int grid1d(long long n, int threads) {
+  long long b = (n + threads - 1) / threads;
+  if (b > 152 * 16) b = 152 * 16;
+  if (b < 1) b = 1;
+  return (int)b;
+}
+
+lbm_status check_launch(lbm_elastic_t *h, const char *what) {
+  h->launches++;
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(h, e, what);
+  return LBM_OK;
+}
+
+// Reads the device error flag (synchronises the stream).
+lbm_status sync_flags(lbm_elastic_t *h) {
+  int flags[2] = {0, 0};
+  LBM_CUDA(h, cudaMemcpyAsync(flags, at<int>(h, h->L.flags), sizeof(flags),
+                              cudaMemcpyDeviceToHost, h->stream));
+  LBM_CUDA(h, cudaStreamSynchronize(h->stream));
+  if (flags[0] & 1)
+    return fail(h, LBM_ERR_NONFINITE, "a step met a non-finite value (unstable run)");
+  return LBM_OK;
+}
+
+StepParams base_params(lbm_elastic_t *h) {
+  const lbm_elastic_config &c = h->cfg;
+  const Layout &L = h->L;
+  StepParams p;
+  memset(&p, 0, sizeof(p));
+  p.fin = h->ws + L.f[h->cur];
+  p.fout = h->ws + L.f[1 - h->cur];
+  p.u = h->ws + L.u;
+  p.plane = L.plane;
+  p.nx = c.nx;
+  p.ny = c.ny;
+  p.pitch = L.pitch;
+  p.bc_top = c.bc_top;
+  p.bc_bottom = c.bc_bottom;
+  p.bc_left = c.bc_left;
+  p.bc_right = c.bc_right;
+  p.sp_top = c.sponge_top;
+  p.sp_bottom = c.sponge_bottom;
+  p.sp_left = c.sponge_left;
+  p.sp_right = c.sponge_right;
+  p.fs_order = c.free_surface_order;
+  const int Ls[4] = {c.sponge_top, c.sponge_bottom, c.sponge_left, c.sponge_right};
+  for (int s = 0; s < 4; ++s) {
+    double a = 0.0;
+    if (Ls[s] > 0) {
+      const double amax = c.sponge_amax > 0.0 ? c.sponge_amax : 12.8 / Ls[s];
+      a = amax / ((double)Ls[s] * Ls[s]);
+    }
+    p.spA[s] = a;
+    p.spA_f[s] = (float)a;
+  }
+  p.omega = 1.0 / c.tau;
+  p.fcoef = 1.0 - 1.0 / (2.0 * c.tau);
+  p.omega_f = (float)p.omega;
+  p.fcoef_f = (float)p.fcoef;
+  p.lam = h->ws + L.lam;
+  p.irho = h->ws + L.irho;
+  p.mat_per_cell = c.material_per_cell;
+  p.src = at<SourceDev>(h, L.src);
+  p.nsrc = h->nsrc;
+  p.n = h->step;
+  p.trace_slot = -1;
+  p.rec_tile_ptr = at<int>(h, L.rec_ptr);
+  p.rec_xy = at<int>(h, L.rec_xy);
+  p.rec_id = at<int>(h, L.rec_id);
+  p.rec_tiles_x = L.rec_tiles_x;
+  p.nrec = h->nrec;
+  p.traces = at<double>(h, L.traces);
+  p.err = at<int>(h, L.flags);
+  return p;
+}
+
+constexpr int kBX = 32, kBY = 8;
+
+lbm_status launch_step(lbm_elastic_t *h, const StepParams &p, int mode, int rows) {
+  dim3 block(kBX, kBY);
+  dim3 grid((h->cfg.nx + kBX - 1) / kBX, (rows + kBY - 1) / kBY);
+  if (h->cfg.storage == LBM_F64)
+    launch_step_f64(p, h->lambda_nonzero, mode, grid, block, h->stream);
+  else
+    launch_step_f32(p, h->lambda_nonzero, h->cfg.u_fp64 != 0, mode, grid, block, h->stream);
+  return check_launch(h, "step kernel launch");
+}
+
+template <class T>
+lbm_status state_io(lbm_elastic_t *h, T *planes, long long splane, int nplanes, double *dst,
+                    const double *src, int on_device, long long dense_plane) {
+  // dst (to f64) or src (from f64): [nplanes][ny][nx]
+  const lbm_elastic_config &c = h->cfg;
+  const Layout &L = h->L;
+  if (on_device) {
+    const long long n = (long long)c.nx * c.ny * nplanes;
+    if (dst)
+      to_f64_kernel<T><<<grid1d(n, 256), 256, 0, h->stream>>>(planes, splane, L.pitch, c.nx, 0,
+                                                               c.ny, nplanes, dst, dense_plane);
+    else
+      from_f64_kernel<T><<<grid1d(n, 256), 256, 0, h->stream>>>(planes, splane, L.pitch, c.nx, 0,
+                                                                 c.ny, nplanes, src, dense_plane);
+    return check_launch(h, "state conversion launch");
+  }
+  double *stage = at<double>(h, L.stage);
+  for (int r0 = 0; r0 < c.ny; r0 += L.stage_rows) {
+    const int nr = (r0 + L.stage_rows <= c.ny) ? L.stage_rows : c.ny - r0;
+    const long long chunk = (long long)nr * c.nx;
+    const long long n = chunk * nplanes;
+    if (dst) {
+      to_f64_kernel<T><<<grid1d(n, 256), 256, 0, h->stream>>>(planes, splane, L.pitch, c.nx, r0,
+                                                               nr, nplanes, stage, chunk);
+      lbm_status s = check_launch(h, "state conversion launch");
+      if (s) return s;
+      for (int pl = 0; pl < nplanes; ++pl)
+        LBM_CUDA(h, cudaMemcpyAsync(dst + pl * dense_plane + (long long)r0 * c.nx,
+                                    stage + pl * chunk, chunk * sizeof(double),
+                                    cudaMemcpyDeviceToHost, h->stream));
+    } else {
+      if (src)
+        for (int pl = 0; pl < nplanes; ++pl)
+          LBM_CUDA(h, cudaMemcpyAsync(stage + pl * chunk,
+                                      src + pl * dense_plane + (long long)r0 * c.nx,
+                                      chunk * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+      from_f64_kernel<T><<<grid1d(n, 256), 256, 0, h->stream>>>(
+          planes, splane, L.pitch, c.nx, r0, nr, nplanes, src ? stage : nullptr, chunk);
+      lbm_status s = check_launch(h, "state conversion launch");
+      if (s) return s;
+    }
+    // the staging area is reused by the next chunk: wait for this one
+    LBM_CUDA(h, cudaStreamSynchronize(h->stream));
+  }
+  return LBM_OK;
+}
+
+lbm_status f_io(lbm_elastic_t *h, double *dst, const double *src, int on_device) {
+  void *f = h->ws + h->L.f[h->cur];
+  const long long dp = (long long)h->cfg.nx * h->cfg.ny;
+  if (h->cfg.storage == LBM_F64)
+    return state_io<double>(h, (double *)f, h->L.plane, 9, dst, src, on_device, dp);
+  return state_io<float>(h, (float *)f, h->L.plane, 9, dst, src, on_device, dp);
+}
+
+lbm_status u_io(lbm_elastic_t *h, double *dst, const double *src, int on_device) {
+  void *u = h->ws + h->L.u;
+  const long long dp = (long long)h->cfg.nx * h->cfg.ny;
+  if (h->L.usize == 8)
+    return state_io<double>(h, (double *)u, h->L.plane, 2, dst, src, on_device, dp);
+  return state_io<float>(h, (float *)u, h->L.plane, 2, dst, src, on_device, dp);
+}
+
+lbm_status clear_state(lbm_elastic_t *h) {
+  const Layout &L = h->L;
+  LBM_CUDA(h, cudaMemsetAsync(h->ws + L.f[0], 0, 9 * (size_t)L.plane * L.tsize, h->stream));
+  LBM_CUDA(h, cudaMemsetAsync(h->ws + L.f[1], 0, 9 * (size_t)L.plane * L.tsize, h->stream));
+  LBM_CUDA(h, cudaMemsetAsync(h->ws + L.u, 0, 2 * (size_t)L.plane * L.usize, h->stream));
+  LBM_CUDA(h, cudaMemsetAsync(h->ws + L.flags, 0, 64, h->stream));
+  h->cur = 0;
+  h->step = 0;
+  h->traced = 0;
+  return LBM_OK;
+}
+
+}  // namespace
+
+// ------------------------------------------------------------ C ABI
+
+extern "C" {
+
+size_t lbm_elastic_workspace_bytes(const lbm_elastic_config *cfg) {
+  if (!config_ok(cfg, nullptr)) return 0;
+  return make_layout(cfg).total;
+}
+
+lbm_status lbm_elastic_create(const lbm_elastic_config *cfg, void *d_workspace,
+                              size_t workspace_bytes, void *cuda_stream, lbm_elastic_t **out) {
+  std::string why;
+  if (!out) return fail(nullptr, LBM_ERR_ARG, "out is NULL");
+  *out = nullptr;
+  if (!config_ok(cfg, &why)) return fail(nullptr, LBM_ERR_ARG, why);
+  Layout L = make_layout(cfg);
+  if (!d_workspace) return fail(nullptr, LBM_ERR_WORKSPACE, "workspace is NULL");
+  if ((uintptr_t)d_workspace % kAlign)
+    return fail(nullptr, LBM_ERR_WORKSPACE, "workspace must be 256-byte aligned");
+  if (workspace_bytes < L.total)
+    return fail(nullptr, LBM_ERR_WORKSPACE,
+                "workspace too small: need " + std::to_string(L.total) + " bytes");
+  lbm_elastic_t *h = new (std::nothrow) lbm_elastic();
+  if (!h) return fail(nullptr, LBM_ERR_ARG, "out of host memory");
+  h->cfg = *cfg;
+  h->L = L;
+  h->ws = (char *)d_workspace;
+  h->stream = (cudaStream_t)cuda_stream;
+  lbm_status s = clear_state(h);
+  if (s == LBM_OK) {
+    // default material: homogeneous Poisson solid, rho0 = 1 (Lambda = 0)
+    if (L.csize == 8) {
+      fill_kernel<double><<<grid1d(L.mat_count, 256), 256, 0, h->stream>>>(
+          at<double>(h, L.lam), L.mat_count, 0.0);
+      fill_kernel<double><<<grid1d(L.mat_count, 256), 256, 0, h->stream>>>(
+          at<double>(h, L.irho), L.mat_count, 1.0);
+    } else {
+      fill_kernel<float><<<grid1d(L.mat_count, 256), 256, 0, h->stream>>>(
+          at<float>(h, L.lam), L.mat_count, 0.0f);
+      fill_kernel<float><<<grid1d(L.mat_count, 256), 256, 0, h->stream>>>(
+          at<float>(h, L.irho), L.mat_count, 1.0f);
+    }
+    s = check_launch(h, "material fill launch");
+  }
+  if (s == LBM_OK) {
+    cudaError_t e = cudaMemsetAsync(h->ws + L.rec_ptr, 0, ((size_t)L.rec_tiles + 1) * sizeof(int),
+                                    h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) s = cuda_fail(h, e, "create");
+  }
+  if (s != LBM_OK) {
+    g_create_error = h->err;
+    delete h;
+    return s;
+  }
+  *out = h;
+  return LBM_OK;
+}
+
+lbm_status lbm_elastic_set_material(lbm_elastic_t *h, const double *rho0, const double *lambda,
+                                    const double *mu, int on_device) {
+  if (!h) return LBM_ERR_ARG;
+  if (!rho0 || !lambda || !mu) return fail(h, LBM_ERR_ARG, "material pointer is NULL");
+  const lbm_elastic_config &c = h->cfg;
+  const Layout &L = h->L;
+  int *flags = at<int>(h, L.flags) + 1;
+  LBM_CUDA(h, cudaMemsetAsync(flags, 0, sizeof(int), h->stream));
+  const long long total = c.material_per_cell ? (long long)c.nx * c.ny : c.ny;
+  const long long chunk = c.material_per_cell ? (long long)L.stage_rows * c.nx : c.ny;
+  double *stage = at<double>(h, L.stage);
+  for (long long off = 0; off < total; off += chunk) {
+    const long long n = off + chunk <= total ? chunk : total - off;
+    const double *r = rho0 + off, *l = lambda + off, *m = mu + off;
+    if (!on_device) {
+      LBM_CUDA(h, cudaMemcpyAsync(stage, r, n * 8, cudaMemcpyHostToDevice, h->stream));
+      LBM_CUDA(h, cudaMemcpyAsync(stage + n, l, n * 8, cudaMemcpyHostToDevice, h->stream));
+      LBM_CUDA(h, cudaMemcpyAsync(stage + 2 * n, m, n * 8, cudaMemcpyHostToDevice, h->stream));
+      r = stage;
+      l = stage + n;
+      m = stage + 2 * n;
+    }
+    if (L.csize == 8)
+      material_kernel<double><<<grid1d(n, 256), 256, 0, h->stream>>>(
+          r, l, m, n, c.material_per_cell, c.nx, L.pitch, off, at<double>(h, L.lam),
+          at<double>(h, L.irho), flags);
+    else
+      material_kernel<float><<<grid1d(n, 256), 256, 0, h->stream>>>(
+          r, l, m, n, c.material_per_cell, c.nx, L.pitch, off, at<float>(h, L.lam),
+          at<float>(h, L.irho), flags);
+    lbm_status s = check_launch(h, "material kernel launch");
+    if (s) return s;
+    LBM_CUDA(h, cudaStreamSynchronize(h->stream));
+  }
+  int fl = 0;
+  LBM_CUDA(h, cudaMemcpyAsync(&fl, flags, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+  LBM_CUDA(h, cudaStreamSynchronize(h->stream));
+  h->lambda_nonzero = (fl & 1) != 0;
+  if (fl & 4) return fail(h, LBM_ERR_ARG, "material: rho0 <= 0 or a non-finite value");
+  if (fl & 2) {
+    h->err = "material: mu/rho0 differs from b^2 = 1/3; v_S stays 1/sqrt(3)";
+    return LBM_WARN_VS_NOT_B;
+  }
+  return LBM_OK;
+}
+
+lbm_status lbm_elastic_set_sources(lbm_elastic_t *h, const lbm_source *src, int n) {
+  if (!h) return LBM_ERR_ARG;
+  if (n < 0 || (n > 0 && !src)) return fail(h, LBM_ERR_ARG, "invalid source list");
+  if (n > h->cfg.max_sources)
+    return fail(h, LBM_ERR_CAPACITY, "more sources than max_sources");
+  std::vector<SourceDev> v((size_t)n);
+  for (int k = 0; k < n; ++k) {
+    const lbm_source &s = src[k];
+    const double vals[9] = {s.x, s.y, s.sigma, s.dir_x, s.dir_y, s.amplitude, s.f_peak, s.t0, s.r_cut};
+    for (double d : vals)
+      if (!std::isfinite(d)) return fail(h, LBM_ERR_ARG, "source value not finite");
+    if (!(s.sigma > 0.0) || s.r_cut < 0.0) return fail(h, LBM_ERR_ARG, "sigma <= 0 or r_cut < 0");
+    SourceDev &q = v[k];
+    q.x = s.x;
+    q.y = s.y;
+    q.inv2s2 = 1.0 / (2.0 * s.sigma * s.sigma);
+    q.rcut = s.r_cut;
+    q.rcut2 = s.r_cut * s.r_cut;
+    q.ax = s.amplitude * s.dir_x;
+    q.ay = s.amplitude * s.dir_y;
+    q.pif2 = M_PI * M_PI * s.f_peak * s.f_peak;
+    q.t0 = s.t0;
+    q.pad = 0.0;
+  }
+  h->src_host = v;
+  if (n)
+    LBM_CUDA(h, cudaMemcpyAsync(h->ws + h->L.src, h->src_host.data(), n * sizeof(SourceDev),
+                                cudaMemcpyHostToDevice, h->stream));
+  LBM_CUDA(h, cudaStreamSynchronize(h->stream));
+  h->nsrc = n;
+  return LBM_OK;
+}
+
+lbm_status lbm_elastic_set_receivers(lbm_elastic_t *h, const int *xy, int n) {
+  if (!h) return LBM_ERR_ARG;
+  if (n < 0 || (n > 0 && !xy)) return fail(h, LBM_ERR_ARG, "invalid receiver list");
+  if (n > h->cfg.max_receivers)
+    return fail(h, LBM_ERR_CAPACITY, "more receivers than max_receivers");
+  const Layout &L = h->L;
+  for (int r = 0; r < n; ++r)
+    if (xy[2 * r] < 0 || xy[2 * r] >= h->cfg.nx || xy[2 * r + 1] < 0 || xy[2 * r + 1] >= h->cfg.ny)
+      return fail(h, LBM_ERR_ARG, "receiver outside the grid");
+  // CSR by receiver tile (counting sort)
+  std::vector<int> ptr((size_t)L.rec_tiles + 1, 0), sxy(2 * (size_t)n + 2), sid((size_t)n + 1);
+  auto tile_of = [&](int r) {
+    return (xy[2 * r + 1] / kRecTileY) * L.rec_tiles_x + xy[2 * r] / kRecTileX;
+  };
+  for (int r = 0; r < n; ++r) ptr[tile_of(r) + 1]++;
+  for (int t = 0; t < L.rec_tiles; ++t) ptr[t + 1] += ptr[t];
+  std::vector<int> fill(ptr.begin(), ptr.end() - 1);
+  for (int r = 0; r < n; ++r) {
+    const int k = fill[tile_of(r)]++;
+    sxy[2 * k] = xy[2 * r];
+    sxy[2 * k + 1] = xy[2 * r + 1];
+    sid[k] = r;
+  }
+  LBM_CUDA(h, cudaMemcpyAsync(h->ws + L.rec_ptr, ptr.data(), ptr.size() * sizeof(int),
+                              cudaMemcpyHostToDevice, h->stream));
+  if (n) {
+    LBM_CUDA(h, cudaMemcpyAsync(h->ws + L.rec_xy, sxy.data(), 2 * (size_t)n * sizeof(int),
+                                cudaMemcpyHostToDevice, h->stream));
+    LBM_CUDA(h, cudaMemcpyAsync(h->ws + L.rec_id, sid.data(), (size_t)n * sizeof(int),
+                                cudaMemcpyHostToDevice, h->stream));
+  }
+  LBM_CUDA(h, cudaStreamSynchronize(h->stream));  // host vectors die here
+  h->nrec = n;
+  h->traced = 0;
+  return LBM_OK;
+}
+
+lbm_status lbm_elastic_reset(lbm_elastic_t *h) {
+  if (!h) return LBM_ERR_ARG;
+  return clear_state(h);
+}
+
+lbm_status lbm_elastic_step(lbm_elastic_t *h, int nsteps) {
+  if (!h) return LBM_ERR_ARG;
+  if (nsteps < 0) return fail(h, LBM_ERR_ARG, "nsteps < 0");
+  for (int s = 0; s < nsteps; ++s) {
+    StepParams p = base_params(h);
+    if (h->nrec > 0 && h->traced < h->cfg.max_steps_traced) p.trace_slot = h->traced;
+    lbm_status st = launch_step(h, p, 0, h->cfg.ny);
+    if (st) return st;
+    if (p.trace_slot >= 0) h->traced++;
+    h->cur ^= 1;
+    h->step++;
+  }
+  return LBM_OK;
+}
+
+long long lbm_elastic_step_index(const lbm_elastic_t *h) { return h ? h->step : -1; }
+
+lbm_status lbm_elastic_read_fields(lbm_elastic_t *h, double *ux, double *uy, double *vx,
+                                   double *vy, double *rho, double *pxx, double *pxy,
+                                   double *pyy, int on_device) {
+  if (!h) return LBM_ERR_ARG;
+  const lbm_elastic_config &c = h->cfg;
+  const Layout &L = h->L;
+  double *outs[8] = {ux, uy, vx, vy, rho, pxx, pxy, pyy};
+  StepParams p = base_params(h);
+  if (on_device) {
+    p.row0 = 0;
+    p.nrows = c.ny;
+    for (int k = 0; k < 8; ++k) p.out[k] = outs[k];
+    lbm_status s = launch_step(h, p, 1, c.ny);
+    if (s) return s;
+  } else {
+    double *stage = at<double>(h, L.stage);
+    for (int r0 = 0; r0 < c.ny; r0 += L.stage_rows) {
+      const int nr = (r0 + L.stage_rows <= c.ny) ? L.stage_rows : c.ny - r0;
+      const long long chunk = (long long)nr * c.nx;
+      p.row0 = r0;
+      p.nrows = nr;
+      for (int k = 0; k < 8; ++k) p.out[k] = outs[k] ? stage + k * chunk : nullptr;
+      lbm_status s = launch_step(h, p, 1, nr);
+      if (s) return s;
+      for (int k = 0; k < 8; ++k)
+        if (outs[k])
+          LBM_CUDA(h, cudaMemcpyAsync(outs[k] + (long long)r0 * c.nx, stage + k * chunk,
+                                      chunk * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+      LBM_CUDA(h, cudaStreamSynchronize(h->stream));
+    }
+  }
+  return sync_flags(h);
+}
+
+int lbm_elastic_traces_recorded(const lbm_elastic_t *h) { return h ? h->traced : 0; }
+
+lbm_status lbm_elastic_read_traces(lbm_elastic_t *h, double *out, int on_device) {
+  if (!h) return LBM_ERR_ARG;
+  const size_t bytes = (size_t)h->traced * h->nrec * 4 * sizeof(double);
+  if (bytes) {
+    if (!out) return fail(h, LBM_ERR_ARG, "out is NULL");
+    LBM_CUDA(h, cudaMemcpyAsync(out, h->ws + h->L.traces, bytes,
+                                on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                                h->stream));
+  }
+  return sync_flags(h);
+}
+
+lbm_status lbm_elastic_set_state(lbm_elastic_t *h, const double *f9, const double *u2,
+                                 long long step, int on_device) {
+  if (!h) return LBM_ERR_ARG;
+  if (!f9) return fail(h, LBM_ERR_ARG, "f9 is NULL");
+  if (step < 0) return fail(h, LBM_ERR_ARG, "step < 0");
+  lbm_status s = f_io(h, nullptr, f9, on_device);
+  if (s) return s;
+  s = u_io(h, nullptr, u2, on_device);
+  if (s) return s;
+  LBM_CUDA(h, cudaMemsetAsync(h->ws + h->L.flags, 0, 64, h->stream));
+  LBM_CUDA(h, cudaStreamSynchronize(h->stream));
+  h->step = step;
+  h->traced = 0;
+  return LBM_OK;
+}
+
+lbm_status lbm_elastic_get_state(lbm_elastic_t *h, double *f9, double *u2, int on_device) {
+  if (!h) return LBM_ERR_ARG;
+  if (f9) {
+    lbm_status s = f_io(h, f9, nullptr, on_device);
+    if (s) return s;
+  }
+  if (u2) {
+    lbm_status s = u_io(h, u2, nullptr, on_device);
+    if (s) return s;
+  }
+  return sync_flags(h);
+}
+
+size_t lbm_elastic_checkpoint_bytes(const lbm_elastic_t *h) {
+  if (!h) return 0;
+  return 256 + align_up(9 * (size_t)h->L.plane * h->L.tsize, kAlign) +
+         2 * (size_t)h->L.plane * h->L.usize;
+}
+
+lbm_status lbm_elastic_save(lbm_elastic_t *h, void *buf, int on_device) {
+  if (!h) return LBM_ERR_ARG;
+  if (!buf) return fail(h, LBM_ERR_ARG, "buffer is NULL");
+  long long hdr[8] = {(long long)kMagic, h->cfg.nx, h->cfg.ny, h->cfg.storage,
+                      (long long)h->L.usize, h->step, 0, 0};
+  char *b = (char *)buf;
+  const cudaMemcpyKind k = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+  const size_t fb = 9 * (size_t)h->L.plane * h->L.tsize;
+  if (on_device)
+    LBM_CUDA(h, cudaMemcpyAsync(b, hdr, sizeof(hdr), cudaMemcpyHostToDevice, h->stream));
+  else
+    memcpy(b, hdr, sizeof(hdr));
+  LBM_CUDA(h, cudaMemcpyAsync(b + 256, h->ws + h->L.f[h->cur], fb, k, h->stream));
+  LBM_CUDA(h, cudaMemcpyAsync(b + 256 + align_up(fb, kAlign), h->ws + h->L.u,
+                              2 * (size_t)h->L.plane * h->L.usize, k, h->stream));
+  return sync_flags(h);
+}
+
+lbm_status lbm_elastic_load(lbm_elastic_t *h, const void *buf, int on_device) {
+  if (!h) return LBM_ERR_ARG;
+  if (!buf) return fail(h, LBM_ERR_ARG, "buffer is NULL");
+  long long hdr[8];
+  const char *b = (const char *)buf;
+  if (on_device) {
+    LBM_CUDA(h, cudaMemcpyAsync(hdr, b, sizeof(hdr), cudaMemcpyDeviceToHost, h->stream));
+    LBM_CUDA(h, cudaStreamSynchronize(h->stream));
+  } else {
+    memcpy(hdr, b, sizeof(hdr));
+  }
+  if (hdr[0] != (long long)kMagic || hdr[1] != h->cfg.nx || hdr[2] != h->cfg.ny ||
+      hdr[3] != h->cfg.storage || hdr[4] != (long long)h->L.usize || hdr[5] < 0)
+    return fail(h, LBM_ERR_ARG, "checkpoint does not match this configuration");
+  const cudaMemcpyKind k = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  const size_t fb = 9 * (size_t)h->L.plane * h->L.tsize;
+  LBM_CUDA(h, cudaMemcpyAsync(h->ws + h->L.f[h->cur], b + 256, fb, k, h->stream));
+  LBM_CUDA(h, cudaMemcpyAsync(h->ws + h->L.u, b + 256 + align_up(fb, kAlign),
+                              2 * (size_t)h->L.plane * h->L.usize, k, h->stream));
+  LBM_CUDA(h, cudaMemsetAsync(h->ws + h->L.flags, 0, 64, h->stream));
+  LBM_CUDA(h, cudaStreamSynchronize(h->stream));
+  h->step = hdr[5];
+  h->traced = 0;
+  return LBM_OK;
+}
+
+lbm_status lbm_elastic_moment_sums(lbm_elastic_t *h, double out[7]) {
+  if (!h) return LBM_ERR_ARG;
+  if (!out) return fail(h, LBM_ERR_ARG, "out is NULL");
+  const Layout &L = h->L;
+  double *partials = at<double>(h, L.partials);
+  const void *f = h->ws + L.f[h->cur];
+  const void *u = h->ws + L.u;
+  if (h->cfg.storage == LBM_F64)
+    moments_partial_kernel<double, double><<<kRedBlocks, kRedThreads, 0, h->stream>>>(
+        (const double *)f, (const double *)u, L.plane, L.pitch, h->cfg.nx, h->cfg.ny, partials);
+  else if (L.usize == 8)
+    moments_partial_kernel<float, double><<<kRedBlocks, kRedThreads, 0, h->stream>>>(
+        (const float *)f, (const double *)u, L.plane, L.pitch, h->cfg.nx, h->cfg.ny, partials);
+  else
+    moments_partial_kernel<float, float><<<kRedBlocks, kRedThreads, 0, h->stream>>>(
+        (const float *)f, (const float *)u, L.plane, L.pitch, h->cfg.nx, h->cfg.ny, partials);
+  lbm_status s = check_launch(h, "moment sums launch");
+  if (s) return s;
+  moments_final_kernel<<<1, kRedThreads, 0, h->stream>>>(partials, kRedBlocks,
+                                                          partials + 8 * kRedBlocks);
+  s = check_launch(h, "moment sums launch");
+  if (s) return s;
+  LBM_CUDA(h, cudaMemcpyAsync(out, partials + 8 * kRedBlocks, 7 * sizeof(double),
+                              cudaMemcpyDeviceToHost, h->stream));
+  return sync_flags(h);
+}
+
+lbm_status lbm_elastic_sync(lbm_elastic_t *h) {
+  if (!h) return LBM_ERR_ARG;
+  return sync_flags(h);
+}
+
+lbm_status lbm_elastic_destroy(lbm_elastic_t *h) {
+  if (!h) return LBM_ERR_ARG;
+  cudaStreamSynchronize(h->stream);
+  delete h;
+  return LBM_OK;
+}
+
+const char *lbm_elastic_last_error(const lbm_elastic_t *h) {
+  return h ? h->err.c_str() : g_create_error.c_str();
+}
+
+const char *lbm_elastic_status_string(int s) {
+  switch (s) {
+    case LBM_OK: return "LBM_OK";
+    case LBM_WARN_VS_NOT_B: return "LBM_WARN_VS_NOT_B";
+    case LBM_ERR_ARG: return "LBM_ERR_ARG";
+    case LBM_ERR_UNSUPPORTED: return "LBM_ERR_UNSUPPORTED";
+    case LBM_ERR_WORKSPACE: return "LBM_ERR_WORKSPACE";
+    case LBM_ERR_CUDA: return "LBM_ERR_CUDA";
+    case LBM_ERR_NONFINITE: return "LBM_ERR_NONFINITE";
+    case LBM_ERR_TIMEOUT: return "LBM_ERR_TIMEOUT";
+    case LBM_ERR_CAPACITY: return "LBM_ERR_CAPACITY";
+    default: return "unknown status";
+  }
+}
+
+long long lbm_elastic_kernel_launches(const lbm_elastic_t *h) { return h ? h->launches : 0; }
+
+}  // extern "C"

@@ -1,0 +1,447 @@
+// Device code of the elastic-solid D2Q9 LBM step (arXiv 2009.06404) for
+// sm_103a.  The per-cell update is, in order:
+//   pull streaming with wall rules        (Eq. 18 left side; Eqs. 36-42)
+//   moments rho, m, P                      (Eq. 12 applied to f)
+//   centred density gradient               (Eq. 10)
+//   source and physical flux               (Eqs. 9, 44, half-force shift)
+//   equilibrium, BGK and forcing           (Eqs. 11, 14, 15, 18)
+//   displacement u += j / rho0 and receivers.
+// Lattice: c_0 = (0,0); c_1..4 = (1,0),(0,1),(-1,0),(0,-1);
+// c_5..8 = (1,1),(-1,1),(-1,-1),(1,-1); weights 4/9, 1/9, 1/36; b^2 = 1/3.
+// Rows are stored top (y = 0) to bottom; population plane i starts at
+// i * plane elements; a row is `pitch` elements long.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace lbm {
+
+enum { BC_PERIODIC = 0, BC_FREE = 1, BC_RIGID = 2 };
+
+// Cells per receiver tile (the receiver lookup table is per tile).
+constexpr int kRecTileX = 64;
+constexpr int kRecTileY = 4;
+
+// One body-force source, prepared on the host from an lbm_source.
+struct SourceDev {
+  double x, y;      // position (cells)
+  double inv2s2;    // 1 / (2 sigma^2)
+  double rcut, rcut2;
+  double ax, ay;    // amplitude * direction
+  double pif2;      // pi^2 f_peak^2
+  double t0;
+  double pad;
+};
+
+struct StepParams {
+  const void *fin;   // post-collision populations of step n-1 (9 planes)
+  void *fout;        // post-collision populations of step n
+  void *u;           // displacement: u_x plane then u_y plane
+  long long plane;   // elements between two planes
+  int nx, ny, pitch;
+  int bc_top, bc_bottom, bc_left, bc_right;
+  int sp_top, sp_bottom, sp_left, sp_right;
+  int fs_order;      // free-surface extrapolation: 1 linear, 0 constant
+  double spA[4];     // A_max / L^2 per layer: top, bottom, left, right
+  float spA_f[4];    // the same in FP32
+  double omega;      // 1 / tau
+  double fcoef;      // 1 - 1 / (2 tau)
+  float omega_f, fcoef_f;
+  const void *lam;   // Lambda = (mu - lambda)/(rho0 b^2), per row or per cell
+  const void *irho;  // 1 / rho0, same layout
+  int mat_per_cell;
+  const SourceDev *src;
+  int nsrc;
+  long long n;       // index of this step (force time t = n)
+  int trace_slot;    // >= 0: record receivers into this slot
+  const int *rec_tile_ptr;  // [tiles + 1] CSR over receiver tiles
+  const int *rec_xy;        // [nrec][2]  sorted by tile
+  const int *rec_id;        // [nrec]     original receiver index
+  int rec_tiles_x;
+  int nrec;
+  double *traces;           // [slots][nrec][4]
+  int *err;                 // bit 0: non-finite value met
+  // fields mode only
+  int row0, nrows;
+  double *out[8];           // ux uy vx vy rho pxx pxy pyy, [nrows][nx] each
+};
+
+// ------------------------------------------------------------ lattice
+
+__host__ __device__ constexpr int cxd(int i) {
+  return (i == 1 || i == 5 || i == 8) ? 1 : ((i == 3 || i == 6 || i == 7) ? -1 : 0);
+}
+__host__ __device__ constexpr int cyd(int i) {
+  return (i == 2 || i == 5 || i == 6) ? 1 : ((i == 4 || i == 7 || i == 8) ? -1 : 0);
+}
+__host__ __device__ constexpr int oppd(int i) {
+  return i == 0 ? 0 : (i <= 4 ? ((i + 1) % 4) + 1 : ((i - 3) % 4) + 5);
+}
+template <class C>
+__host__ __device__ constexpr C wd(int i) {
+  return i == 0 ? C(4) / C(9) : (i <= 4 ? C(1) / C(9) : C(1) / C(36));
+}
+
+// ------------------------------------------------------------ storage I/O
+
+template <class T, class C> __device__ __forceinline__ C ld(const T *p) { return C(*p); }
+template <> __device__ __forceinline__ float ld<__half, float>(const __half *p) {
+  return __half2float(*p);
+}
+template <> __device__ __forceinline__ float ld<__nv_bfloat16, float>(const __nv_bfloat16 *p) {
+  return __bfloat162float(*p);
+}
+template <class T, class C> __device__ __forceinline__ void st(T *p, C v) { *p = T(v); }
+template <> __device__ __forceinline__ void st<__half, float>(__half *p, float v) {
+  *p = __float2half_rn(v);
+}
+template <> __device__ __forceinline__ void st<__nv_bfloat16, float>(__nv_bfloat16 *p, float v) {
+  *p = __float2bfloat16_rn(v);
+}
+
+// ------------------------------------------------------------ wall rules
+
+// Moments rho and the diagonal stress components of the post-collision
+// populations at one in-domain cell (the collision conserves rho and P, so
+// these equal the moments at time t of Eqs. 39-42).
+template <class T, class C>
+__device__ void cell_rho_pdiag(const StepParams &p, const T *f, int x, int y, C &rho,
+                               C &pxx, C &pyy) {
+  const long long c = (long long)y * p.pitch + x;
+  C v[9];
+#pragma unroll
+  for (int i = 0; i < 9; ++i) v[i] = ld<T, C>(f + i * p.plane + c);
+  rho = v[0] + v[1] + v[2] + v[3] + v[4] + v[5] + v[6] + v[7] + v[8];
+  pxx = v[1] + v[3] + v[5] + v[6] + v[7] + v[8];
+  pyy = v[2] + v[4] + v[5] + v[6] + v[7] + v[8];
+}
+
+// Population i entering boundary cell (x, y) through a wall of kind bc with
+// outward normal (nxo, nyo).  Rigid: half-way bounce-back (Eq. 36).  Free
+// surface: anti-bounce-back with rho_air and the tangential stress
+// extrapolated linearly from x_b and x_in = x_b - n; P_air has no other
+// component (Eqs. 37-42).
+template <class T, class C>
+__device__ C wall_value(const StepParams &p, const T *f, int bc, int nxo, int nyo, int i,
+                        int x, int y) {
+  const int k = oppd(i);
+  const C fk = ld<T, C>(f + k * p.plane + (long long)y * p.pitch + x);
+  if (bc == BC_RIGID) return fk;
+  C rb, pxxb, pyyb, ri, pxxi, pyyi;
+  cell_rho_pdiag<T, C>(p, f, x, y, rb, pxxb, pyyb);
+  C rho_air, ptan;  // tangential stress: P_xx on a horizontal wall, P_yy on a vertical one
+  if (p.fs_order == 1) {
+    // linear extrapolation half a cell out (Eq. 39)
+    cell_rho_pdiag<T, C>(p, f, x - nxo, y - nyo, ri, pxxi, pyyi);
+    rho_air = C(1.5) * rb - C(0.5) * ri;
+    ptan = nyo != 0 ? C(1.5) * pxxb - C(0.5) * pxxi : C(1.5) * pyyb - C(0.5) * pyyi;
+  } else {
+    // constant extrapolation: the boundary cell's own values
+    rho_air = rb;
+    ptan = nyo != 0 ? pxxb : pyyb;
+  }
+  const C pnxx = (nyo != 0 ? ptan : C(0)) - rho_air * C(1.0 / 3.0);
+  const C pnyy = (nyo != 0 ? C(0) : ptan) - rho_air * C(1.0 / 3.0);
+  const int cx = cxd(k), cy = cyd(k);
+  const C h = (C(cx * cx) - C(1.0 / 3.0)) * pnxx + (C(cy * cy) - C(1.0 / 3.0)) * pnyy;
+  return -fk + C(2) * wd<C>(k) * (rho_air + C(4.5) * h);
+}
+
+// Pull of population i into (x, y) on a boundary cell (general path).
+template <class T, class C>
+__device__ __noinline__ C pull_general(const StepParams &p, const T *f, int i, int x, int y) {
+  int sx = x - cxd(i), sy = y - cyd(i);
+  if (sy < 0 || sy >= p.ny) {
+    if (p.bc_top == BC_PERIODIC) {
+      sy = sy < 0 ? sy + p.ny : sy - p.ny;
+    } else if (sy < 0) {
+      return wall_value<T, C>(p, f, p.bc_top, 0, -1, i, x, y);
+    } else {
+      return wall_value<T, C>(p, f, p.bc_bottom, 0, 1, i, x, y);
+    }
+  }
+  if (sx < 0 || sx >= p.nx) {
+    if (p.bc_left == BC_PERIODIC) {
+      sx = sx < 0 ? sx + p.nx : sx - p.nx;
+    } else if (sx < 0) {
+      return wall_value<T, C>(p, f, p.bc_left, -1, 0, i, x, y);
+    } else {
+      return wall_value<T, C>(p, f, p.bc_right, 1, 0, i, x, y);
+    }
+  }
+  return ld<T, C>(f + i * p.plane + (long long)sy * p.pitch + sx);
+}
+
+// All nine streamed populations of (x, y).
+template <class T, class C>
+__device__ __forceinline__ void gather(const StepParams &p, const T *f, int x, int y, C *fo) {
+  if (x > 0 && x < p.nx - 1 && y > 0 && y < p.ny - 1) {
+#pragma unroll
+    for (int i = 0; i < 9; ++i)
+      fo[i] = ld<T, C>(f + i * p.plane + (long long)(y - cyd(i)) * p.pitch + (x - cxd(i)));
+  } else {
+#pragma unroll
+    for (int i = 0; i < 9; ++i) fo[i] = pull_general<T, C>(p, f, i, x, y);
+  }
+}
+
+template <class T, class C>
+__device__ C rho_at(const StepParams &p, const T *f, int x, int y) {
+  C v[9];
+  gather<T, C>(p, f, x, y, v);
+  return v[0] + v[1] + v[2] + v[3] + v[4] + v[5] + v[6] + v[7] + v[8];
+}
+
+// Centred density gradient (Eq. 10) with wall ghosts: free surface
+// 2 rho_b - rho_in (linear extrapolation) or rho_b (constant), rigid wall
+// rho_b; periodic axes wrap.
+template <class T, class C>
+__device__ void grad_rho(const StepParams &p, const T *f, int x, int y, C rho, C &gx, C &gy) {
+  C rxm, rxp, rym, ryp;
+  // x direction
+  {
+    const bool lo = x == 0, hi = x == p.nx - 1;
+    int xm = x - 1, xp = x + 1;
+    if (p.bc_left == BC_PERIODIC) {
+      if (lo) xm = p.nx - 1;
+      if (hi) xp = 0;
+    }
+    rxp = (hi && p.bc_left != BC_PERIODIC) ? C(0) : rho_at<T, C>(p, f, xp, y);
+    rxm = (lo && p.bc_left != BC_PERIODIC) ? C(0) : rho_at<T, C>(p, f, xm, y);
+    const bool lin = p.fs_order == 1;
+    if (lo && p.bc_left != BC_PERIODIC)
+      rxm = (p.bc_left == BC_FREE && lin) ? C(2) * rho - rxp : rho;
+    if (hi && p.bc_right != BC_PERIODIC)
+      rxp = (p.bc_right == BC_FREE && lin) ? C(2) * rho - rxm : rho;
+  }
+  {
+    const bool lo = y == 0, hi = y == p.ny - 1;
+    int ym = y - 1, yp = y + 1;
+    if (p.bc_top == BC_PERIODIC) {
+      if (lo) ym = p.ny - 1;
+      if (hi) yp = 0;
+    }
+    ryp = (hi && p.bc_top != BC_PERIODIC) ? C(0) : rho_at<T, C>(p, f, x, yp);
+    rym = (lo && p.bc_top != BC_PERIODIC) ? C(0) : rho_at<T, C>(p, f, x, ym);
+    const bool lin = p.fs_order == 1;
+    if (lo && p.bc_top != BC_PERIODIC)
+      rym = (p.bc_top == BC_FREE && lin) ? C(2) * rho - ryp : rho;
+    if (hi && p.bc_bottom != BC_PERIODIC)
+      ryp = (p.bc_bottom == BC_FREE && lin) ? C(2) * rho - rym : rho;
+  }
+  gx = C(0.5) * (rxp - rxm);
+  gy = C(0.5) * (ryp - rym);
+}
+
+// Scalar parameter in the compute type (FP32 kernels read the FP32 copy, so
+// no FP64 conversion runs per cell).
+template <class C> __device__ __forceinline__ C par(double d, float f);
+template <> __device__ __forceinline__ double par<double>(double d, float) { return d; }
+template <> __device__ __forceinline__ float par<float>(double, float f) { return f; }
+
+// Absorbing-layer coefficient A(x) = A_max (d/L)^2, d = depth into the layer
+// (0 on the first interior cell); the largest value where layers overlap.
+template <class C>
+__device__ __forceinline__ C sponge_A(const StepParams &p, int x, int y) {
+  C a = C(0);
+  int d;
+  d = p.sp_top - y;
+  if (d > 0) a = max(a, par<C>(p.spA[0], p.spA_f[0]) * C(d * d));
+  d = y - (p.ny - 1 - p.sp_bottom);
+  if (d > 0) a = max(a, par<C>(p.spA[1], p.spA_f[1]) * C(d * d));
+  d = p.sp_left - x;
+  if (d > 0) a = max(a, par<C>(p.spA[2], p.spA_f[2]) * C(d * d));
+  d = x - (p.nx - 1 - p.sp_right);
+  if (d > 0) a = max(a, par<C>(p.spA[3], p.spA_f[3]) * C(d * d));
+  return a;
+}
+
+// Body force of step n at (x, y) (Sec. 5): sum over sources of
+// amplitude * dir * exp(-r^2/(2 sigma^2)) * ricker(n), r <= r_cut, with
+// minimum-image distances on periodic axes.  Sources are culled per warp
+// (one lane per source tests the warp's row segment), and the few cells near
+// a source evaluate the Gaussian and the wavelet in FP64.
+template <class C>
+__device__ void body_force(const StepParams &p, int x, int y, C &Fx, C &Fy) {
+  Fx = C(0);
+  Fy = C(0);
+  if (p.nsrc == 0) return;
+  const int lane = threadIdx.x & 31;
+  // the row segment this warp covers (all lanes share y when blockDim.x % 32 == 0)
+  const int xw0 = x - lane;
+  for (int s0 = 0; s0 < p.nsrc; s0 += 32) {
+    bool hit = false;
+    const int s = s0 + lane;
+    if (s < p.nsrc) {
+      const SourceDev q = p.src[s];
+      double dy = (double)y - q.y;
+      if (p.bc_top == BC_PERIODIC) dy -= p.ny * floor(dy / p.ny + 0.5);
+      // x distance from the source to the segment [xw0, xw0 + 31]
+      double dxa = (double)xw0 - q.x, dxb = (double)(xw0 + 31) - q.x;
+      double dmin;
+      if (p.bc_left == BC_PERIODIC) {
+        // distance from the source (wrapped) to the segment
+        double c = 0.5 * (dxa + dxb);
+        c -= p.nx * floor(c / p.nx + 0.5);
+        dmin = fmax(0.0, fabs(c) - 15.5);
+      } else {
+        dmin = (dxa <= 0.0 && dxb >= 0.0) ? 0.0 : fmin(fabs(dxa), fabs(dxb));
+      }
+      hit = fabs(dy) <= q.rcut + 1.0 && dmin <= q.rcut + 1.0;
+    }
+    unsigned mask = __ballot_sync(0xffffffffu, hit);
+    while (mask) {
+      const int b = __ffs(mask) - 1;
+      mask &= mask - 1;
+      const SourceDev q = p.src[s0 + b];
+      double dx = (double)x - q.x, dy = (double)y - q.y;
+      if (p.bc_left == BC_PERIODIC) dx -= p.nx * floor(dx / p.nx + 0.5);
+      if (p.bc_top == BC_PERIODIC) dy -= p.ny * floor(dy / p.ny + 0.5);
+      const double r2 = dx * dx + dy * dy;
+      if (r2 <= q.rcut2) {
+        const double tt = (double)p.n - q.t0;
+        const double a = q.pif2 * tt * tt;
+        const double rk = (1.0 - 2.0 * a) * exp(-a);
+        const double g = exp(-r2 * q.inv2s2) * rk;
+        Fx += C(q.ax * g);
+        Fy += C(q.ay * g);
+      }
+    }
+  }
+}
+
+template <class C>
+__device__ __forceinline__ C mat_at(const void *tab, int per_cell, int x, int y, int pitch) {
+  const C *t = (const C *)tab;
+  return per_cell ? t[(long long)y * pitch + x] : t[y];
+}
+
+// ------------------------------------------------------------ the step
+
+// One thread per cell.  MODE 0: full step.  MODE 1: fields of the current
+// state (no state change), rows [row0, row0 + nrows).
+template <class T, class C, class U, bool LAM, int MODE>
+__global__ void __launch_bounds__(256) step_kernel(const StepParams p) {
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  const int y = blockIdx.y * blockDim.y + threadIdx.y + (MODE == 1 ? p.row0 : 0);
+  const int yend = MODE == 1 ? p.row0 + p.nrows : p.ny;
+  // Whole warps stay alive for the warp-level source culling; cells outside
+  // the grid are clamped and write nothing.
+  const bool active = x < p.nx && y < yend;
+  const int xc = x < p.nx ? x : p.nx - 1;
+  const int yc = y < yend ? y : yend - 1;
+  const T *fin = (const T *)p.fin;
+
+  C f[9];
+  gather<T, C>(p, fin, xc, yc, f);
+  const C rho = f[0] + f[1] + f[2] + f[3] + f[4] + f[5] + f[6] + f[7] + f[8];
+  const C mx = f[1] - f[3] + f[5] - f[6] - f[7] + f[8];
+  const C my = f[2] - f[4] + f[5] + f[6] - f[7] - f[8];
+  const C pxx = f[1] + f[3] + f[5] + f[6] + f[7] + f[8];
+  const C pyy = f[2] + f[4] + f[5] + f[6] + f[7] + f[8];
+  const C pxy = f[5] - f[6] + f[7] - f[8];
+
+  C Gx = C(0), Gy = C(0);
+  if (LAM) {
+    C gx, gy;
+    grad_rho<T, C>(p, fin, xc, yc, rho, gx, gy);
+    // elastic force (mu - lambda)/rho0 grad rho = Lambda b^2 grad rho (Eq. 9)
+    const C lb2 = mat_at<C>(p.lam, p.mat_per_cell, xc, yc, p.pitch) * C(1.0 / 3.0);
+    Gx = lb2 * gx;
+    Gy = lb2 * gy;
+  }
+  C Fx, Fy;
+  body_force<C>(p, xc, yc, Fx, Fy);
+  const C A = sponge_A<C>(p, xc, yc);
+  // physical flux with the half-force shift; the absorbing term -A j is
+  // taken implicitly (Eq. 44 as a forcing)
+  const C inv = C(1) / (C(1) + C(0.5) * A);
+  const C jx = (mx + C(0.5) * (Gx + Fx)) * inv;
+  const C jy = (my + C(0.5) * (Gy + Fy)) * inv;
+  const C Sx = Gx + Fx - A * jx;
+  const C Sy = Gy + Fy - A * jy;
+  const C irho = mat_at<C>(p.irho, p.mat_per_cell, xc, yc, p.pitch);
+
+  if (MODE == 1) {
+    if (!active) return;
+    const long long o = (long long)(y - p.row0) * p.nx + x;
+    const long long c = (long long)y * p.pitch + x;
+    const U *u = (const U *)p.u;
+    if (p.out[0]) p.out[0][o] = (double)u[c];
+    if (p.out[1]) p.out[1][o] = (double)u[p.plane + c];
+    if (p.out[2]) p.out[2][o] = (double)(jx * irho);
+    if (p.out[3]) p.out[3][o] = (double)(jy * irho);
+    if (p.out[4]) p.out[4][o] = (double)rho;
+    if (p.out[5]) p.out[5][o] = (double)pxx;
+    if (p.out[6]) p.out[6][o] = (double)pxy;
+    if (p.out[7]) p.out[7][o] = (double)pyy;
+    return;
+  }
+
+  // Equilibrium (Eqs. 14-15) with b^2 = 1/3: f^eq_i = w_i (rho + 3 c_i.j
+  // + 9/2 H_i:P^n), H_i = c_i c_i - I/3, P^n = P - rho/3 I.
+  const C third = C(1.0 / 3.0);
+  const C a = pxx - rho * third;   // P^n_xx
+  const C d = pyy - rho * third;   // P^n_yy
+  const C hp0 = -(a + d) * third;                     // H_0 : P^n
+  const C hpx = C(2) * third * a - third * d;         // i = 1, 3
+  const C hpy = C(2) * third * d - third * a;         // i = 2, 4
+  const C hpdp = C(2) * third * (a + d) + C(2) * pxy; // i = 5, 7 (c_x c_y = +1)
+  const C hpdm = C(2) * third * (a + d) - C(2) * pxy; // i = 6, 8 (c_x c_y = -1)
+  const C om = par<C>(p.omega, p.omega_f), fc = par<C>(p.fcoef, p.fcoef_f);
+  const C k1 = C(1) - om;
+  // forcing S_i = 3 w_i c_i.S (Eq. 11); collision f* = (1-w) f + w f^eq + fc S_i
+  C fs[9];
+  {
+    const C w0 = C(4.0 / 9.0), w1 = C(1.0 / 9.0), w2 = C(1.0 / 36.0);
+    const C r45 = C(4.5);
+    fs[0] = k1 * f[0] + om * w0 * (rho + r45 * hp0);
+    const C ex1 = w1 * (rho + r45 * hpx), ey1 = w1 * (rho + r45 * hpy);
+    const C jx3 = C(3) * jx, jy3 = C(3) * jy, sx3 = C(3) * Sx, sy3 = C(3) * Sy;
+    fs[1] = k1 * f[1] + om * (ex1 + w1 * jx3) + fc * w1 * sx3;
+    fs[3] = k1 * f[3] + om * (ex1 - w1 * jx3) - fc * w1 * sx3;
+    fs[2] = k1 * f[2] + om * (ey1 + w1 * jy3) + fc * w1 * sy3;
+    fs[4] = k1 * f[4] + om * (ey1 - w1 * jy3) - fc * w1 * sy3;
+    const C edp = w2 * (rho + r45 * hpdp), edm = w2 * (rho + r45 * hpdm);
+    const C jp = jx3 + jy3, jm = jx3 - jy3, sp = sx3 + sy3, sm = sx3 - sy3;
+    fs[5] = k1 * f[5] + om * (edp + w2 * jp) + fc * w2 * sp;   // ( 1,  1)
+    fs[7] = k1 * f[7] + om * (edp - w2 * jp) - fc * w2 * sp;   // (-1, -1)
+    fs[8] = k1 * f[8] + om * (edm + w2 * jm) + fc * w2 * sm;   // ( 1, -1)
+    fs[6] = k1 * f[6] + om * (edm - w2 * jm) - fc * w2 * sm;   // (-1,  1)
+  }
+  if (!active) return;
+  const long long c = (long long)y * p.pitch + x;
+  T *fout = (T *)p.fout;
+#pragma unroll
+  for (int i = 0; i < 9; ++i) st<T, C>(fout + i * p.plane + c, fs[i]);
+  U *u = (U *)p.u;
+  const U vx = U(jx * irho), vy = U(jy * irho);
+  const U ux = u[c] + vx, uy = u[p.plane + c] + vy;
+  u[c] = ux;
+  u[p.plane + c] = uy;
+  if (!(isfinite(rho) && isfinite(jx) && isfinite(jy))) atomicOr(p.err, 1);
+  if (p.trace_slot >= 0) {
+    const int tile = (y / kRecTileY) * p.rec_tiles_x + x / kRecTileX;
+    const int r0 = p.rec_tile_ptr[tile], r1 = p.rec_tile_ptr[tile + 1];
+    for (int r = r0; r < r1; ++r) {
+      if (p.rec_xy[2 * r] == x && p.rec_xy[2 * r + 1] == y) {
+        double *t = p.traces + ((long long)p.trace_slot * p.nrec + p.rec_id[r]) * 4;
+        t[0] = (double)ux;
+        t[1] = (double)uy;
+        t[2] = (double)vx;
+        t[3] = (double)vy;
+      }
+    }
+  }
+}
+
+// Launch entry points, one translation unit per storage type.
+void launch_step_f64(const StepParams &p, bool lam, int mode, dim3 grid, dim3 block,
+                     cudaStream_t s);
+void launch_step_f32(const StepParams &p, bool lam, bool u64, int mode, dim3 grid, dim3 block,
+                     cudaStream_t s);
+
+}  // namespace lbm

@@ -1,0 +1,25 @@
+// FP32 storage and arithmetic instantiations of the step kernel, with the
+// displacement accumulated in FP32 or FP64.
+#include "lbm_kernels.cuh"
+
+namespace lbm {
+
+template <class U>
+static void launch_u(const StepParams &p, bool lam, int mode, dim3 grid, dim3 block,
+                     cudaStream_t s) {
+  if (mode == 0) {
+    if (lam) step_kernel<float, float, U, true, 0><<<grid, block, 0, s>>>(p);
+    else step_kernel<float, float, U, false, 0><<<grid, block, 0, s>>>(p);
+  } else {
+    if (lam) step_kernel<float, float, U, true, 1><<<grid, block, 0, s>>>(p);
+    else step_kernel<float, float, U, false, 1><<<grid, block, 0, s>>>(p);
+  }
+}
+
+void launch_step_f32(const StepParams &p, bool lam, bool u64, int mode, dim3 grid, dim3 block,
+                     cudaStream_t s) {
+  if (u64) launch_u<double>(p, lam, mode, grid, block, s);
+  else launch_u<float>(p, lam, mode, grid, block, s);
+}
+
+}  // namespace lbm

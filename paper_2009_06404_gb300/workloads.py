@@ -37,6 +37,7 @@ class Workload:
     bc: Sequence[str] = ("periodic",) * 4      # top, bottom, left, right
     sponge: Sequence[int] = (0, 0, 0, 0)       # top, bottom, left, right
     sponge_amax: float = 0.0                   # <= 0: 12.8 / L per layer
+    fs_order: int = 0                          # free-surface extrapolation: 0 constant, 1 linear
     rho0: np.ndarray = None                    # per row [ny] or per cell [ny][nx]
     lam: np.ndarray = None
     mu: np.ndarray = None

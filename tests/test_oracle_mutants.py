@@ -34,6 +34,8 @@ MUTANTS = {
                  "double fk = cplane(fs, p, k)[c];\n  if (bc == BC_RIGID) return cplane(fs, p, i)[c];"),
     # free-surface extrapolation weights swapped (Eq. 39)
     "abb_extrapolation": ("rho_air = 1.5 * rb - 0.5 * ri;", "rho_air = 0.5 * rb + 0.5 * ri;"),
+    # constant free-surface extrapolation taking the inner cell (reading of Eq. 39)
+    "abb_constant": ("rho_air = rb;\n", "rho_air = ri;\n"),
     # anti-bounce-back without the sign flip (Eq. 38)
     "abb_sign": ("return -fk + 2.0 * wt[k] *", "return fk + 2.0 * wt[k] *"),
     # a diagonal weight off (Sec. 2, D2Q9)

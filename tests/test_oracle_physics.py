@@ -105,7 +105,7 @@ def test_spectral_reference_converges(ncpu):
     assert ps[2] < 0.6 * ps[1]
 
 
-def _reflection_signs(wall, ncpu):
+def _reflection_signs(wall, ncpu, fs_order=1):
     """Vertical P pulse towards a wall: j_y of the direct and reflected pulses
     at a receiver between the source and the wall."""
     nx, ny = 64, 240
@@ -114,7 +114,7 @@ def _reflection_signs(wall, ncpu):
     else:
         ys, yr, bc = 40, 20, dict(bc_top="free", bc_bottom="rigid")
     src = [nx / 2, ys, 3.0, 0.0, 1.0, 1.0, 0.05, 30.0, 24.0]
-    prob = _problem(nx, ny, 0.25, src, [[nx // 2, yr]], nthreads=ncpu, **bc)
+    prob = _problem(nx, ny, 0.25, src, [[nx // 2, yr]], nthreads=ncpu, fs_order=fs_order, **bc)
     _, tr = oracle.run(prob, 130)
     jy = tr[:, 0, 3]
     # P speed is 1 at nu = 0.25: direct at ~t0 + 20, reflected at ~t0 + 60
@@ -124,12 +124,13 @@ def _reflection_signs(wall, ncpu):
 
 
 @pytest.mark.slow
-def test_reflection_phase_rigid_and_free(ncpu):
+@pytest.mark.parametrize("fs_order", [0, 1])
+def test_reflection_phase_rigid_and_free(ncpu, fs_order):
     """Sec. 6.3: after reflection the vertical flux keeps its sign at a free
     surface and changes sign at a rigid wall."""
-    d, r = _reflection_signs("rigid", ncpu)
+    d, r = _reflection_signs("rigid", ncpu, fs_order)
     assert np.sign(d) != np.sign(r) and abs(r) > 0.2 * abs(d)
-    d, r = _reflection_signs("free", ncpu)
+    d, r = _reflection_signs("free", ncpu, fs_order)
     assert np.sign(d) == np.sign(r) and abs(r) > 0.2 * abs(d)
 
 
@@ -167,7 +168,8 @@ def test_absorbing_layer_reflection(ncpu):
 
 
 @pytest.mark.slow
-def test_rayleigh_wave_speed(golden, ncpu):
+@pytest.mark.parametrize("fs_order", [0, 1])
+def test_rayleigh_wave_speed(golden, ncpu, fs_order):
     """Sec. 7: on a half-space with a free top the surface wave travels at the
     Rayleigh speed v_R = v_S sqrt(0.8453) = 0.5308 for nu = 0.25 (Eq. 46); the
     paper measures 0.5315.  Cross-correlating the vertical flux of two surface
@@ -176,7 +178,7 @@ def test_rayleigh_wave_speed(golden, ncpu):
     src = [160.0, 2.0, 3.0, 0.0, 1.0, 1.0, 0.05, 30.0, 24.0]
     x1, x2 = 300, 500
     prob = _problem(nx, ny, 0.25, src, [[x1, 0], [x2, 0]], nthreads=ncpu,
-                    bc_top="free", bc_bottom="rigid", sponge=(0, L, L, L))
+                    bc_top="free", bc_bottom="rigid", sponge=(0, L, L, L), fs_order=fs_order)
     T = 760
     _, tr = oracle.run(prob, T)
     a, b = tr[:, 0, 3], tr[:, 1, 3]

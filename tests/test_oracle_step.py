@@ -112,12 +112,14 @@ def test_bounce_back_rule():
     np.testing.assert_array_equal(f[5][3], np.roll(fs[5][2], 1))
 
 
-def test_free_surface_rule_preserves_equilibrium_of_air_state():
+@pytest.mark.parametrize("fs_order", [0, 1])
+def test_free_surface_rule_preserves_equilibrium_of_air_state(fs_order):
     """Eqs. 37-42: if the post-collision populations at the surface cell and
     the cell below are the equilibria of a state with zero flux whose stress
     has only the tangential component, the anti-bounce-back returns the
-    equilibrium population itself (-f + 2 f^eq = f^eq)."""
-    prob = _prob(6, bc_top="free", bc_bottom="rigid")
+    equilibrium population itself (-f + 2 f^eq = f^eq), with either
+    extrapolation to the wall."""
+    prob = _prob(6, bc_top="free", bc_bottom="rigid", fs_order=fs_order)
     rho, pxx = 0.37, 0.21
     feq = oracle.equilibrium(rho, 0.0, 0.0, pxx, 0.0, 0.0)
     fs = np.zeros((9, 6, 6))
@@ -127,13 +129,14 @@ def test_free_surface_rule_preserves_equilibrium_of_air_state():
         np.testing.assert_allclose(f[i][0], feq[i], atol=1e-15)
 
 
-def test_free_surface_extrapolation():
-    """Eqs. 39-42: rho_air = 1.5 rho_b - 0.5 rho_in and the same linear
-    extrapolation for the tangential stress; the normal and shear components
-    of P_air are zero.  Checked through the returned population against the
-    formula f_ibar = -f*_i + 2 w_i (rho_air + P^n_air : H_i / (2 b^4))."""
+@pytest.mark.parametrize("fs_order", [0, 1])
+def test_free_surface_extrapolation(fs_order):
+    """Eqs. 38-42: f_ibar = -f*_i + 2 w_i (rho_air + P^n_air : H_i / (2 b^4)),
+    with P_air keeping only the tangential stress.  fs_order = 1 is the
+    printed linear extrapolation rho_air = 1.5 rho_b - 0.5 rho_in (Eq. 39) and
+    the same for the stress; fs_order = 0 takes the boundary cell's values."""
     _, _, w, b2 = oracle.lattice()
-    prob = _prob(5, bc_top="free", bc_bottom="free")
+    prob = _prob(5, bc_top="free", bc_bottom="free", fs_order=fs_order)
     rng = np.random.default_rng(5)
     fs = rng.standard_normal((9, 5, 5))
     f = oracle.stream(prob, fs)
@@ -147,14 +150,54 @@ def test_free_surface_extrapolation():
     for (yb, yin, incoming) in ((0, 1, (2, 5, 6)), (4, 3, (4, 7, 8))):
         rb, pb = mom(yb)
         ri, pi = mom(yin)
-        rho_air = 1.5 * rb - 0.5 * ri
-        pxx_air = 1.5 * pb - 0.5 * pi
+        if fs_order == 1:
+            rho_air, pxx_air = 1.5 * rb - 0.5 * ri, 1.5 * pb - 0.5 * pi
+        else:
+            rho_air, pxx_air = rb, pb
         Pn = np.array([[pxx_air - b2 * rho_air, 0.0], [0.0, -b2 * rho_air]])
         for i in incoming:
             k = [j for j in range(9) if CX[j] == -CX[i] and CY[j] == -CY[i]][0]
             H = np.outer(c[k], c[k]) - b2 * np.eye(2)
             want = -fs[k, yb, x] + 2 * w[k] * (rho_air + np.sum(Pn * H) / (2 * b2 * b2))
             assert f[i, yb, x] == pytest.approx(want, abs=1e-14)
+
+
+def _boundary_radius(fs_order, nu, tau, ny=12, n=8, bc=("free", "rigid")):
+    """Largest |eigenvalue| of the one-step operator of a channel that is
+    periodic in x (plane waves exp(i k_x x), k_x = 2 pi m / n) and bounded by
+    the given walls in y, built column by column from the oracle's step."""
+    lam, mu = theory.lame_from_nu(nu)
+    p = oracle.Problem(nx=n, ny=ny, tau=tau, bc_top=bc[0], bc_bottom=bc[1], rho0=np.ones(ny),
+                       lam=np.full(ny, lam), mu=np.full(ny, mu), fs_order=fs_order)
+    X = np.arange(n)
+    best = 0.0
+    for m in range(n // 2 + 1):
+        ph = np.exp(2j * np.pi * m * X / n)
+        M = np.zeros((9 * ny, 9 * ny), complex)
+        for col in range(9 * ny):
+            i, y = divmod(col, ny)
+            out = np.zeros((9, ny, n), complex)
+            for part, sc in ((ph.real, 1.0), (ph.imag, 1j)):
+                fs = np.zeros((9, ny, n))
+                fs[i, y, :] = part
+                st, _ = oracle.run(p, 1, oracle.State(p, fs=fs), traces=False)
+                out += sc * st.fs
+            M[:, col] = out[:, :, 0].reshape(-1)
+        best = max(best, float(np.abs(np.linalg.eigvals(M)).max()))
+    return best
+
+
+@pytest.mark.slow
+def test_wall_stability():
+    """Rigid walls (Eq. 36) and the free surface with constant extrapolation
+    add no growing mode (|eig| <= 1 for every tangential wavenumber, nu = 0.2
+    and 0.3 at tau = 1); the printed linear extrapolation (Eq. 39) does: its
+    largest eigenvalue exceeds 1 (about 1.046 per step at nu = 0.25, tau = 1)."""
+    assert _boundary_radius(0, 0.25, 1.0, bc=("rigid", "rigid")) <= 1 + 1e-12
+    for nu in (0.2, 0.3):
+        assert _boundary_radius(0, nu, 1.0) <= 1 + 1e-12
+    r = _boundary_radius(1, 0.25, 1.0)
+    assert r > 1.02
 
 
 def _rotate90(fs):
