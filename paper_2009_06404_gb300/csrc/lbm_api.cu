@@ -40,7 +40,12 @@ bool config_ok(const lbm_elastic_config *c, std::string *why) {
   };
   if (!c) return bad("config is NULL");
   if (c->nx < 3 || c->ny < 3) return bad("nx and ny must be >= 3");
-  if ((long long)c->nx * c->ny > (1LL << 33) || c->ny > 500000) return bad("grid too large");
+  {
+    // 32-bit element offsets inside the kernels: 9 planes of the padded grid
+    const long long per_line = c->storage == LBM_F64 ? 16 : 32;
+    const long long pitch = (c->nx + per_line - 1) / per_line * per_line;
+    if (c->ny > 500000 || 9 * pitch * c->ny >= (1LL << 31)) return bad("grid too large");
+  }
   if (c->storage < LBM_F64 || c->storage > LBM_BF16) return bad("unknown storage type");
   if (!(c->tau > 0.5) || !std::isfinite(c->tau)) return bad("tau must be finite and > 0.5");
   const int bcs[4] = {c->bc_top, c->bc_bottom, c->bc_left, c->bc_right};
@@ -551,13 +556,17 @@ lbm_status lbm_elastic_set_sources(lbm_elastic_t *h, const lbm_source *src, int 
     q.x = s.x;
     q.y = s.y;
     q.inv2s2 = 1.0 / (2.0 * s.sigma * s.sigma);
-    q.rcut = s.r_cut;
     q.rcut2 = s.r_cut * s.r_cut;
+    if (std::fabs(s.x) > 1e9 || std::fabs(s.y) > 1e9 || s.r_cut > 1e9)
+      return fail(h, LBM_ERR_ARG, "source position or r_cut out of range");
+    q.xc = (int)std::floor(s.x + 0.5);
+    q.yc = (int)std::floor(s.y + 0.5);
+    q.rb = (int)std::ceil(s.r_cut) + 1;
+    q.pad = 0;
     q.ax = s.amplitude * s.dir_x;
     q.ay = s.amplitude * s.dir_y;
     q.pif2 = M_PI * M_PI * s.f_peak * s.f_peak;
     q.t0 = s.t0;
-    q.pad = 0.0;
   }
   h->src_host = v;
   if (n)

@@ -29,18 +29,20 @@ constexpr int kRecTileY = 4;
 struct SourceDev {
   double x, y;      // position (cells)
   double inv2s2;    // 1 / (2 sigma^2)
-  double rcut, rcut2;
+  double rcut2;     // r_cut^2
   double ax, ay;    // amplitude * direction
   double pif2;      // pi^2 f_peak^2
   double t0;
-  double pad;
+  int xc, yc;       // nearest cell of the position
+  int rb;           // integer bound: ceil(r_cut) + 1 cells around (xc, yc)
+  int pad;
 };
 
 struct StepParams {
   const void *fin;   // post-collision populations of step n-1 (9 planes)
   void *fout;        // post-collision populations of step n
   void *u;           // displacement: u_x plane then u_y plane
-  long long plane;   // elements between two planes
+  int plane;         // elements between two planes (9 * plane < 2^31)
   int nx, ny, pitch;
   int bc_top, bc_bottom, bc_left, bc_right;
   int sp_top, sp_bottom, sp_left, sp_right;
@@ -110,7 +112,7 @@ template <> __device__ __forceinline__ void st<__nv_bfloat16, float>(__nv_bfloat
 template <class T, class C>
 __device__ void cell_rho_pdiag(const StepParams &p, const T *f, int x, int y, C &rho,
                                C &pxx, C &pyy) {
-  const long long c = (long long)y * p.pitch + x;
+  const int c = y * p.pitch + x;
   C v[9];
 #pragma unroll
   for (int i = 0; i < 9; ++i) v[i] = ld<T, C>(f + i * p.plane + c);
@@ -128,7 +130,7 @@ template <class T, class C>
 __device__ C wall_value(const StepParams &p, const T *f, int bc, int nxo, int nyo, int i,
                         int x, int y) {
   const int k = oppd(i);
-  const C fk = ld<T, C>(f + k * p.plane + (long long)y * p.pitch + x);
+  const C fk = ld<T, C>(f + k * p.plane + y * p.pitch + x);
   if (bc == BC_RIGID) return fk;
   C rb, pxxb, pyyb, ri, pxxi, pyyi;
   cell_rho_pdiag<T, C>(p, f, x, y, rb, pxxb, pyyb);
@@ -172,16 +174,16 @@ __device__ __noinline__ C pull_general(const StepParams &p, const T *f, int i, i
       return wall_value<T, C>(p, f, p.bc_right, 1, 0, i, x, y);
     }
   }
-  return ld<T, C>(f + i * p.plane + (long long)sy * p.pitch + sx);
+  return ld<T, C>(f + i * p.plane + sy * p.pitch + sx);
 }
 
 // All nine streamed populations of (x, y).
 template <class T, class C>
 __device__ __forceinline__ void gather(const StepParams &p, const T *f, int x, int y, C *fo) {
   if (x > 0 && x < p.nx - 1 && y > 0 && y < p.ny - 1) {
+    const T *b = f + (y * p.pitch + x);
 #pragma unroll
-    for (int i = 0; i < 9; ++i)
-      fo[i] = ld<T, C>(f + i * p.plane + (long long)(y - cyd(i)) * p.pitch + (x - cxd(i)));
+    for (int i = 0; i < 9; ++i) fo[i] = ld<T, C>(b + (i * p.plane - cyd(i) * p.pitch - cxd(i)));
   } else {
 #pragma unroll
     for (int i = 0; i < 9; ++i) fo[i] = pull_general<T, C>(p, f, i, x, y);
@@ -264,51 +266,55 @@ __device__ __forceinline__ C sponge_A(const StepParams &p, int x, int y) {
 // minimum-image distances on periodic axes.  Sources are culled per warp
 // (one lane per source tests the warp's row segment), and the few cells near
 // a source evaluate the Gaussian and the wavelet in FP64.
+// Force of one source at (x, y) for step n, in FP64 (only called for the
+// few cells of warps near a source; out of line so that the compiler cannot
+// hoist its FP64 conversions into the path every cell takes).
+static __device__ __noinline__ double2 source_term(const SourceDev &q, int x, int y, long long n, int nx,
+                                            int ny, int wrap_x, int wrap_y) {
+  double dx = (double)x - q.x, dy = (double)y - q.y;
+  if (wrap_x) dx -= nx * floor(dx / nx + 0.5);
+  if (wrap_y) dy -= ny * floor(dy / ny + 0.5);
+  const double r2 = dx * dx + dy * dy;
+  if (!(r2 <= q.rcut2)) return make_double2(0.0, 0.0);
+  const double tt = (double)n - q.t0;
+  const double a = q.pif2 * tt * tt;
+  const double g = exp(-r2 * q.inv2s2) * (1.0 - 2.0 * a) * exp(-a);
+  return make_double2(q.ax * g, q.ay * g);
+}
+
 template <class C>
 __device__ void body_force(const StepParams &p, int x, int y, C &Fx, C &Fy) {
   Fx = C(0);
   Fy = C(0);
   if (p.nsrc == 0) return;
   const int lane = threadIdx.x & 31;
-  // the row segment this warp covers (all lanes share y when blockDim.x % 32 == 0)
-  const int xw0 = x - lane;
+  // the row segment this warp covers (all lanes share y when blockDim.x % 32 == 0);
+  // the cull test uses integers only
+  const int xmid = x - lane + 16;
   for (int s0 = 0; s0 < p.nsrc; s0 += 32) {
     bool hit = false;
     const int s = s0 + lane;
     if (s < p.nsrc) {
-      const SourceDev q = p.src[s];
-      double dy = (double)y - q.y;
-      if (p.bc_top == BC_PERIODIC) dy -= p.ny * floor(dy / p.ny + 0.5);
-      // x distance from the source to the segment [xw0, xw0 + 31]
-      double dxa = (double)xw0 - q.x, dxb = (double)(xw0 + 31) - q.x;
-      double dmin;
-      if (p.bc_left == BC_PERIODIC) {
-        // distance from the source (wrapped) to the segment
-        double c = 0.5 * (dxa + dxb);
-        c -= p.nx * floor(c / p.nx + 0.5);
-        dmin = fmax(0.0, fabs(c) - 15.5);
-      } else {
-        dmin = (dxa <= 0.0 && dxb >= 0.0) ? 0.0 : fmin(fabs(dxa), fabs(dxb));
+      const SourceDev &q = p.src[s];
+      int dy = y - q.yc, dx = xmid - q.xc;
+      if (p.bc_top == BC_PERIODIC) {
+        if (dy > p.ny / 2) dy -= p.ny;
+        else if (dy < -(p.ny / 2)) dy += p.ny;
       }
-      hit = fabs(dy) <= q.rcut + 1.0 && dmin <= q.rcut + 1.0;
+      if (p.bc_left == BC_PERIODIC) {
+        if (dx > p.nx / 2) dx -= p.nx;
+        else if (dx < -(p.nx / 2)) dx += p.nx;
+      }
+      hit = abs(dy) <= q.rb && abs(dx) <= q.rb + 17;
     }
     unsigned mask = __ballot_sync(0xffffffffu, hit);
     while (mask) {
       const int b = __ffs(mask) - 1;
       mask &= mask - 1;
-      const SourceDev q = p.src[s0 + b];
-      double dx = (double)x - q.x, dy = (double)y - q.y;
-      if (p.bc_left == BC_PERIODIC) dx -= p.nx * floor(dx / p.nx + 0.5);
-      if (p.bc_top == BC_PERIODIC) dy -= p.ny * floor(dy / p.ny + 0.5);
-      const double r2 = dx * dx + dy * dy;
-      if (r2 <= q.rcut2) {
-        const double tt = (double)p.n - q.t0;
-        const double a = q.pif2 * tt * tt;
-        const double rk = (1.0 - 2.0 * a) * exp(-a);
-        const double g = exp(-r2 * q.inv2s2) * rk;
-        Fx += C(q.ax * g);
-        Fy += C(q.ay * g);
-      }
+      const double2 F = source_term(p.src[s0 + b], x, y, p.n, p.nx, p.ny,
+                                    p.bc_left == BC_PERIODIC, p.bc_top == BC_PERIODIC);
+      Fx += C(F.x);
+      Fy += C(F.y);
     }
   }
 }
@@ -316,45 +322,48 @@ __device__ void body_force(const StepParams &p, int x, int y, C &Fx, C &Fy) {
 template <class C>
 __device__ __forceinline__ C mat_at(const void *tab, int per_cell, int x, int y, int pitch) {
   const C *t = (const C *)tab;
-  return per_cell ? t[(long long)y * pitch + x] : t[y];
+  return per_cell ? t[y * pitch + x] : t[y];
 }
 
 // ------------------------------------------------------------ the step
 
-// One thread per cell.  MODE 0: full step.  MODE 1: fields of the current
-// state (no state change), rows [row0, row0 + nrows).
-template <class T, class C, class U, bool LAM, int MODE>
-__global__ void __launch_bounds__(256) step_kernel(const StepParams p) {
-  const int x = blockIdx.x * blockDim.x + threadIdx.x;
-  const int y = blockIdx.y * blockDim.y + threadIdx.y + (MODE == 1 ? p.row0 : 0);
-  const int yend = MODE == 1 ? p.row0 + p.nrows : p.ny;
-  // Whole warps stay alive for the warp-level source culling; cells outside
-  // the grid are clamped and write nothing.
-  const bool active = x < p.nx && y < yend;
-  const int xc = x < p.nx ? x : p.nx - 1;
-  const int yc = y < yend ? y : yend - 1;
-  const T *fin = (const T *)p.fin;
+// Density of the streamed populations at an interior cell whose nine
+// upstream cells all lie inside the grid (direct loads only).
+template <class T, class C>
+__device__ __forceinline__ C rho_direct(const StepParams &p, const T *f, int x, int y) {
+  const T *b = f + (y * p.pitch + x);
+  C r = C(0);
+#pragma unroll
+  for (int i = 0; i < 9; ++i) r += ld<T, C>(b + (i * p.plane - cyd(i) * p.pitch - cxd(i)));
+  return r;
+}
 
-  C f[9];
-  gather<T, C>(p, fin, xc, yc, f);
-  const C rho = f[0] + f[1] + f[2] + f[3] + f[4] + f[5] + f[6] + f[7] + f[8];
-  const C mx = f[1] - f[3] + f[5] - f[6] - f[7] + f[8];
-  const C my = f[2] - f[4] + f[5] + f[6] - f[7] - f[8];
-  const C pxx = f[1] + f[3] + f[5] + f[6] + f[7] + f[8];
-  const C pyy = f[2] + f[4] + f[5] + f[6] + f[7] + f[8];
-  const C pxy = f[5] - f[6] + f[7] - f[8];
+// Everything after streaming and the density gradient: moments, source and
+// physical flux, equilibrium/BGK/forcing, stores, displacement, receivers.
+// MODE 0: full step.  MODE 1: fields of the current state (no state change).
+template <class T, class C, class U, bool LAM, int MODE>
+__device__ __forceinline__ void finish_cell(const StepParams &p, const C *f, C gx, C gy, C Fx,
+                                            C Fy, int x, int y, int xc, int yc, bool active) {
+  // moments (Eq. 12 applied to f), summed pairwise over opposite links
+  const C s13 = f[1] + f[3], d13 = f[1] - f[3];
+  const C s24 = f[2] + f[4], d24 = f[2] - f[4];
+  const C s57 = f[5] + f[7], d57 = f[5] - f[7];
+  const C s68 = f[6] + f[8], d68 = f[6] - f[8];
+  const C sd = s57 + s68;
+  const C rho = (f[0] + s13) + (s24 + sd);
+  const C mx = d13 + (d57 - d68);
+  const C my = d24 + (d57 + d68);
+  const C pxx = s13 + sd;
+  const C pyy = s24 + sd;
+  const C pxy = s57 - s68;
 
   C Gx = C(0), Gy = C(0);
   if (LAM) {
-    C gx, gy;
-    grad_rho<T, C>(p, fin, xc, yc, rho, gx, gy);
     // elastic force (mu - lambda)/rho0 grad rho = Lambda b^2 grad rho (Eq. 9)
     const C lb2 = mat_at<C>(p.lam, p.mat_per_cell, xc, yc, p.pitch) * C(1.0 / 3.0);
     Gx = lb2 * gx;
     Gy = lb2 * gy;
   }
-  C Fx, Fy;
-  body_force<C>(p, xc, yc, Fx, Fy);
   const C A = sponge_A<C>(p, xc, yc);
   // physical flux with the half-force shift; the absorbing term -A j is
   // taken implicitly (Eq. 44 as a forcing)
@@ -368,7 +377,7 @@ __global__ void __launch_bounds__(256) step_kernel(const StepParams p) {
   if (MODE == 1) {
     if (!active) return;
     const long long o = (long long)(y - p.row0) * p.nx + x;
-    const long long c = (long long)y * p.pitch + x;
+    const int c = y * p.pitch + x;
     const U *u = (const U *)p.u;
     if (p.out[0]) p.out[0][o] = (double)u[c];
     if (p.out[1]) p.out[1][o] = (double)u[p.plane + c];
@@ -381,48 +390,50 @@ __global__ void __launch_bounds__(256) step_kernel(const StepParams p) {
     return;
   }
 
-  // Equilibrium (Eqs. 14-15) with b^2 = 1/3: f^eq_i = w_i (rho + 3 c_i.j
-  // + 9/2 H_i:P^n), H_i = c_i c_i - I/3, P^n = P - rho/3 I.
-  const C third = C(1.0 / 3.0);
-  const C a = pxx - rho * third;   // P^n_xx
-  const C d = pyy - rho * third;   // P^n_yy
-  const C hp0 = -(a + d) * third;                     // H_0 : P^n
-  const C hpx = C(2) * third * a - third * d;         // i = 1, 3
-  const C hpy = C(2) * third * d - third * a;         // i = 2, 4
-  const C hpdp = C(2) * third * (a + d) + C(2) * pxy; // i = 5, 7 (c_x c_y = +1)
-  const C hpdm = C(2) * third * (a + d) - C(2) * pxy; // i = 6, 8 (c_x c_y = -1)
+  // Equilibrium (Eqs. 14-15) with b^2 = 1/3, f^eq_i = w_i (rho + 3 c_i.j
+  // + 9/2 H_i:P^n), H_i = c_i c_i - I/3, P^n = P - rho/3 I, expanded in
+  // (rho, j, P):
+  //   f^eq_0   = 8/9 rho - 2/3 (Pxx + Pyy)
+  //   f^eq_1,3 = rho/18 + Pxx/3 - Pyy/6 +- jx/3      (2,4: x <-> y)
+  //   f^eq_5,7 = -rho/36 + (Pxx + Pyy)/12 + Pxy/4 +- (jx + jy)/12
+  //   f^eq_8,6 = -rho/36 + (Pxx + Pyy)/12 - Pxy/4 +- (jx - jy)/12
+  // Forcing S_i = 3 w_i c_i.S (Eq. 11): S/3 on axis links, S/12 on diagonals.
+  // Collision (Eq. 18): f* = (1 - w) f + w f^eq + (1 - 1/(2 tau)) S_i; for
+  // tau = 1 the first term is exactly zero and f* = f^eq + forcing.
   const C om = par<C>(p.omega, p.omega_f), fc = par<C>(p.fcoef, p.fcoef_f);
   const C k1 = C(1) - om;
-  // forcing S_i = 3 w_i c_i.S (Eq. 11); collision f* = (1-w) f + w f^eq + fc S_i
+  const C third = C(1.0 / 3.0), twelfth = C(1.0 / 12.0);
+  const C ps = pxx + pyy;
+  const C eqx = C(1.0 / 18.0) * rho + third * pxx - C(1.0 / 6.0) * pyy;
+  const C eqy = C(1.0 / 18.0) * rho + third * pyy - C(1.0 / 6.0) * pxx;
+  const C eqd = twelfth * ps - C(1.0 / 36.0) * rho;
+  const C eqdp = eqd + C(0.25) * pxy, eqdm = eqd - C(0.25) * pxy;
+  const C jx3 = third * jx, jy3 = third * jy;
+  const C jp = twelfth * (jx + jy), jm = twelfth * (jx - jy);
+  const C fsx = fc * third * Sx, fsy = fc * third * Sy;
+  const C fsp = fc * twelfth * (Sx + Sy), fsm = fc * twelfth * (Sx - Sy);
   C fs[9];
-  {
-    const C w0 = C(4.0 / 9.0), w1 = C(1.0 / 9.0), w2 = C(1.0 / 36.0);
-    const C r45 = C(4.5);
-    fs[0] = k1 * f[0] + om * w0 * (rho + r45 * hp0);
-    const C ex1 = w1 * (rho + r45 * hpx), ey1 = w1 * (rho + r45 * hpy);
-    const C jx3 = C(3) * jx, jy3 = C(3) * jy, sx3 = C(3) * Sx, sy3 = C(3) * Sy;
-    fs[1] = k1 * f[1] + om * (ex1 + w1 * jx3) + fc * w1 * sx3;
-    fs[3] = k1 * f[3] + om * (ex1 - w1 * jx3) - fc * w1 * sx3;
-    fs[2] = k1 * f[2] + om * (ey1 + w1 * jy3) + fc * w1 * sy3;
-    fs[4] = k1 * f[4] + om * (ey1 - w1 * jy3) - fc * w1 * sy3;
-    const C edp = w2 * (rho + r45 * hpdp), edm = w2 * (rho + r45 * hpdm);
-    const C jp = jx3 + jy3, jm = jx3 - jy3, sp = sx3 + sy3, sm = sx3 - sy3;
-    fs[5] = k1 * f[5] + om * (edp + w2 * jp) + fc * w2 * sp;   // ( 1,  1)
-    fs[7] = k1 * f[7] + om * (edp - w2 * jp) - fc * w2 * sp;   // (-1, -1)
-    fs[8] = k1 * f[8] + om * (edm + w2 * jm) + fc * w2 * sm;   // ( 1, -1)
-    fs[6] = k1 * f[6] + om * (edm - w2 * jm) - fc * w2 * sm;   // (-1,  1)
-  }
+  fs[0] = k1 * f[0] + om * (C(8.0 / 9.0) * rho - C(2.0 / 3.0) * ps);
+  fs[1] = k1 * f[1] + om * (eqx + jx3) + fsx;
+  fs[3] = k1 * f[3] + om * (eqx - jx3) - fsx;
+  fs[2] = k1 * f[2] + om * (eqy + jy3) + fsy;
+  fs[4] = k1 * f[4] + om * (eqy - jy3) - fsy;
+  fs[5] = k1 * f[5] + om * (eqdp + jp) + fsp;   // ( 1,  1)
+  fs[7] = k1 * f[7] + om * (eqdp - jp) - fsp;   // (-1, -1)
+  fs[8] = k1 * f[8] + om * (eqdm + jm) + fsm;   // ( 1, -1)
+  fs[6] = k1 * f[6] + om * (eqdm - jm) - fsm;   // (-1,  1)
   if (!active) return;
-  const long long c = (long long)y * p.pitch + x;
-  T *fout = (T *)p.fout;
+  const int c = y * p.pitch + x;
+  T *fout = (T *)p.fout + c;
 #pragma unroll
-  for (int i = 0; i < 9; ++i) st<T, C>(fout + i * p.plane + c, fs[i]);
+  for (int i = 0; i < 9; ++i) st<T, C>(fout + i * p.plane, fs[i]);
   U *u = (U *)p.u;
   const U vx = U(jx * irho), vy = U(jy * irho);
   const U ux = u[c] + vx, uy = u[p.plane + c] + vy;
   u[c] = ux;
   u[p.plane + c] = uy;
-  if (!(isfinite(rho) && isfinite(jx) && isfinite(jy))) atomicOr(p.err, 1);
+  // non-finite guard: x * 0 == 0 fails exactly for NaN and +-Inf
+  if (!((rho + jx + jy) * C(0) == C(0))) atomicOr(p.err, 1);
   if (p.trace_slot >= 0) {
     const int tile = (y / kRecTileY) * p.rec_tiles_x + x / kRecTileX;
     const int r0 = p.rec_tile_ptr[tile], r1 = p.rec_tile_ptr[tile + 1];
@@ -436,6 +447,64 @@ __global__ void __launch_bounds__(256) step_kernel(const StepParams p) {
       }
     }
   }
+}
+
+// Cells near a wall or a periodic seam: every pull goes through the general
+// path with the wall rules, and so do the neighbours' densities.  Kept out
+// of line so that the interior path carries none of this code.
+template <class T, class C, class U, bool LAM, int MODE>
+__device__ __noinline__ void boundary_cell(const StepParams &p, C Fx, C Fy, int x, int y, int xc,
+                                           int yc, bool active) {
+  const T *fin = (const T *)p.fin;
+  C f[9];
+#pragma unroll
+  for (int i = 0; i < 9; ++i) f[i] = pull_general<T, C>(p, fin, i, xc, yc);
+  C gx = C(0), gy = C(0);
+  if (LAM) {
+    const C rho = f[0] + f[1] + f[2] + f[3] + f[4] + f[5] + f[6] + f[7] + f[8];
+    grad_rho<T, C>(p, fin, xc, yc, rho, gx, gy);
+  }
+  finish_cell<T, C, U, LAM, MODE>(p, f, gx, gy, Fx, Fy, x, y, xc, yc, active);
+}
+
+// One thread per cell, blocks of 32 x 8 (a warp is 32 consecutive cells of a
+// row).  MODE 0: full step.  MODE 1: fields of the current state, rows
+// [row0, row0 + nrows).
+template <class T, class C, class U, bool LAM, int MODE>
+__global__ void __launch_bounds__(256, 4) step_kernel(const StepParams p) {
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  const int y = blockIdx.y * blockDim.y + threadIdx.y + (MODE == 1 ? p.row0 : 0);
+  const int yend = MODE == 1 ? p.row0 + p.nrows : p.ny;
+  // Whole warps stay alive for the warp-level source culling; cells outside
+  // the grid are clamped and write nothing.
+  const bool active = x < p.nx && y < yend;
+  const int xc = x < p.nx ? x : p.nx - 1;
+  const int yc = y < yend ? y : yend - 1;
+
+  C Fx, Fy;
+  body_force<C>(p, xc, yc, Fx, Fy);  // all lanes of the warp take part
+
+  // interior: all upstream cells (and, with the density gradient, those of
+  // the four neighbours) lie inside the grid
+  const int m = LAM ? 2 : 1;
+  if (!(xc >= m && xc < p.nx - m && yc >= m && yc < p.ny - m)) {
+    boundary_cell<T, C, U, LAM, MODE>(p, Fx, Fy, x, y, xc, yc, active);
+    return;
+  }
+  const T *fin = (const T *)p.fin;
+  C f[9];
+  {
+    const T *b = fin + (yc * p.pitch + xc);
+#pragma unroll
+    for (int i = 0; i < 9; ++i) f[i] = ld<T, C>(b + (i * p.plane - cyd(i) * p.pitch - cxd(i)));
+  }
+  C gx = C(0), gy = C(0);
+  if (LAM) {
+    // centred difference of the streamed density (Eq. 10)
+    gx = C(0.5) * (rho_direct<T, C>(p, fin, xc + 1, yc) - rho_direct<T, C>(p, fin, xc - 1, yc));
+    gy = C(0.5) * (rho_direct<T, C>(p, fin, xc, yc + 1) - rho_direct<T, C>(p, fin, xc, yc - 1));
+  }
+  finish_cell<T, C, U, LAM, MODE>(p, f, gx, gy, Fx, Fy, x, y, xc, yc, active);
 }
 
 // Launch entry points, one translation unit per storage type.

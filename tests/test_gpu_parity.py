@@ -317,9 +317,9 @@ def test_moment_sums_match_state():
     m = sim.moment_sums()
     cx = np.array([0, 1, 0, -1, 0, 1, -1, -1, 1])
     cy = np.array([0, 0, 1, 0, -1, 1, 1, -1, -1])
-    want = [fs0.sum(), np.einsum("iyx,i", fs0, cx), np.einsum("iyx,i", fs0, cy),
-            np.einsum("iyx,i", fs0, cx * cx), np.einsum("iyx,i", fs0, cx * cy),
-            np.einsum("iyx,i", fs0, cy * cy), (u0 ** 2).sum()]
+    want = [fs0.sum(), np.einsum("iyx,i->", fs0, cx), np.einsum("iyx,i->", fs0, cy),
+            np.einsum("iyx,i->", fs0, cx * cx), np.einsum("iyx,i->", fs0, cx * cy),
+            np.einsum("iyx,i->", fs0, cy * cy), (u0 ** 2).sum()]
     np.testing.assert_allclose(m, want, rtol=1e-12, atol=1e-14)
     assert np.array_equal(m, sim.moment_sums())
 
