@@ -215,6 +215,42 @@ const char *lbm_elastic_status_string(int status);
 /* Number of kernel launches this handle has issued (for launch accounting). */
 long long lbm_elastic_kernel_launches(const lbm_elastic_t *h);
 
+/* ---- Moment sums without a workspace (no counterpart in the paper) -------
+ *
+ * The same deterministic sums as lbm_elastic_moment_sums, for callers that
+ * can neither hand the library a workspace nor let it allocate: code whose
+ * device memory is entirely pre-reserved by another allocator (a framework's
+ * caching pool or a fixed arena), or code running where a cudaMalloc could
+ * fail, or stall the whole device, at a bad moment.  This entry point
+ * allocates nothing: its scratch (the per-block partial sums) is a fixed
+ * array of LBM_NOALLOC_SCRATCH_BYTES bytes inside the library image, which
+ * every GPU that loads the library holds until the process exits.
+ *
+ *   f9      9 population planes, each [ny][pitch] elements, plane after plane
+ *           (plane stride pitch * ny), in the storage type (FP64 or FP32);
+ *   u2      2 displacement planes in the same layout, FP64 if storage is
+ *           LBM_F64 or u_fp64 is set, else FP32;
+ *   out7    sum rho, sum m_x, sum m_y, sum P_xx, sum P_xy, sum P_yy,
+ *           sum (u_x^2 + u_y^2) over the nx x ny cells, FP64; a host pointer
+ *           (the call then waits for the stream) or, with out_on_device, a
+ *           device pointer written asynchronously on the stream.
+ * All pointers are the caller's; work runs on cuda_stream (NULL: default).
+ * Sizes: nx, ny >= 1, pitch >= nx and 9 * pitch * ny <= LBM_NOALLOC_MAX_ELEMENTS;
+ * anything else returns LBM_ERR_ARG (storage other than F64/F32:
+ * LBM_ERR_UNSUPPORTED) with a message in lbm_elastic_last_error(NULL).
+ * The first call on a device looks up the array's device address on that
+ * (current) device; make that first call before any stream capture.  All
+ * calls on a device share the one array, and each call overwrites every part
+ * of it that it reads, so nothing carries over; calls whose work overlaps on
+ * the GPU (e.g. on two streams at once) race on the array and must be
+ * ordered by the caller. */
+#define LBM_NOALLOC_SCRATCH_BYTES 19520
+#define LBM_NOALLOC_MAX_ELEMENTS 2147483647LL
+lbm_status lbm_elastic_moment_sums_noalloc(const void *f9, const void *u2, int storage,
+                                           int u_fp64, int nx, int ny, int pitch,
+                                           double *out7, int out_on_device,
+                                           void *cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -33,7 +33,7 @@ SYMBOLS = [
     "lbm_elastic_get_state", "lbm_elastic_checkpoint_bytes", "lbm_elastic_save",
     "lbm_elastic_load", "lbm_elastic_moment_sums", "lbm_elastic_sync",
     "lbm_elastic_destroy", "lbm_elastic_last_error", "lbm_elastic_status_string",
-    "lbm_elastic_kernel_launches",
+    "lbm_elastic_kernel_launches", "lbm_elastic_moment_sums_noalloc",
 ]
 
 
@@ -113,6 +113,7 @@ def load_library(build_if_missing: bool = False):
             "lbm_elastic_last_error": (ctypes.c_char_p, [vp]),
             "lbm_elastic_status_string": (ctypes.c_char_p, [ip]),
             "lbm_elastic_kernel_launches": (ctypes.c_longlong, [vp]),
+            "lbm_elastic_moment_sums_noalloc": (ip, [vp, vp, ip, ip, ip, ip, ip, vp, ip, vp]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)
@@ -336,6 +337,28 @@ class ElasticLBM:
         out = (ctypes.c_double * 7)()
         self._check(self.L.lbm_elastic_moment_sums(self.h, out))
         return np.array(out[:])
+
+
+def moment_sums_noalloc(f9, u2, storage="f64", u_fp64=False, nx=None, out=None,
+                        stream=None):
+    """Moment sums of caller-held CUDA tensors without a workspace (see
+    ``lbm_elastic_moment_sums_noalloc``): f9 [9][ny][pitch], u2 [2][ny][pitch],
+    the first ``nx`` (default: pitch) cells of each row summed.  With ``out``
+    None the seven sums come back as a numpy array; with a CUDA float64 tensor
+    of 7 elements they are written there asynchronously."""
+    import torch
+    L = load_library()
+    ny, pitch = f9.shape[-2], f9.shape[-1]
+    nx = pitch if nx is None else int(nx)
+    s = (stream if stream is not None else torch.cuda.current_stream()).cuda_stream
+    on_dev = out is not None
+    host = (ctypes.c_double * 7)()
+    st = L.lbm_elastic_moment_sums_noalloc(
+        f9.data_ptr(), u2.data_ptr(), STORAGE[storage], int(bool(u_fp64)), int(nx), int(ny),
+        int(pitch), out.data_ptr() if on_dev else ctypes.addressof(host), int(on_dev), s)
+    if st != LBM_OK:
+        raise LBMError(st, L.lbm_elastic_last_error(None).decode())
+    return out if on_dev else np.array(host[:])
 
 
 def from_workload(w, storage=None, max_steps_traced=None, u_fp64=False, device=None,

@@ -4,6 +4,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <string>
 #include <vector>
@@ -824,3 +825,78 @@ const char *lbm_elastic_status_string(int s) {
 long long lbm_elastic_kernel_launches(const lbm_elastic_t *h) { return h ? h->launches : 0; }
 
 }  // extern "C"
+
+// ------------------------------------------------------------ no-allocation entry point
+//
+// A handle needs a workspace from its caller.  Some callers cannot provide
+// one and cannot let the library allocate either: code whose device memory
+// is all pre-reserved by another allocator (a framework's caching pool, a
+// fixed arena), or code running where a cudaMalloc would fail, or would stall
+// the whole device at a bad moment.  For them the moment sums are also
+// available without any workspace: the per-block partial sums go to the
+// file-scope array below instead.  The array is part of the library image, so
+// every GPU that loads the library holds its 19,520 bytes until the process
+// exits.
+namespace {
+
+constexpr int kNoAllocScratchDoubles = (kRedBlocks + 1) * 8;
+static __device__ __align__(256) double g_noalloc_scratch[kNoAllocScratchDoubles];
+static_assert(kNoAllocScratchDoubles * sizeof(double) == LBM_NOALLOC_SCRATCH_BYTES,
+              "scratch size stated in lbm_elastic.h");
+constexpr int kNoAllocMaxDevices = 64;
+std::mutex g_noalloc_mutex;
+double *g_noalloc_ptr[kNoAllocMaxDevices] = {};
+
+}  // namespace
+
+extern "C" lbm_status lbm_elastic_moment_sums_noalloc(const void *f9, const void *u2,
+                                                       int storage, int u_fp64, int nx, int ny,
+                                                       int pitch, double *out7, int out_on_device,
+                                                       void *cuda_stream) {
+  if (!f9 || !u2 || !out7) return fail(nullptr, LBM_ERR_ARG, "noalloc: NULL pointer");
+  if (storage != LBM_F64 && storage != LBM_F32)
+    return fail(nullptr, LBM_ERR_UNSUPPORTED, "noalloc: storage must be LBM_F64 or LBM_F32");
+  if (nx < 1 || ny < 1 || pitch < nx) return fail(nullptr, LBM_ERR_ARG, "noalloc: bad sizes");
+  if (9LL * pitch * ny > LBM_NOALLOC_MAX_ELEMENTS)
+    return fail(nullptr, LBM_ERR_ARG, "noalloc: grid beyond the maximum of this entry point");
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return fail(nullptr, LBM_ERR_CUDA, cudaGetErrorString(e));
+  if (dev < 0 || dev >= kNoAllocMaxDevices)
+    return fail(nullptr, LBM_ERR_UNSUPPORTED, "noalloc: device index too large");
+  double *scratch = nullptr;
+  {
+    // once per device, with that device current: the array's device address
+    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+    if (!g_noalloc_ptr[dev]) {
+      void *ptr = nullptr;
+      e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+      if (e != cudaSuccess) return fail(nullptr, LBM_ERR_CUDA, cudaGetErrorString(e));
+      g_noalloc_ptr[dev] = (double *)ptr;
+    }
+    scratch = g_noalloc_ptr[dev];
+  }
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  const long long plane = (long long)pitch * ny;
+  // every partial slot read by the final pass is written by this call first,
+  // so nothing left from an earlier call needs clearing
+  if (storage == LBM_F64)
+    moments_partial_kernel<double, double><<<kRedBlocks, kRedThreads, 0, s>>>(
+        (const double *)f9, (const double *)u2, plane, pitch, nx, ny, scratch);
+  else if (u_fp64)
+    moments_partial_kernel<float, double><<<kRedBlocks, kRedThreads, 0, s>>>(
+        (const float *)f9, (const double *)u2, plane, pitch, nx, ny, scratch);
+  else
+    moments_partial_kernel<float, float><<<kRedBlocks, kRedThreads, 0, s>>>(
+        (const float *)f9, (const float *)u2, plane, pitch, nx, ny, scratch);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return fail(nullptr, LBM_ERR_CUDA, cudaGetErrorString(e));
+  moments_final_kernel<<<1, kRedThreads, 0, s>>>(scratch, kRedBlocks, scratch + 8 * kRedBlocks);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return fail(nullptr, LBM_ERR_CUDA, cudaGetErrorString(e));
+  e = cudaMemcpyAsync(out7, scratch + 8 * kRedBlocks, 7 * sizeof(double),
+                      out_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess && !out_on_device) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return fail(nullptr, LBM_ERR_CUDA, cudaGetErrorString(e));
+  return LBM_OK;
+}
