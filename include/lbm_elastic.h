@@ -100,6 +100,10 @@ typedef struct {
   int max_sources;       /* capacity reserved in the workspace (>= 0)         */
   int max_receivers;     /* capacity reserved in the workspace (>= 0)         */
   int max_steps_traced;  /* receiver samples kept: steps [0, max) after reset */
+  int kernel_variant;    /* step kernel: 0 = default (the faster one measured:
+                          * currently 1), 1 = one thread per cell with direct
+                          * loads, 2 = TMA-staged tiles (FP32 storage only;
+                          * LBM_ERR_UNSUPPORTED otherwise) */
 } lbm_elastic_config;
 
 /* One Ricker x Gaussian body-force source (Sec. 5).  Position in cells (may be

@@ -23,6 +23,7 @@ STATUS = {0: "LBM_OK", 1: "LBM_WARN_VS_NOT_B", -1: "LBM_ERR_ARG", -2: "LBM_ERR_U
           -6: "LBM_ERR_TIMEOUT", -7: "LBM_ERR_CAPACITY"}
 STORAGE = {"f64": 0, "f32": 1, "f16": 2, "bf16": 3}
 BC = {"periodic": 0, "free": 1, "rigid": 2}
+KERNEL = {"auto": 0, "simple": 1, "tma": 2}
 
 #: the exported symbols, as declared in include/lbm_elastic.h
 SYMBOLS = [
@@ -58,7 +59,7 @@ class Config(ctypes.Structure):
         ("sponge_amax", ctypes.c_double), ("free_surface_order", ctypes.c_int),
         ("material_per_cell", ctypes.c_int),
         ("max_sources", ctypes.c_int), ("max_receivers", ctypes.c_int),
-        ("max_steps_traced", ctypes.c_int),
+        ("max_steps_traced", ctypes.c_int), ("kernel_variant", ctypes.c_int),
     ]
 
 
@@ -125,11 +126,12 @@ def load_library(build_if_missing: bool = False):
 
 def make_config(nx, ny, storage="f32", tau=1.0, bc=("periodic",) * 4, sponge=(0, 0, 0, 0),
                 sponge_amax=0.0, material_per_cell=False, max_sources=16, max_receivers=256,
-                max_steps_traced=0, u_fp64=False, fs_order=0) -> Config:
+                max_steps_traced=0, u_fp64=False, fs_order=0, kernel="auto") -> Config:
     return Config(int(nx), int(ny), STORAGE[storage], int(bool(u_fp64)), float(tau),
                   BC[bc[0]], BC[bc[1]], BC[bc[2]], BC[bc[3]], *[int(s) for s in sponge],
                   float(sponge_amax), int(fs_order), int(bool(material_per_cell)),
-                  int(max_sources), int(max_receivers), int(max_steps_traced))
+                  int(max_sources), int(max_receivers), int(max_steps_traced),
+                  KERNEL[kernel])
 
 
 def _ptr(t) -> Optional[int]:
@@ -151,14 +153,15 @@ class ElasticLBM:
     def __init__(self, nx, ny, storage="f32", tau=1.0, bc=("periodic",) * 4,
                  sponge=(0, 0, 0, 0), sponge_amax=0.0, material_per_cell=False,
                  max_sources=16, max_receivers=256, max_steps_traced=0, u_fp64=False,
-                 fs_order=0, device=None, stream=None):
+                 fs_order=0, kernel="auto", device=None, stream=None):
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("ElasticLBM needs a CUDA device (no CPU fallback)")
         self._torch = torch
         self.L = load_library()
         self.cfg = make_config(nx, ny, storage, tau, bc, sponge, sponge_amax, material_per_cell,
-                               max_sources, max_receivers, max_steps_traced, u_fp64, fs_order)
+                               max_sources, max_receivers, max_steps_traced, u_fp64, fs_order,
+                               kernel)
         self.nx, self.ny = int(nx), int(ny)
         self.device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
         nbytes = self.L.lbm_elastic_workspace_bytes(ctypes.byref(self.cfg))
@@ -362,14 +365,15 @@ def moment_sums_noalloc(f9, u2, storage="f64", u_fp64=False, nx=None, out=None,
 
 
 def from_workload(w, storage=None, max_steps_traced=None, u_fp64=False, device=None,
-                  stream=None) -> ElasticLBM:
+                  stream=None, kernel="auto") -> ElasticLBM:
     """An ElasticLBM set up from a :class:`workloads.Workload`."""
     sim = ElasticLBM(w.nx, w.ny, storage=storage or w.storage, tau=w.tau, bc=tuple(w.bc),
                      sponge=tuple(w.sponge), sponge_amax=w.sponge_amax,
                      material_per_cell=w.per_cell, max_sources=max(1, len(w.sources)),
                      max_receivers=max(1, len(w.receivers)),
                      max_steps_traced=w.nsteps if max_steps_traced is None else max_steps_traced,
-                     u_fp64=u_fp64, fs_order=w.fs_order, device=device, stream=stream)
+                     u_fp64=u_fp64, fs_order=w.fs_order, kernel=kernel, device=device,
+                     stream=stream)
     if w.rho0 is not None:
         sim.set_material(w.rho0, w.lam, w.mu)
     if len(w.sources):

@@ -11,6 +11,7 @@
 
 #include "lbm_elastic.h"
 #include "lbm_kernels.cuh"
+#include "step_tma.cuh"
 
 using namespace lbm;
 
@@ -68,6 +69,7 @@ bool config_ok(const lbm_elastic_config *c, std::string *why) {
     return bad("capacities must be >= 0");
   if (c->storage == LBM_F16 || c->storage == LBM_BF16)
     return bad("FP16/BF16 storage is not built in this library version");
+  if (c->kernel_variant < 0 || c->kernel_variant > 2) return bad("unknown kernel_variant");
   return true;
 }
 
@@ -234,6 +236,9 @@ __global__ void __launch_bounds__(kRedThreads) moments_final_kernel(const double
 // ------------------------------------------------------------ the handle
 
 struct lbm_elastic {
+  TmaMaps maps;                // tensor maps of the TMA-staged kernel
+  bool use_tma = false;
+  int nsm = 0;                 // multiprocessors of the device
   lbm_elastic_config cfg;
   Layout L;
   char *ws = nullptr;
@@ -290,6 +295,8 @@ lbm_status sync_flags(lbm_elastic_t *h) {
   LBM_CUDA(h, cudaMemcpyAsync(flags, at<int>(h, h->L.flags), sizeof(flags),
                               cudaMemcpyDeviceToHost, h->stream));
   LBM_CUDA(h, cudaStreamSynchronize(h->stream));
+  if (flags[0] & 2)
+    return fail(h, LBM_ERR_TIMEOUT, "a bounded wait in the step kernel gave up");
   if (flags[0] & 1)
     return fail(h, LBM_ERR_NONFINITE, "a step met a non-finite value (unstable run)");
   return LBM_OK;
@@ -434,6 +441,91 @@ lbm_status clear_state(lbm_elastic_t *h) {
   return LBM_OK;
 }
 
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *,
+                                  const cuuint64_t *, const cuuint64_t *, const cuuint32_t *,
+                                  const cuuint32_t *, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                  CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+// cuTensorMapEncodeTiled from the driver, looked up once through the runtime.
+EncodeTiledFn encode_tiled() {
+  static EncodeTiledFn fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void *ptr = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &ptr, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (EncodeTiledFn)ptr;
+  });
+  return fn;
+}
+
+// Builds the tensor maps of the TMA-staged kernel; false if TMA cannot be used.
+bool setup_tma(lbm_elastic_t *h, std::string *why) {
+  const lbm_elastic_config &c = h->cfg;
+  const Layout &L = h->L;
+  if (c.storage != LBM_F32) {
+    *why = "the TMA-staged kernel covers FP32 storage only";
+    return false;
+  }
+  EncodeTiledFn enc = encode_tiled();
+  if (!enc) {
+    *why = "cuTensorMapEncodeTiled is not available";
+    return false;
+  }
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&h->nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+    *why = "cannot query the device";
+    return false;
+  }
+  int major = 0;
+  cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev);
+  if (major < 9) {
+    *why = "TMA needs compute capability 9.0 or newer";
+    return false;
+  }
+  const int es = (int)L.tsize;
+  const int halo = tma_halo_x(es);
+  for (int b = 0; b < 2; ++b)
+    for (int hh = 1; hh <= 2; ++hh) {
+      const cuuint64_t dims[3] = {(cuuint64_t)c.nx, (cuuint64_t)c.ny, 9};
+      const cuuint64_t strides[2] = {(cuuint64_t)L.pitch * es, (cuuint64_t)L.plane * es};
+      const cuuint32_t box[3] = {(cuuint32_t)(kTileW + 2 * halo), (cuuint32_t)(kTileH + 2 * hh), 9};
+      const cuuint32_t estr[3] = {1, 1, 1};
+      CUresult r = enc(&h->maps.f[b][hh - 1], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, h->ws + L.f[b],
+                       dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                       CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                       CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+      if (r != CUDA_SUCCESS) {
+        *why = "cuTensorMapEncodeTiled failed for the populations";
+        return false;
+      }
+    }
+  {
+    const int us = (int)L.usize;
+    const cuuint64_t dims[3] = {(cuuint64_t)c.nx, (cuuint64_t)c.ny, 2};
+    const cuuint64_t strides[2] = {(cuuint64_t)L.pitch * us, (cuuint64_t)L.plane * us};
+    const cuuint32_t box[3] = {(cuuint32_t)kTileW, (cuuint32_t)kTileH, 2};
+    const cuuint32_t estr[3] = {1, 1, 1};
+    CUresult r = enc(&h->maps.u, us == 8 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64
+                                         : CU_TENSOR_MAP_DATA_TYPE_FLOAT32,
+                     3, h->ws + L.u, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                     CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) {
+      *why = "cuTensorMapEncodeTiled failed for the displacement";
+      return false;
+    }
+  }
+  if (tma_prepare(c.storage, L.usize == 8) != cudaSuccess) {
+    *why = "cannot reserve the kernel's shared memory";
+    return false;
+  }
+  return true;
+}
+
 }  // namespace
 
 // ------------------------------------------------------------ C ABI
@@ -485,6 +577,15 @@ lbm_status lbm_elastic_create(const lbm_elastic_config *cfg, void *d_workspace,
                                     h->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
     if (e != cudaSuccess) s = cuda_fail(h, e, "create");
+  }
+  // The TMA-staged kernel is built on request only: on the half-space
+  // workload it measures slower than the direct-load kernel.
+  if (s == LBM_OK && cfg->kernel_variant == 2) {
+    std::string why;
+    h->use_tma = setup_tma(h, &why);
+    cudaGetLastError();  // a failed optional query leaves no sticky state behind
+    if (!h->use_tma && cfg->kernel_variant == 2)
+      s = fail(h, LBM_ERR_UNSUPPORTED, "TMA-staged kernel unavailable: " + why);
   }
   if (s != LBM_OK) {
     g_create_error = h->err;
@@ -626,7 +727,15 @@ lbm_status lbm_elastic_step(lbm_elastic_t *h, int nsteps) {
   for (int s = 0; s < nsteps; ++s) {
     StepParams p = base_params(h);
     if (h->nrec > 0 && h->traced < h->cfg.max_steps_traced) p.trace_slot = h->traced;
-    lbm_status st = launch_step(h, p, 0, h->cfg.ny);
+    lbm_status st;
+    if (h->use_tma) {
+      const cudaError_t e = launch_step_tma(p, h->maps, h->cur, h->cfg.storage,
+                                            h->L.usize == 8, h->lambda_nonzero, h->nsm, h->stream);
+      st = e != cudaSuccess ? cuda_fail(h, e, "TMA step kernel launch")
+                            : check_launch(h, "TMA step kernel launch");
+    } else {
+      st = launch_step(h, p, 0, h->cfg.ny);
+    }
     if (st) return st;
     if (p.trace_slot >= 0) h->traced++;
     h->cur ^= 1;

@@ -338,25 +338,105 @@ __device__ __forceinline__ C rho_direct(const StepParams &p, const T *f, int x, 
   return r;
 }
 
-// Everything after streaming and the density gradient: moments, source and
-// physical flux, equilibrium/BGK/forcing, stores, displacement, receivers.
-// MODE 0: full step.  MODE 1: fields of the current state (no state change).
-template <class T, class C, class U, bool LAM, int MODE>
-__device__ __forceinline__ void finish_cell(const StepParams &p, const C *f, C gx, C gy, C Fx,
-                                            C Fy, int x, int y, int xc, int yc, bool active) {
-  // moments (Eq. 12 applied to f), summed pairwise over opposite links
+// Raw moments of the streamed populations, summed pairwise over opposite
+// links: rho, m, P (Eq. 12 applied to f) and the three higher moments
+// Q_xxy = sum f c_x^2 c_y, Q_xyy = sum f c_x c_y^2, R = sum f c_x^2 c_y^2.
+template <class C>
+struct Moments {
+  C rho, mx, my, pxx, pxy, pyy, qxxy, qxyy, r;
+};
+
+template <class C>
+__device__ __forceinline__ Moments<C> cell_moments(const C *f) {
   const C s13 = f[1] + f[3], d13 = f[1] - f[3];
   const C s24 = f[2] + f[4], d24 = f[2] - f[4];
   const C s57 = f[5] + f[7], d57 = f[5] - f[7];
   const C s68 = f[6] + f[8], d68 = f[6] - f[8];
-  const C sd = s57 + s68;
-  const C rho = (f[0] + s13) + (s24 + sd);
-  const C mx = d13 + (d57 - d68);
-  const C my = d24 + (d57 + d68);
-  const C pxx = s13 + sd;
-  const C pyy = s24 + sd;
-  const C pxy = s57 - s68;
+  Moments<C> M;
+  M.r = s57 + s68;
+  M.pxy = s57 - s68;
+  M.qxxy = d57 + d68;
+  M.qxyy = d57 - d68;
+  M.pxx = s13 + M.r;
+  M.pyy = s24 + M.r;
+  M.rho = (f[0] + s13) + (s24 + M.r);
+  M.mx = d13 + M.qxyy;
+  M.my = d24 + M.qxxy;
+  return M;
+}
 
+// Physical flux with the half-force shift and the source; the absorbing term
+// -A j is taken implicitly (Eq. 44 treated as a forcing, Eqs. 9, 12, 22).
+template <class C>
+__device__ __forceinline__ void flux_and_source(C mx, C my, C Gx, C Gy, C Fx, C Fy, C A, C &jx,
+                                                C &jy, C &Sx, C &Sy) {
+  const C inv = C(1) / (C(1) + C(0.5) * A);
+  jx = (mx + C(0.5) * (Gx + Fx)) * inv;
+  jy = (my + C(0.5) * (Gy + Fy)) * inv;
+  Sx = Gx + Fx - A * jx;
+  Sy = Gy + Fy - A * jy;
+}
+
+// BGK collision with forcing (Eqs. 11, 14, 15, 18), carried out on the raw
+// moments.  The map f -> (rho, m, P, Q_xxy, Q_xyy, R) is one to one on D2Q9,
+// so f* = f - w (f - f^eq) + (1 - 1/(2 tau)) S_i is equivalent to:
+//   rho* = rho, P* = P                    (conserved: Eqs. 12, 22)
+//   m*   = m + S                          (Guo forcing with j = m + S/2)
+//   Q*_xxy = (1 - w) Q_xxy + b^2 (w j_y + (1 - 1/(2 tau)) S_y)
+//   Q*_xyy = (1 - w) Q_xyy + b^2 (w j_x + (1 - 1/(2 tau)) S_x)
+//   R*   = (1 - w) R + w (b^2 (P_xx + P_yy) - b^4 rho)
+// using the moments of f^eq (Q^eq_xxy = b^2 j_y, R^eq = b^2 tr P - b^4 rho) and
+// of S_i (sum S_i c_x^2 c_y = b^2 S_y).  The populations follow from the
+// inverse map, whose coefficients (1/2, 1/4) are exact in binary, so the
+// conserved moments pass through unchanged apart from the final rounding.
+template <class C>
+__device__ __forceinline__ void collide_cell(const Moments<C> &M, C jx, C jy, C Sx, C Sy, C om,
+                                             C fc, C *fs) {
+  const C k1 = C(1) - om, b2 = C(1.0 / 3.0);
+  const C mxs = M.mx + Sx, mys = M.my + Sy;
+  const C qxxy = k1 * M.qxxy + b2 * (om * jy + fc * Sy);
+  const C qxyy = k1 * M.qxyy + b2 * (om * jx + fc * Sx);
+  const C r = k1 * M.r + om * (b2 * (M.pxx + M.pyy) - C(1.0 / 9.0) * M.rho);
+  const C rp = r + M.pxy, rm = r - M.pxy, qp = qxxy + qxyy, qm = qxxy - qxyy;
+  fs[5] = C(0.25) * (rp + qp);   // ( 1,  1)
+  fs[7] = C(0.25) * (rp - qp);   // (-1, -1)
+  fs[6] = C(0.25) * (rm + qm);   // (-1,  1)
+  fs[8] = C(0.25) * (rm - qm);   // ( 1, -1)
+  const C ax = M.pxx - r, ay = M.pyy - r, bx = mxs - qxyy, by = mys - qxxy;
+  fs[1] = C(0.5) * (ax + bx);
+  fs[3] = C(0.5) * (ax - bx);
+  fs[2] = C(0.5) * (ay + by);
+  fs[4] = C(0.5) * (ay - by);
+  fs[0] = (M.rho - (M.pxx + M.pyy)) + r;
+}
+
+// Writes (u^{n+1}, v^n) into the trace slot of the receiver at (x, y), if any.
+template <class U>
+__device__ __forceinline__ void record_receiver(const StepParams &p, int x, int y, U ux, U uy,
+                                                U vx, U vy) {
+  const int tile = (y / kRecTileY) * p.rec_tiles_x + x / kRecTileX;
+  const int r0 = p.rec_tile_ptr[tile], r1 = p.rec_tile_ptr[tile + 1];
+  for (int r = r0; r < r1; ++r) {
+    if (p.rec_xy[2 * r] == x && p.rec_xy[2 * r + 1] == y) {
+      double *t = p.traces + ((long long)p.trace_slot * p.nrec + p.rec_id[r]) * 4;
+      t[0] = (double)ux;
+      t[1] = (double)uy;
+      t[2] = (double)vx;
+      t[3] = (double)vy;
+    }
+  }
+}
+
+// Everything after streaming and the density gradient: moments, source and
+// physical flux, equilibrium/BGK/forcing, stores, displacement, receivers.
+// MODE 0: full step.  MODE 1: fields of the current state (no state change).
+// With UIN the current displacement comes in (ux0, uy0) instead of being read
+// from global memory.
+template <class T, class C, class U, bool LAM, int MODE, bool UIN = false>
+__device__ __forceinline__ void finish_cell(const StepParams &p, const C *f, C gx, C gy, C Fx,
+                                            C Fy, int x, int y, int xc, int yc, bool active,
+                                            U ux0 = U(0), U uy0 = U(0)) {
+  const Moments<C> M = cell_moments<C>(f);
   C Gx = C(0), Gy = C(0);
   if (LAM) {
     // elastic force (mu - lambda)/rho0 grad rho = Lambda b^2 grad rho (Eq. 9)
@@ -365,13 +445,8 @@ __device__ __forceinline__ void finish_cell(const StepParams &p, const C *f, C g
     Gy = lb2 * gy;
   }
   const C A = sponge_A<C>(p, xc, yc);
-  // physical flux with the half-force shift; the absorbing term -A j is
-  // taken implicitly (Eq. 44 as a forcing)
-  const C inv = C(1) / (C(1) + C(0.5) * A);
-  const C jx = (mx + C(0.5) * (Gx + Fx)) * inv;
-  const C jy = (my + C(0.5) * (Gy + Fy)) * inv;
-  const C Sx = Gx + Fx - A * jx;
-  const C Sy = Gy + Fy - A * jy;
+  C jx, jy, Sx, Sy;
+  flux_and_source<C>(M.mx, M.my, Gx, Gy, Fx, Fy, A, jx, jy, Sx, Sy);
   const C irho = mat_at<C>(p.irho, p.mat_per_cell, xc, yc, p.pitch);
 
   if (MODE == 1) {
@@ -383,45 +458,15 @@ __device__ __forceinline__ void finish_cell(const StepParams &p, const C *f, C g
     if (p.out[1]) p.out[1][o] = (double)u[p.plane + c];
     if (p.out[2]) p.out[2][o] = (double)(jx * irho);
     if (p.out[3]) p.out[3][o] = (double)(jy * irho);
-    if (p.out[4]) p.out[4][o] = (double)rho;
-    if (p.out[5]) p.out[5][o] = (double)pxx;
-    if (p.out[6]) p.out[6][o] = (double)pxy;
-    if (p.out[7]) p.out[7][o] = (double)pyy;
+    if (p.out[4]) p.out[4][o] = (double)M.rho;
+    if (p.out[5]) p.out[5][o] = (double)M.pxx;
+    if (p.out[6]) p.out[6][o] = (double)M.pxy;
+    if (p.out[7]) p.out[7][o] = (double)M.pyy;
     return;
   }
 
-  // Equilibrium (Eqs. 14-15) with b^2 = 1/3, f^eq_i = w_i (rho + 3 c_i.j
-  // + 9/2 H_i:P^n), H_i = c_i c_i - I/3, P^n = P - rho/3 I, expanded in
-  // (rho, j, P):
-  //   f^eq_0   = 8/9 rho - 2/3 (Pxx + Pyy)
-  //   f^eq_1,3 = rho/18 + Pxx/3 - Pyy/6 +- jx/3      (2,4: x <-> y)
-  //   f^eq_5,7 = -rho/36 + (Pxx + Pyy)/12 + Pxy/4 +- (jx + jy)/12
-  //   f^eq_8,6 = -rho/36 + (Pxx + Pyy)/12 - Pxy/4 +- (jx - jy)/12
-  // Forcing S_i = 3 w_i c_i.S (Eq. 11): S/3 on axis links, S/12 on diagonals.
-  // Collision (Eq. 18): f* = (1 - w) f + w f^eq + (1 - 1/(2 tau)) S_i; for
-  // tau = 1 the first term is exactly zero and f* = f^eq + forcing.
-  const C om = par<C>(p.omega, p.omega_f), fc = par<C>(p.fcoef, p.fcoef_f);
-  const C k1 = C(1) - om;
-  const C third = C(1.0 / 3.0), twelfth = C(1.0 / 12.0);
-  const C ps = pxx + pyy;
-  const C eqx = C(1.0 / 18.0) * rho + third * pxx - C(1.0 / 6.0) * pyy;
-  const C eqy = C(1.0 / 18.0) * rho + third * pyy - C(1.0 / 6.0) * pxx;
-  const C eqd = twelfth * ps - C(1.0 / 36.0) * rho;
-  const C eqdp = eqd + C(0.25) * pxy, eqdm = eqd - C(0.25) * pxy;
-  const C jx3 = third * jx, jy3 = third * jy;
-  const C jp = twelfth * (jx + jy), jm = twelfth * (jx - jy);
-  const C fsx = fc * third * Sx, fsy = fc * third * Sy;
-  const C fsp = fc * twelfth * (Sx + Sy), fsm = fc * twelfth * (Sx - Sy);
   C fs[9];
-  fs[0] = k1 * f[0] + om * (C(8.0 / 9.0) * rho - C(2.0 / 3.0) * ps);
-  fs[1] = k1 * f[1] + om * (eqx + jx3) + fsx;
-  fs[3] = k1 * f[3] + om * (eqx - jx3) - fsx;
-  fs[2] = k1 * f[2] + om * (eqy + jy3) + fsy;
-  fs[4] = k1 * f[4] + om * (eqy - jy3) - fsy;
-  fs[5] = k1 * f[5] + om * (eqdp + jp) + fsp;   // ( 1,  1)
-  fs[7] = k1 * f[7] + om * (eqdp - jp) - fsp;   // (-1, -1)
-  fs[8] = k1 * f[8] + om * (eqdm + jm) + fsm;   // ( 1, -1)
-  fs[6] = k1 * f[6] + om * (eqdm - jm) - fsm;   // (-1,  1)
+  collide_cell<C>(M, jx, jy, Sx, Sy, par<C>(p.omega, p.omega_f), par<C>(p.fcoef, p.fcoef_f), fs);
   if (!active) return;
   const int c = y * p.pitch + x;
   T *fout = (T *)p.fout + c;
@@ -429,24 +474,12 @@ __device__ __forceinline__ void finish_cell(const StepParams &p, const C *f, C g
   for (int i = 0; i < 9; ++i) st<T, C>(fout + i * p.plane, fs[i]);
   U *u = (U *)p.u;
   const U vx = U(jx * irho), vy = U(jy * irho);
-  const U ux = u[c] + vx, uy = u[p.plane + c] + vy;
+  const U ux = (UIN ? ux0 : u[c]) + vx, uy = (UIN ? uy0 : u[p.plane + c]) + vy;
   u[c] = ux;
   u[p.plane + c] = uy;
   // non-finite guard: x * 0 == 0 fails exactly for NaN and +-Inf
-  if (!((rho + jx + jy) * C(0) == C(0))) atomicOr(p.err, 1);
-  if (p.trace_slot >= 0) {
-    const int tile = (y / kRecTileY) * p.rec_tiles_x + x / kRecTileX;
-    const int r0 = p.rec_tile_ptr[tile], r1 = p.rec_tile_ptr[tile + 1];
-    for (int r = r0; r < r1; ++r) {
-      if (p.rec_xy[2 * r] == x && p.rec_xy[2 * r + 1] == y) {
-        double *t = p.traces + ((long long)p.trace_slot * p.nrec + p.rec_id[r]) * 4;
-        t[0] = (double)ux;
-        t[1] = (double)uy;
-        t[2] = (double)vx;
-        t[3] = (double)vy;
-      }
-    }
-  }
+  if (!((M.rho + jx + jy) * C(0) == C(0))) atomicOr(p.err, 1);
+  if (p.trace_slot >= 0) record_receiver<U>(p, x, y, ux, uy, vx, vy);
 }
 
 // Cells near a wall or a periodic seam: every pull goes through the general

@@ -111,11 +111,14 @@ def _random_case(nx, ny, bc, sponge, nu_rows, per_cell, seed, storage, fs_order=
                        receivers=rec)
 
 
-@pytest.mark.parametrize("storage", ["f64", "f32"])
+STORAGE_KERNELS = [("f64", "simple"), ("f32", "simple"), ("f32", "tma")]
+
+
+@pytest.mark.parametrize("storage,kernel", STORAGE_KERNELS)
 @pytest.mark.parametrize("bcname", sorted(BCS))
-@pytest.mark.parametrize("nx,ny", [(13, 7), (70, 45)])
+@pytest.mark.parametrize("nx,ny", [(13, 7), (70, 45), (300, 37)])
 @pytest.mark.parametrize("fs_order", [0, 1])
-def test_random_state_all_boundaries(storage, bcname, nx, ny, fs_order):
+def test_random_state_all_boundaries(storage, kernel, bcname, nx, ny, fs_order):
     """From a random state, five steps on odd grids (one partial block; several
     blocks with ragged edges) with every boundary kind, absorbing layers,
     per-row non-Poisson layers, two sources and three receivers: populations,
@@ -127,7 +130,7 @@ def test_random_state_all_boundaries(storage, bcname, nx, ny, fs_order):
         pytest.skip("extrapolation order only matters at a free surface")
     w = _random_case(nx, ny, bc, sponge, nu_rows, False, 3, storage, fs_order)
     fs0, u0 = _wl().random_state(nx, ny, seed=5)
-    sim = _pkg().from_workload(w)
+    sim = _pkg().from_workload(w, kernel=kernel)
     sim.set_state(fs0, u0, step=3)
     sim.step(w.nsteps)
     fs, u = sim.get_state()
@@ -140,8 +143,8 @@ def test_random_state_all_boundaries(storage, bcname, nx, ny, fs_order):
     assert max_rel(tr, tro) <= tol
 
 
-@pytest.mark.parametrize("storage", ["f64", "f32"])
-def test_per_cell_material(storage):
+@pytest.mark.parametrize("storage,kernel", STORAGE_KERNELS)
+def test_per_cell_material(storage, kernel):
     """Per-cell rho0 and Poisson ratio (Lambda varies cell by cell)."""
     nx, ny = 45, 33
     rng = np.random.default_rng(9)
@@ -149,7 +152,7 @@ def test_per_cell_material(storage):
     w = _random_case(nx, ny, ("free", "rigid", "periodic", "periodic"), (0, 4, 3, 3), nu_rows,
                      True, 4, storage)
     fs0, u0 = _wl().random_state(nx, ny, seed=6)
-    sim = _pkg().from_workload(w)
+    sim = _pkg().from_workload(w, kernel=kernel)
     sim.set_state(fs0, u0, step=0)
     sim.step(w.nsteps)
     fs, u = sim.get_state()
@@ -177,14 +180,14 @@ def test_layered_halfspace_traces_f64():
 
 # ------------------------------------------------------------ full size
 
-@pytest.mark.parametrize("storage", ["f64", "f32"])
-def test_halfspace_full_size_single_step(storage):
+@pytest.mark.parametrize("storage,kernel", STORAGE_KERNELS)
+def test_halfspace_full_size_single_step(storage, kernel):
     """Full half-space size (2048 x 1024, free top, 64-cell layers, the bench's
     launch configuration): one step from a random state equals the oracle's
     step at every cell."""
     w = _wl().halfspace(nsteps=1, storage=storage)
     fs0, u0 = _wl().random_state(w.nx, w.ny, seed=21)
-    sim = _pkg().from_workload(w)
+    sim = _pkg().from_workload(w, kernel=kernel)
     sim.set_state(fs0, u0, step=40)
     sim.step(1)
     fs, u = sim.get_state()
@@ -382,3 +385,28 @@ def test_per_row_equals_per_cell_material_bitwise():
         sim.step(7)
         out.append(sim.get_state())
     assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][1], out[1][1])
+
+
+@pytest.mark.parametrize("nu", [0.25, 0.3])
+def test_tma_kernel_equals_simple_kernel_layered(nu):
+    """The TMA-staged and the one-thread-per-cell FP32 kernels agree to a few
+    FP32 roundings on a layered half-space with sources and receivers, with
+    and without the density-gradient force, over 50 steps."""
+    wl = _wl()
+    w = wl.layered_halfspace(517, 133, 50, seed=9, sponge=12, nrec=16, storage="f32")
+    if nu == 0.25:
+        rho0, lam, mu = wl.homogeneous(w.ny, 0.25)
+        w = w.with_(rho0=rho0, lam=lam, mu=mu)
+    out = []
+    for kernel in ("simple", "tma"):
+        sim = _pkg().from_workload(w, kernel=kernel)
+        sim.step(w.nsteps)
+        out.append((sim.get_state(), sim.read_traces()))
+    (a, ua), ta = out[0]
+    (b, ub), tb = out[1]
+    assert max_rel(b, a) <= 1e-5 and max_rel(ub, ua) <= 1e-5 and max_rel(tb, ta) <= 1e-5
+
+
+def test_tma_kernel_needs_fp32():
+    with pytest.raises(_pkg().LBMError):
+        _pkg().ElasticLBM(64, 32, storage="f64", kernel="tma")
