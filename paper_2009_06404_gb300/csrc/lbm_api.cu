@@ -3,6 +3,8 @@
 // caller's workspace; this file never allocates device memory.
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
+#include <algorithm>
 #include <cstring>
 #include <mutex>
 #include <new>
@@ -28,6 +30,8 @@ size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 struct Layout {
   int pitch = 0;
   long long plane = 0;
+  int finter = 1;                 // population rows interleaved ([y][i][x])
+  long long fplane = 0, frow = 0; // population strides (elements)
   size_t tsize = 0, usize = 0, csize = 0;
   size_t f[2] = {0, 0}, u = 0, lam = 0, irho = 0, src = 0, rec_ptr = 0, rec_xy = 0,
          rec_id = 0, traces = 0, partials = 0, flags = 0, stage = 0, total = 0;
@@ -81,6 +85,9 @@ Layout make_layout(const lbm_elastic_config *c) {
   const int per_line = (int)(128 / L.tsize);
   L.pitch = (c->nx + per_line - 1) / per_line * per_line;
   L.plane = (long long)L.pitch * c->ny;
+  L.finter = 1;
+  L.fplane = L.finter ? L.pitch : L.plane;
+  L.frow = L.finter ? 9LL * L.pitch : L.pitch;
   L.rec_tiles_x = (c->nx + kRecTileX - 1) / kRecTileX;
   L.rec_tiles = L.rec_tiles_x * ((c->ny + kRecTileY - 1) / kRecTileY);
   L.mat_count = c->material_per_cell ? L.plane : c->ny;
@@ -200,16 +207,17 @@ __device__ void block_reduce7(double *v, double *out) {
 
 template <class T, class U>
 __global__ void __launch_bounds__(kRedThreads)
-    moments_partial_kernel(const T *f, const U *u, long long plane, int pitch, int nx, int ny,
-                           double *partials) {
+    moments_partial_kernel(const T *f, const U *u, long long plane, int pitch, long long fplane,
+                           long long frow, int nx, int ny, double *partials) {
   double v[7] = {0, 0, 0, 0, 0, 0, 0};
   const long long n = (long long)nx * ny;
   for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n;
        k += (long long)gridDim.x * blockDim.x) {
     const long long c = (k / nx) * pitch + k % nx;
+    const long long cf = (k / nx) * frow + k % nx;
     double q[9];
 #pragma unroll
-    for (int i = 0; i < 9; ++i) q[i] = (double)f[i * plane + c];
+    for (int i = 0; i < 9; ++i) q[i] = (double)f[i * fplane + cf];
     v[0] += q[0] + q[1] + q[2] + q[3] + q[4] + q[5] + q[6] + q[7] + q[8];
     v[1] += q[1] - q[3] + q[5] - q[6] - q[7] + q[8];
     v[2] += q[2] - q[4] + q[5] + q[6] - q[7] - q[8];
@@ -250,6 +258,8 @@ struct lbm_elastic {
   bool lambda_nonzero = false;
   long long launches = 0;
   std::vector<SourceDev> src_host;
+  int src_box[4] = {0, -1, 0, -1};  // x0, x1, y0, y1 of all source footprints
+  int rec_box[4] = {0, -1, 0, -1};  // x0, x1, y0, y1 of all receivers
   std::string err;
 };
 
@@ -310,7 +320,10 @@ StepParams base_params(lbm_elastic_t *h) {
   p.fin = h->ws + L.f[h->cur];
   p.fout = h->ws + L.f[1 - h->cur];
   p.u = h->ws + L.u;
-  p.plane = L.plane;
+  p.plane = (int)L.plane;
+  p.fplane = (int)L.fplane;
+  p.frow = (int)L.frow;
+  p.finter = L.finter;
   p.nx = c.nx;
   p.ny = c.ny;
   p.pitch = L.pitch;
@@ -351,6 +364,15 @@ StepParams base_params(lbm_elastic_t *h) {
   p.nrec = h->nrec;
   p.traces = at<double>(h, L.traces);
   p.err = at<int>(h, L.flags);
+  p.src_x0 = h->src_box[0];
+  p.src_x1 = h->src_box[1];
+  p.src_y0 = h->src_box[2];
+  p.src_y1 = h->src_box[3];
+  p.rec_x0 = h->rec_box[0];
+  p.rec_x1 = h->rec_box[1];
+  p.rec_y0 = h->rec_box[2];
+  p.rec_y1 = h->rec_box[3];
+  p.reverse = (int)(h->step & 1);
   return p;
 }
 
@@ -367,18 +389,18 @@ lbm_status launch_step(lbm_elastic_t *h, const StepParams &p, int mode, int rows
 }
 
 template <class T>
-lbm_status state_io(lbm_elastic_t *h, T *planes, long long splane, int nplanes, double *dst,
-                    const double *src, int on_device, long long dense_plane) {
+lbm_status state_io(lbm_elastic_t *h, T *planes, long long splane, int srow, int nplanes,
+                    double *dst, const double *src, int on_device, long long dense_plane) {
   // dst (to f64) or src (from f64): [nplanes][ny][nx]
   const lbm_elastic_config &c = h->cfg;
   const Layout &L = h->L;
   if (on_device) {
     const long long n = (long long)c.nx * c.ny * nplanes;
     if (dst)
-      to_f64_kernel<T><<<grid1d(n, 256), 256, 0, h->stream>>>(planes, splane, L.pitch, c.nx, 0,
+      to_f64_kernel<T><<<grid1d(n, 256), 256, 0, h->stream>>>(planes, splane, srow, c.nx, 0,
                                                                c.ny, nplanes, dst, dense_plane);
     else
-      from_f64_kernel<T><<<grid1d(n, 256), 256, 0, h->stream>>>(planes, splane, L.pitch, c.nx, 0,
+      from_f64_kernel<T><<<grid1d(n, 256), 256, 0, h->stream>>>(planes, splane, srow, c.nx, 0,
                                                                  c.ny, nplanes, src, dense_plane);
     return check_launch(h, "state conversion launch");
   }
@@ -388,7 +410,7 @@ lbm_status state_io(lbm_elastic_t *h, T *planes, long long splane, int nplanes, 
     const long long chunk = (long long)nr * c.nx;
     const long long n = chunk * nplanes;
     if (dst) {
-      to_f64_kernel<T><<<grid1d(n, 256), 256, 0, h->stream>>>(planes, splane, L.pitch, c.nx, r0,
+      to_f64_kernel<T><<<grid1d(n, 256), 256, 0, h->stream>>>(planes, splane, srow, c.nx, r0,
                                                                nr, nplanes, stage, chunk);
       lbm_status s = check_launch(h, "state conversion launch");
       if (s) return s;
@@ -403,7 +425,7 @@ lbm_status state_io(lbm_elastic_t *h, T *planes, long long splane, int nplanes, 
                                       src + pl * dense_plane + (long long)r0 * c.nx,
                                       chunk * sizeof(double), cudaMemcpyHostToDevice, h->stream));
       from_f64_kernel<T><<<grid1d(n, 256), 256, 0, h->stream>>>(
-          planes, splane, L.pitch, c.nx, r0, nr, nplanes, src ? stage : nullptr, chunk);
+          planes, splane, srow, c.nx, r0, nr, nplanes, src ? stage : nullptr, chunk);
       lbm_status s = check_launch(h, "state conversion launch");
       if (s) return s;
     }
@@ -417,16 +439,17 @@ lbm_status f_io(lbm_elastic_t *h, double *dst, const double *src, int on_device)
   void *f = h->ws + h->L.f[h->cur];
   const long long dp = (long long)h->cfg.nx * h->cfg.ny;
   if (h->cfg.storage == LBM_F64)
-    return state_io<double>(h, (double *)f, h->L.plane, 9, dst, src, on_device, dp);
-  return state_io<float>(h, (float *)f, h->L.plane, 9, dst, src, on_device, dp);
+    return state_io<double>(h, (double *)f, h->L.fplane, (int)h->L.frow, 9, dst, src, on_device,
+                            dp);
+  return state_io<float>(h, (float *)f, h->L.fplane, (int)h->L.frow, 9, dst, src, on_device, dp);
 }
 
 lbm_status u_io(lbm_elastic_t *h, double *dst, const double *src, int on_device) {
   void *u = h->ws + h->L.u;
   const long long dp = (long long)h->cfg.nx * h->cfg.ny;
   if (h->L.usize == 8)
-    return state_io<double>(h, (double *)u, h->L.plane, 2, dst, src, on_device, dp);
-  return state_io<float>(h, (float *)u, h->L.plane, 2, dst, src, on_device, dp);
+    return state_io<double>(h, (double *)u, h->L.plane, h->L.pitch, 2, dst, src, on_device, dp);
+  return state_io<float>(h, (float *)u, h->L.plane, h->L.pitch, 2, dst, src, on_device, dp);
 }
 
 lbm_status clear_state(lbm_elastic_t *h) {
@@ -490,9 +513,15 @@ bool setup_tma(lbm_elastic_t *h, std::string *why) {
   const int halo = tma_halo_x(es);
   for (int b = 0; b < 2; ++b)
     for (int hh = 1; hh <= 2; ++hh) {
-      const cuuint64_t dims[3] = {(cuuint64_t)c.nx, (cuuint64_t)c.ny, 9};
-      const cuuint64_t strides[2] = {(cuuint64_t)L.pitch * es, (cuuint64_t)L.plane * es};
-      const cuuint32_t box[3] = {(cuuint32_t)(kTileW + 2 * halo), (cuuint32_t)(kTileH + 2 * hh), 9};
+      // dims listed fastest first; [y][plane][x] when rows are interleaved
+      const cuuint64_t dims[3] = {(cuuint64_t)c.nx, L.finter ? 9u : (cuuint64_t)c.ny,
+                                  L.finter ? (cuuint64_t)c.ny : 9u};
+      const cuuint64_t strides[2] = {
+          (cuuint64_t)(L.finter ? L.fplane : L.frow) * es,
+          (cuuint64_t)(L.finter ? L.frow : L.fplane) * es};
+      const cuuint32_t box[3] = {(cuuint32_t)(kTileW + 2 * halo),
+                                 L.finter ? 9u : (cuuint32_t)(kTileH + 2 * hh),
+                                 L.finter ? (cuuint32_t)(kTileH + 2 * hh) : 9u};
       const cuuint32_t estr[3] = {1, 1, 1};
       CUresult r = enc(&h->maps.f[b][hh - 1], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, h->ws + L.f[b],
                        dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
@@ -670,6 +699,30 @@ lbm_status lbm_elastic_set_sources(lbm_elastic_t *h, const lbm_source *src, int 
     q.pif2 = M_PI * M_PI * s.f_peak * s.f_peak;
     q.t0 = s.t0;
   }
+  // bounding box of every footprint (the whole axis when it wraps around)
+  int bx0 = h->cfg.nx, bx1 = -1, by0 = h->cfg.ny, by1 = -1;
+  for (const SourceDev &q : v) {
+    const long long lo_x = (long long)q.xc - q.rb, hi_x = (long long)q.xc + q.rb;
+    const long long lo_y = (long long)q.yc - q.rb, hi_y = (long long)q.yc + q.rb;
+    if (lo_x < 0 || hi_x >= h->cfg.nx) {
+      bx0 = 0;
+      bx1 = h->cfg.nx - 1;
+    } else {
+      bx0 = std::min<long long>(bx0, lo_x);
+      bx1 = std::max<long long>(bx1, hi_x);
+    }
+    if (lo_y < 0 || hi_y >= h->cfg.ny) {
+      by0 = 0;
+      by1 = h->cfg.ny - 1;
+    } else {
+      by0 = std::min<long long>(by0, lo_y);
+      by1 = std::max<long long>(by1, hi_y);
+    }
+  }
+  h->src_box[0] = bx0;
+  h->src_box[1] = bx1;
+  h->src_box[2] = by0;
+  h->src_box[3] = by1;
   h->src_host = v;
   if (n)
     LBM_CUDA(h, cudaMemcpyAsync(h->ws + h->L.src, h->src_host.data(), n * sizeof(SourceDev),
@@ -711,6 +764,16 @@ lbm_status lbm_elastic_set_receivers(lbm_elastic_t *h, const int *xy, int n) {
                                 cudaMemcpyHostToDevice, h->stream));
   }
   LBM_CUDA(h, cudaStreamSynchronize(h->stream));  // host vectors die here
+  h->rec_box[0] = h->cfg.nx;
+  h->rec_box[1] = -1;
+  h->rec_box[2] = h->cfg.ny;
+  h->rec_box[3] = -1;
+  for (int r = 0; r < n; ++r) {
+    h->rec_box[0] = std::min(h->rec_box[0], xy[2 * r]);
+    h->rec_box[1] = std::max(h->rec_box[1], xy[2 * r]);
+    h->rec_box[2] = std::min(h->rec_box[2], xy[2 * r + 1]);
+    h->rec_box[3] = std::max(h->rec_box[3], xy[2 * r + 1]);
+  }
   h->nrec = n;
   h->traced = 0;
   return LBM_OK;
@@ -882,13 +945,16 @@ lbm_status lbm_elastic_moment_sums(lbm_elastic_t *h, double out[7]) {
   const void *u = h->ws + L.u;
   if (h->cfg.storage == LBM_F64)
     moments_partial_kernel<double, double><<<kRedBlocks, kRedThreads, 0, h->stream>>>(
-        (const double *)f, (const double *)u, L.plane, L.pitch, h->cfg.nx, h->cfg.ny, partials);
+        (const double *)f, (const double *)u, L.plane, L.pitch, L.fplane, L.frow, h->cfg.nx,
+        h->cfg.ny, partials);
   else if (L.usize == 8)
     moments_partial_kernel<float, double><<<kRedBlocks, kRedThreads, 0, h->stream>>>(
-        (const float *)f, (const double *)u, L.plane, L.pitch, h->cfg.nx, h->cfg.ny, partials);
+        (const float *)f, (const double *)u, L.plane, L.pitch, L.fplane, L.frow, h->cfg.nx,
+        h->cfg.ny, partials);
   else
     moments_partial_kernel<float, float><<<kRedBlocks, kRedThreads, 0, h->stream>>>(
-        (const float *)f, (const float *)u, L.plane, L.pitch, h->cfg.nx, h->cfg.ny, partials);
+        (const float *)f, (const float *)u, L.plane, L.pitch, L.fplane, L.frow, h->cfg.nx,
+        h->cfg.ny, partials);
   lbm_status s = check_launch(h, "moment sums launch");
   if (s) return s;
   moments_final_kernel<<<1, kRedThreads, 0, h->stream>>>(partials, kRedBlocks,
@@ -991,13 +1057,13 @@ extern "C" lbm_status lbm_elastic_moment_sums_noalloc(const void *f9, const void
   // so nothing left from an earlier call needs clearing
   if (storage == LBM_F64)
     moments_partial_kernel<double, double><<<kRedBlocks, kRedThreads, 0, s>>>(
-        (const double *)f9, (const double *)u2, plane, pitch, nx, ny, scratch);
+        (const double *)f9, (const double *)u2, plane, pitch, plane, pitch, nx, ny, scratch);
   else if (u_fp64)
     moments_partial_kernel<float, double><<<kRedBlocks, kRedThreads, 0, s>>>(
-        (const float *)f9, (const double *)u2, plane, pitch, nx, ny, scratch);
+        (const float *)f9, (const double *)u2, plane, pitch, plane, pitch, nx, ny, scratch);
   else
     moments_partial_kernel<float, float><<<kRedBlocks, kRedThreads, 0, s>>>(
-        (const float *)f9, (const float *)u2, plane, pitch, nx, ny, scratch);
+        (const float *)f9, (const float *)u2, plane, pitch, plane, pitch, nx, ny, scratch);
   e = cudaGetLastError();
   if (e != cudaSuccess) return fail(nullptr, LBM_ERR_CUDA, cudaGetErrorString(e));
   moments_final_kernel<<<1, kRedThreads, 0, s>>>(scratch, kRedBlocks, scratch + 8 * kRedBlocks);

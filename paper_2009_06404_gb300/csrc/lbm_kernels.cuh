@@ -42,8 +42,10 @@ struct StepParams {
   const void *fin;   // post-collision populations of step n-1 (9 planes)
   void *fout;        // post-collision populations of step n
   void *u;           // displacement: u_x plane then u_y plane
-  int plane;         // elements between two planes (9 * plane < 2^31)
-  int nx, ny, pitch;
+  int plane;         // displacement / per-cell material: elements between planes
+  int nx, ny, pitch; // pitch: elements between rows of those arrays
+  int fplane, frow;  // populations: elements between planes i and i+1, rows y and y+1
+  int finter;        // 1: rows of the nine planes interleaved (frow = 9 fplane)
   int bc_top, bc_bottom, bc_left, bc_right;
   int sp_top, sp_bottom, sp_left, sp_right;
   int fs_order;      // free-surface extrapolation: 1 linear, 0 constant
@@ -66,6 +68,11 @@ struct StepParams {
   int nrec;
   double *traces;           // [slots][nrec][4]
   int *err;                 // bit 0: non-finite value met
+  // bounding boxes (inclusive, in cells) of every receiver and of every
+  // source footprint; blocks outside them skip the per-block lookups
+  int rec_x0, rec_x1, rec_y0, rec_y1;
+  int src_x0, src_x1, src_y0, src_y1;
+  int reverse;              // 1: blocks visit the grid in reverse order
   // fields mode only
   int row0, nrows;
   double *out[8];           // ux uy vx vy rho pxx pxy pyy, [nrows][nx] each
@@ -112,10 +119,10 @@ template <> __device__ __forceinline__ void st<__nv_bfloat16, float>(__nv_bfloat
 template <class T, class C>
 __device__ void cell_rho_pdiag(const StepParams &p, const T *f, int x, int y, C &rho,
                                C &pxx, C &pyy) {
-  const int c = y * p.pitch + x;
+  const int c = y * p.frow + x;
   C v[9];
 #pragma unroll
-  for (int i = 0; i < 9; ++i) v[i] = ld<T, C>(f + i * p.plane + c);
+  for (int i = 0; i < 9; ++i) v[i] = ld<T, C>(f + i * p.fplane + c);
   rho = v[0] + v[1] + v[2] + v[3] + v[4] + v[5] + v[6] + v[7] + v[8];
   pxx = v[1] + v[3] + v[5] + v[6] + v[7] + v[8];
   pyy = v[2] + v[4] + v[5] + v[6] + v[7] + v[8];
@@ -130,7 +137,7 @@ template <class T, class C>
 __device__ C wall_value(const StepParams &p, const T *f, int bc, int nxo, int nyo, int i,
                         int x, int y) {
   const int k = oppd(i);
-  const C fk = ld<T, C>(f + k * p.plane + y * p.pitch + x);
+  const C fk = ld<T, C>(f + k * p.fplane + y * p.frow + x);
   if (bc == BC_RIGID) return fk;
   C rb, pxxb, pyyb, ri, pxxi, pyyi;
   cell_rho_pdiag<T, C>(p, f, x, y, rb, pxxb, pyyb);
@@ -174,16 +181,16 @@ __device__ __noinline__ C pull_general(const StepParams &p, const T *f, int i, i
       return wall_value<T, C>(p, f, p.bc_right, 1, 0, i, x, y);
     }
   }
-  return ld<T, C>(f + i * p.plane + sy * p.pitch + sx);
+  return ld<T, C>(f + i * p.fplane + sy * p.frow + sx);
 }
 
 // All nine streamed populations of (x, y).
 template <class T, class C>
 __device__ __forceinline__ void gather(const StepParams &p, const T *f, int x, int y, C *fo) {
   if (x > 0 && x < p.nx - 1 && y > 0 && y < p.ny - 1) {
-    const T *b = f + (y * p.pitch + x);
+    const T *b = f + (y * p.frow + x);
 #pragma unroll
-    for (int i = 0; i < 9; ++i) fo[i] = ld<T, C>(b + (i * p.plane - cyd(i) * p.pitch - cxd(i)));
+    for (int i = 0; i < 9; ++i) fo[i] = ld<T, C>(b + (i * p.fplane - cyd(i) * p.frow - cxd(i)));
   } else {
 #pragma unroll
     for (int i = 0; i < 9; ++i) fo[i] = pull_general<T, C>(p, f, i, x, y);
@@ -331,10 +338,10 @@ __device__ __forceinline__ C mat_at(const void *tab, int per_cell, int x, int y,
 // upstream cells all lie inside the grid (direct loads only).
 template <class T, class C>
 __device__ __forceinline__ C rho_direct(const StepParams &p, const T *f, int x, int y) {
-  const T *b = f + (y * p.pitch + x);
+  const T *b = f + (y * p.frow + x);
   C r = C(0);
 #pragma unroll
-  for (int i = 0; i < 9; ++i) r += ld<T, C>(b + (i * p.plane - cyd(i) * p.pitch - cxd(i)));
+  for (int i = 0; i < 9; ++i) r += ld<T, C>(b + (i * p.fplane - cyd(i) * p.frow - cxd(i)));
   return r;
 }
 
@@ -469,9 +476,9 @@ __device__ __forceinline__ void finish_cell(const StepParams &p, const C *f, C g
   collide_cell<C>(M, jx, jy, Sx, Sy, par<C>(p.omega, p.omega_f), par<C>(p.fcoef, p.fcoef_f), fs);
   if (!active) return;
   const int c = y * p.pitch + x;
-  T *fout = (T *)p.fout + c;
+  T *fout = (T *)p.fout + (y * p.frow + x);
 #pragma unroll
-  for (int i = 0; i < 9; ++i) st<T, C>(fout + i * p.plane, fs[i]);
+  for (int i = 0; i < 9; ++i) st<T, C>(fout + i * p.fplane, fs[i]);
   U *u = (U *)p.u;
   const U vx = U(jx * irho), vy = U(jy * irho);
   const U ux = (UIN ? ux0 : u[c]) + vx, uy = (UIN ? uy0 : u[p.plane + c]) + vy;
@@ -500,26 +507,57 @@ __device__ __noinline__ void boundary_cell(const StepParams &p, C Fx, C Fy, int 
   finish_cell<T, C, U, LAM, MODE>(p, f, gx, gy, Fx, Fy, x, y, xc, yc, active);
 }
 
-// One thread per cell, blocks of 32 x 8 (a warp is 32 consecutive cells of a
-// row).  MODE 0: full step.  MODE 1: fields of the current state, rows
-// [row0, row0 + nrows).
+// Whether the block's cells [x0, x0 + 32) x [y0, y0 + h) need anything
+// beyond the bulk update: a wall or periodic seam within m cells, a source,
+// or (when recording) a receiver.  Warp-wide
+// (all 32 lanes call it); every lane gets the same answer.
+__device__ __forceinline__ bool block_is_special(const StepParams &p, int x0, int y0, int h,
+                                                 int m) {
+  if (x0 < m || x0 + 32 > p.nx - m || y0 < m || y0 + h > p.ny - m) return true;
+  const bool near_src = p.nsrc > 0 && x0 <= p.src_x1 && x0 + 31 >= p.src_x0 &&
+                        y0 <= p.src_y1 && y0 + h - 1 >= p.src_y0;
+  const bool near_rec = p.trace_slot >= 0 && x0 <= p.rec_x1 && x0 + 31 >= p.rec_x0 &&
+                        y0 <= p.rec_y1 && y0 + h - 1 >= p.rec_y0;
+  if (!near_src && !near_rec) return false;
+  if (p.nsrc > 32) return true;
+  const int lane = threadIdx.x & 31;
+  bool hit = false;
+  if (near_src && lane < p.nsrc) {
+    const SourceDev &q = p.src[lane];
+    int dx = x0 + 16 - q.xc, dy = y0 + h / 2 - q.yc;
+    if (p.bc_left == BC_PERIODIC) {
+      if (dx > p.nx / 2) dx -= p.nx;
+      else if (dx < -(p.nx / 2)) dx += p.nx;
+    }
+    if (p.bc_top == BC_PERIODIC) {
+      if (dy > p.ny / 2) dy -= p.ny;
+      else if (dy < -(p.ny / 2)) dy += p.ny;
+    }
+    hit = abs(dx) <= q.rb + 17 && abs(dy) <= q.rb + h / 2 + 1;
+  }
+  if (near_rec && lane >= 30) {
+    // receiver tiles are 64 x 4; this block spans one tile column, and rows
+    // y0 / 4 .. (y0 + h - 1) / 4
+    for (int ty = y0 / kRecTileY + (lane - 30); ty * kRecTileY < y0 + h && ty * kRecTileY < p.ny;
+         ty += 2) {
+      const int t = ty * p.rec_tiles_x + x0 / kRecTileX;
+      hit |= p.rec_tile_ptr[t + 1] > p.rec_tile_ptr[t];
+    }
+  }
+  return __ballot_sync(0xffffffffu, hit) != 0u;
+}
+
+// Full update of one cell with every feature (walls, layers, sources,
+// receivers): the path of blocks that are special, kept out of line so the
+// bulk path carries none of its registers.
 template <class T, class C, class U, bool LAM, int MODE>
-__global__ void __launch_bounds__(256, 4) step_kernel(const StepParams p) {
-  const int x = blockIdx.x * blockDim.x + threadIdx.x;
-  const int y = blockIdx.y * blockDim.y + threadIdx.y + (MODE == 1 ? p.row0 : 0);
-  const int yend = MODE == 1 ? p.row0 + p.nrows : p.ny;
-  // Whole warps stay alive for the warp-level source culling; cells outside
-  // the grid are clamped and write nothing.
+__device__ __noinline__ void general_cell(const StepParams &p, int x, int y, int yend) {
+  const int m = LAM ? 2 : 1;
   const bool active = x < p.nx && y < yend;
   const int xc = x < p.nx ? x : p.nx - 1;
   const int yc = y < yend ? y : yend - 1;
-
   C Fx, Fy;
   body_force<C>(p, xc, yc, Fx, Fy);  // all lanes of the warp take part
-
-  // interior: all upstream cells (and, with the density gradient, those of
-  // the four neighbours) lie inside the grid
-  const int m = LAM ? 2 : 1;
   if (!(xc >= m && xc < p.nx - m && yc >= m && yc < p.ny - m)) {
     boundary_cell<T, C, U, LAM, MODE>(p, Fx, Fy, x, y, xc, yc, active);
     return;
@@ -527,17 +565,110 @@ __global__ void __launch_bounds__(256, 4) step_kernel(const StepParams p) {
   const T *fin = (const T *)p.fin;
   C f[9];
   {
-    const T *b = fin + (yc * p.pitch + xc);
+    const T *b = fin + (yc * p.frow + xc);
 #pragma unroll
-    for (int i = 0; i < 9; ++i) f[i] = ld<T, C>(b + (i * p.plane - cyd(i) * p.pitch - cxd(i)));
+    for (int i = 0; i < 9; ++i) f[i] = ld<T, C>(b + (i * p.fplane - cyd(i) * p.frow - cxd(i)));
   }
+  const U *u = (const U *)p.u;
+  const int c = yc * p.pitch + xc;
+  const U ux0 = u[c], uy0 = u[p.plane + c];  // before any store
   C gx = C(0), gy = C(0);
   if (LAM) {
-    // centred difference of the streamed density (Eq. 10)
     gx = C(0.5) * (rho_direct<T, C>(p, fin, xc + 1, yc) - rho_direct<T, C>(p, fin, xc - 1, yc));
     gy = C(0.5) * (rho_direct<T, C>(p, fin, xc, yc + 1) - rho_direct<T, C>(p, fin, xc, yc - 1));
   }
-  finish_cell<T, C, U, LAM, MODE>(p, f, gx, gy, Fx, Fy, x, y, xc, yc, active);
+  finish_cell<T, C, U, LAM, MODE, true>(p, f, gx, gy, Fx, Fy, x, y, xc, yc, active, ux0, uy0);
+}
+
+// One thread per cell, blocks of 32 x 8 threads (a warp is 32 consecutive
+// cells of a row).  Blocks in the bulk (no wall, source or receiver nearby)
+// do only what the bulk needs: pull, moments, the absorbing layer where the
+// block overlaps one, the density-gradient force when some Lambda != 0,
+// collision, stores, displacement.  MODE 0: full step.  MODE 1: fields of the
+// current state, rows [row0, row0 + nrows).
+// Resident blocks per SM the compiler is asked to allow for (sets the
+// register budget of the step kernel: 65536 / (256 x this)).
+#ifndef LBM_STEP_MIN_BLOCKS
+#define LBM_STEP_MIN_BLOCKS 6
+#endif
+
+template <class T, class C, class U, bool LAM, int MODE>
+__global__ void __launch_bounds__(256, LBM_STEP_MIN_BLOCKS) step_kernel(const StepParams p) {
+  // alternate steps visit the blocks in reverse order: the rows written last
+  // by one step (still in L2) are the first the next step reads
+  const int bx = (MODE == 0 && p.reverse) ? gridDim.x - 1 - blockIdx.x : blockIdx.x;
+  const int by = (MODE == 0 && p.reverse) ? gridDim.y - 1 - blockIdx.y : blockIdx.y;
+  const int x0 = bx * blockDim.x;
+  const int x = x0 + threadIdx.x;
+  const int y0 = by * blockDim.y + (MODE == 1 ? p.row0 : 0);
+  const int y = y0 + threadIdx.y;
+  const int yend = MODE == 1 ? p.row0 + p.nrows : p.ny;
+  const int m = LAM ? 2 : 1;
+  if (MODE == 1 || block_is_special(p, x0, y0, blockDim.y, m)) {
+    general_cell<T, C, U, LAM, MODE>(p, x, y, yend);
+    return;
+  }
+  // bulk cell: every upstream cell (and every neighbour's) is inside the
+  // grid.  All loads of the cell are issued before any store (the
+  // displacement could otherwise not be read until the populations are
+  // written).
+  const T *fin = (const T *)p.fin;
+  C f[9];
+  {
+    const T *b = fin + (y * p.frow + x);
+#pragma unroll
+    for (int i = 0; i < 9; ++i) f[i] = ld<T, C>(b + (i * p.fplane - cyd(i) * p.frow - cxd(i)));
+  }
+  const int c = y * p.pitch + x;
+  U *u = (U *)p.u;
+  const U ux0 = u[c], uy0 = u[p.plane + c];
+  const C irho = mat_at<C>(p.irho, p.mat_per_cell, x, y, p.pitch);
+  const Moments<C> M = cell_moments<C>(f);
+  C Gx = C(0), Gy = C(0);
+  if (LAM) {
+    // streamed density of the block and a one-cell ring in shared memory
+    // (every block in this branch is bulk: the barrier is uniform)
+    __shared__ C rho_s[10][34];
+    rho_s[threadIdx.y + 1][threadIdx.x + 1] = M.rho;
+    const int t = threadIdx.y * 32 + threadIdx.x;
+    if (t < 80) {
+      int hx, hy;  // ring cell: rows above/below (64), columns left/right (16)
+      if (t < 64) {
+        hx = t & 31;
+        hy = t < 32 ? -1 : 8;
+      } else {
+        hx = (t & 1) ? 32 : -1;
+        hy = (t - 64) >> 1;
+      }
+      rho_s[hy + 1][hx + 1] = rho_direct<T, C>(p, fin, x0 + hx, y0 + hy);
+    }
+    __syncthreads();
+    // elastic force Lambda b^2 grad rho with the centred difference (Eqs. 9-10)
+    const C gx = C(0.5) * (rho_s[threadIdx.y + 1][threadIdx.x + 2] - rho_s[threadIdx.y + 1][threadIdx.x]);
+    const C gy = C(0.5) * (rho_s[threadIdx.y + 2][threadIdx.x + 1] - rho_s[threadIdx.y][threadIdx.x + 1]);
+    const C lb2 = mat_at<C>(p.lam, p.mat_per_cell, x, y, p.pitch) * C(1.0 / 3.0);
+    Gx = lb2 * gx;
+    Gy = lb2 * gy;
+  }
+  C jx, jy, Sx, Sy;
+  if (x0 < p.sp_left || x0 + 32 > p.nx - p.sp_right || y0 < p.sp_top ||
+      y0 + (int)blockDim.y > p.ny - p.sp_bottom) {
+    flux_and_source<C>(M.mx, M.my, Gx, Gy, C(0), C(0), sponge_A<C>(p, x, y), jx, jy, Sx, Sy);
+  } else {
+    // no absorbing layer: j = m + G/2, S = G
+    jx = M.mx + C(0.5) * Gx;
+    jy = M.my + C(0.5) * Gy;
+    Sx = Gx;
+    Sy = Gy;
+  }
+  C fs[9];
+  collide_cell<C>(M, jx, jy, Sx, Sy, par<C>(p.omega, p.omega_f), par<C>(p.fcoef, p.fcoef_f), fs);
+  T *fout = (T *)p.fout + (y * p.frow + x);
+#pragma unroll
+  for (int i = 0; i < 9; ++i) st<T, C>(fout + i * p.fplane, fs[i]);
+  u[c] = ux0 + U(jx * irho);
+  u[p.plane + c] = uy0 + U(jy * irho);
+  if (!((M.rho + jx + jy) * C(0) == C(0))) atomicOr(p.err, 1);
 }
 
 // Launch entry points, one translation unit per storage type.
@@ -545,5 +676,6 @@ void launch_step_f64(const StepParams &p, bool lam, int mode, dim3 grid, dim3 bl
                      cudaStream_t s);
 void launch_step_f32(const StepParams &p, bool lam, bool u64, int mode, dim3 grid, dim3 block,
                      cudaStream_t s);
+
 
 }  // namespace lbm

@@ -66,6 +66,17 @@ __device__ __forceinline__ void tma_load_3d(void *dst, const CUtensorMap *map, i
 }
 
 template <class T, class U, int TH, int H>
+struct TileGeom;
+
+// Offset of plane i, tile row r (0 = first halo row) in a stage: the smem
+// tile keeps the order of the global layout ([row][plane] when the rows of
+// the nine planes are interleaved, [plane][row] otherwise).
+template <class G>
+__device__ __forceinline__ int sidx(int inter, int i, int r) {
+  return (inter ? (r * 9 + i) : (i * G::kRows + r)) * G::kRowLen;
+}
+
+template <class T, class U, int TH, int H>
 struct TileGeom {
   static constexpr int kHalo = 16 / (int)sizeof(T);  // x halo: one 16-byte unit
   static constexpr int kRowLen = kTileW + 2 * kHalo; // smem row of one plane
@@ -146,7 +157,10 @@ __global__ void __launch_bounds__(kTmaThreads, 2)
     const int x0 = (t % ntx) * kTileW, y0 = (t / ntx) * TH;
     unsigned char *st = smem + s * G::kStage;
     mbar_expect_tx(&bar[s], (uint32_t)(G::kFBytes + G::kUBytes));
-    tma_load_3d(st, &fmap, x0 - G::kHalo, y0 - H, 0, &bar[s]);
+    if (p.finter)
+      tma_load_3d(st, &fmap, x0 - G::kHalo, 0, y0 - H, &bar[s]);
+    else
+      tma_load_3d(st, &fmap, x0 - G::kHalo, y0 - H, 0, &bar[s]);
     tma_load_3d(st + G::kFBytesAl, &umap, x0, y0, 0, &bar[s]);
   };
 
@@ -194,8 +208,7 @@ __global__ void __launch_bounds__(kTmaThreads, 2)
         float acc = 0.f;
 #pragma unroll
         for (int i = 0; i < 9; ++i)
-          acc += ld<T, float>(sf + (i * G::kRows + (r + H - cyd(i))) * G::kRowLen +
-                              (c + G::kHalo - cxd(i)));
+          acc += ld<T, float>(sf + sidx<G>(p.finter, i, r + H - cyd(i)) + (c + G::kHalo - cxd(i)));
         rho_s[k] = acc;
       }
       __syncthreads();
@@ -234,8 +247,7 @@ __global__ void __launch_bounds__(kTmaThreads, 2)
       float f[9];
 #pragma unroll
       for (int i = 0; i < 9; ++i)
-        f[i] = ld<T, float>(sf + (i * G::kRows + (row + H - cyd(i))) * G::kRowLen +
-                            (lx + G::kHalo - cxd(i)));
+        f[i] = ld<T, float>(sf + sidx<G>(p.finter, i, row + H - cyd(i)) + (lx + G::kHalo - cxd(i)));
       const Moments<float> M = cell_moments<float>(f);
       const int c = y * p.pitch + x;
       float Gx = 0.f, Gy = 0.f;
@@ -252,9 +264,9 @@ __global__ void __launch_bounds__(kTmaThreads, 2)
       flux_and_source<float>(M.mx, M.my, Gx, Gy, Fx, Fy, A, jx, jy, Sx, Sy);
       float fs[9];
       collide_cell<float>(M, jx, jy, Sx, Sy, om, fc, fs);
-      T *fout = (T *)p.fout + c;
+      T *fout = (T *)p.fout + (y * p.frow + x);
 #pragma unroll
-      for (int i = 0; i < 9; ++i) st<T, float>(fout + i * p.plane, fs[i]);
+      for (int i = 0; i < 9; ++i) st<T, float>(fout + i * p.fplane, fs[i]);
       const float irho = p.mat_per_cell ? ((const float *)p.irho)[c] : irho_row;
       const U vx = U(jx * irho), vy = U(jy * irho);
       const U ux = su[row * kTileW + lx] + vx, uy = su[(TH + row) * kTileW + lx] + vy;
