@@ -586,6 +586,18 @@ __device__ __noinline__ void general_cell(const StepParams &p, int x, int y, int
 // block overlaps one, the density-gradient force when some Lambda != 0,
 // collision, stores, displacement.  MODE 0: full step.  MODE 1: fields of the
 // current state, rows [row0, row0 + nrows).
+// LBM_PDL: launch the steps with programmatic dependent launch (the next
+// step's blocks are scheduled while the previous step drains; each waits for
+// the previous step to complete before reading).  LBM_ORDER 1: on reversed
+// steps the top block row (free surface, receivers) is still visited first,
+// so the slower wall blocks never form the last wave.
+#ifndef LBM_PDL
+#define LBM_PDL 1
+#endif
+#ifndef LBM_ORDER
+#define LBM_ORDER 1
+#endif
+
 // Resident blocks per SM the compiler is asked to allow for (sets the
 // register budget of the step kernel: 65536 / (256 x this)).
 #ifndef LBM_STEP_MIN_BLOCKS
@@ -594,10 +606,28 @@ __device__ __noinline__ void general_cell(const StepParams &p, int x, int y, int
 
 template <class T, class C, class U, bool LAM, int MODE>
 __global__ void __launch_bounds__(256, LBM_STEP_MIN_BLOCKS) step_kernel(const StepParams p) {
+#if LBM_PDL
+  // programmatic dependent launch: wait for the previous step to complete
+  // (its populations are this step's input), then let the next step's
+  // blocks be scheduled as SMs free up
+  if (MODE == 0) {
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;");
+  }
+#endif
   // alternate steps visit the blocks in reverse order: the rows written last
   // by one step (still in L2) are the first the next step reads
-  const int bx = (MODE == 0 && p.reverse) ? gridDim.x - 1 - blockIdx.x : blockIdx.x;
-  const int by = (MODE == 0 && p.reverse) ? gridDim.y - 1 - blockIdx.y : blockIdx.y;
+  int bx = blockIdx.x, by = blockIdx.y;
+  if (MODE == 0 && p.reverse) {
+#if LBM_ORDER == 1
+    // the top block row (walls, receivers) still goes first
+    if (by > 0) by = gridDim.y - by;
+    bx = gridDim.x - 1 - bx;
+#else
+    bx = gridDim.x - 1 - bx;
+    by = gridDim.y - 1 - by;
+#endif
+  }
   const int x0 = bx * blockDim.x;
   const int x = x0 + threadIdx.x;
   const int y0 = by * blockDim.y + (MODE == 1 ? p.row0 : 0);
@@ -676,6 +706,28 @@ void launch_step_f64(const StepParams &p, bool lam, int mode, dim3 grid, dim3 bl
                      cudaStream_t s);
 void launch_step_f32(const StepParams &p, bool lam, bool u64, int mode, dim3 grid, dim3 block,
                      cudaStream_t s);
+
+// Launches kernel k with programmatic stream serialization when LBM_PDL is
+// set (the kernel then starts with griddepcontrol.wait), else plainly.
+template <class K>
+inline cudaError_t launch_pdl(K k, dim3 grid, dim3 block, cudaStream_t s, const StepParams &p) {
+#if LBM_PDL
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, k, p);
+#else
+  k<<<grid, block, 0, s>>>(p);
+  return cudaSuccess;
+#endif
+}
 
 
 }  // namespace lbm

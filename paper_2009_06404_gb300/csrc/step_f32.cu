@@ -8,8 +8,8 @@ template <class U>
 static void launch_u(const StepParams &p, bool lam, int mode, dim3 grid, dim3 block,
                      cudaStream_t s) {
   if (mode == 0) {
-    if (lam) step_kernel<float, float, U, true, 0><<<grid, block, 0, s>>>(p);
-    else step_kernel<float, float, U, false, 0><<<grid, block, 0, s>>>(p);
+    if (lam) launch_pdl(step_kernel<float, float, U, true, 0>, grid, block, s, p);
+    else launch_pdl(step_kernel<float, float, U, false, 0>, grid, block, s, p);
   } else {
     if (lam) step_kernel<float, float, U, true, 1><<<grid, block, 0, s>>>(p);
     else step_kernel<float, float, U, false, 1><<<grid, block, 0, s>>>(p);

@@ -6,8 +6,8 @@ namespace lbm {
 void launch_step_f64(const StepParams &p, bool lam, int mode, dim3 grid, dim3 block,
                      cudaStream_t s) {
   if (mode == 0) {
-    if (lam) step_kernel<double, double, double, true, 0><<<grid, block, 0, s>>>(p);
-    else step_kernel<double, double, double, false, 0><<<grid, block, 0, s>>>(p);
+    if (lam) launch_pdl(step_kernel<double, double, double, true, 0>, grid, block, s, p);
+    else launch_pdl(step_kernel<double, double, double, false, 0>, grid, block, s, p);
   } else {
     if (lam) step_kernel<double, double, double, true, 1><<<grid, block, 0, s>>>(p);
     else step_kernel<double, double, double, false, 1><<<grid, block, 0, s>>>(p);
