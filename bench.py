@@ -109,6 +109,19 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def aggregate(elapsed_ms: float, units_per_rank: float, dist=None, device="cpu"):
+    """Whole-job throughput of independent replicas: the slowest rank's time
+    (max over ranks) and the units all ranks processed.  Returns
+    (max_elapsed_ms, units_per_second)."""
+    import torch
+    world = dist.get_world_size() if dist is not None else 1
+    t = torch.tensor([elapsed_ms], dtype=torch.float64, device=device)
+    if dist is not None:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    tmax = float(t.item())
+    return tmax, world * units_per_rank / (tmax / 1e3)
+
+
 def _dist():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -245,12 +258,9 @@ def run_gpu(args):
         barrier()
     sim.sync()
     gpu_launches = sim.kernel_launches - launches0
-    t = torch.tensor([elapsed], dtype=torch.float64, device="cuda")
-    if dist is not None:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    elapsed_max = float(t.item())
     cells_steps = w.cells * w.nsteps
-    value = world * cells_steps * args.steps / (elapsed_max / 1e3) / 1e6
+    elapsed_max, rate = aggregate(elapsed, cells_steps * args.steps, dist, "cuda")
+    value = rate / 1e6
 
     # --------------------------------------------------- end to end (host buffers)
     rho0, lam, mu = (np.ascontiguousarray(a) for a in (w.rho0, w.lam, w.mu))
@@ -287,10 +297,8 @@ def run_gpu(args):
         b.record(stream)
         torch.cuda.synchronize()
         e2e_ms += a.elapsed_time(b)
-    t = torch.tensor([e2e_ms], dtype=torch.float64, device="cuda")
-    if dist is not None:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    e2e_value = world * cells_steps * args.steps / (float(t.item()) / 1e3) / 1e6
+    _, e2e_rate = aggregate(e2e_ms, cells_steps * args.steps, dist, "cuda")
+    e2e_value = e2e_rate / 1e6
 
     # --------------------------------------------------- roofline of the step kernel
     peak, peak_kind = _peaks()
