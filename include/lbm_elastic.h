@@ -75,7 +75,8 @@ typedef enum {
 } lbm_status;
 
 /* Storage type of the populations.  F64 computes in FP64; the others compute
- * in FP32. */
+ * in FP32 (F16/BF16 store deviations from rest times 2^store_scale_log2,
+ * rounded to the 16-bit type at every step). */
 typedef enum { LBM_F64 = 0, LBM_F32 = 1, LBM_F16 = 2, LBM_BF16 = 3 } lbm_storage;
 
 /* Boundary kinds (Sec. 6). */
@@ -104,6 +105,9 @@ typedef struct {
                           * currently 1), 1 = one thread per cell with direct
                           * loads, 2 = TMA-staged tiles (FP32 storage only;
                           * LBM_ERR_UNSUPPORTED otherwise) */
+  int store_scale_log2;  /* 16-bit storage keeps f * 2^k (k in [-60, 60]) so
+                          * that the populations' range fits FP16; ignored
+                          * for FP32/FP64 */
 } lbm_elastic_config;
 
 /* One Ricker x Gaussian body-force source (Sec. 5).  Position in cells (may be

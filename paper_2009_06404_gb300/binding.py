@@ -60,6 +60,7 @@ class Config(ctypes.Structure):
         ("material_per_cell", ctypes.c_int),
         ("max_sources", ctypes.c_int), ("max_receivers", ctypes.c_int),
         ("max_steps_traced", ctypes.c_int), ("kernel_variant", ctypes.c_int),
+        ("store_scale_log2", ctypes.c_int),
     ]
 
 
@@ -126,12 +127,13 @@ def load_library(build_if_missing: bool = False):
 
 def make_config(nx, ny, storage="f32", tau=1.0, bc=("periodic",) * 4, sponge=(0, 0, 0, 0),
                 sponge_amax=0.0, material_per_cell=False, max_sources=16, max_receivers=256,
-                max_steps_traced=0, u_fp64=False, fs_order=0, kernel="auto") -> Config:
+                max_steps_traced=0, u_fp64=False, fs_order=0, kernel="auto",
+                store_scale_log2=0) -> Config:
     return Config(int(nx), int(ny), STORAGE[storage], int(bool(u_fp64)), float(tau),
                   BC[bc[0]], BC[bc[1]], BC[bc[2]], BC[bc[3]], *[int(s) for s in sponge],
                   float(sponge_amax), int(fs_order), int(bool(material_per_cell)),
                   int(max_sources), int(max_receivers), int(max_steps_traced),
-                  KERNEL[kernel])
+                  KERNEL[kernel], int(store_scale_log2))
 
 
 def _ptr(t) -> Optional[int]:
@@ -153,7 +155,7 @@ class ElasticLBM:
     def __init__(self, nx, ny, storage="f32", tau=1.0, bc=("periodic",) * 4,
                  sponge=(0, 0, 0, 0), sponge_amax=0.0, material_per_cell=False,
                  max_sources=16, max_receivers=256, max_steps_traced=0, u_fp64=False,
-                 fs_order=0, kernel="auto", device=None, stream=None):
+                 fs_order=0, kernel="auto", store_scale_log2=0, device=None, stream=None):
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("ElasticLBM needs a CUDA device (no CPU fallback)")
@@ -161,7 +163,7 @@ class ElasticLBM:
         self.L = load_library()
         self.cfg = make_config(nx, ny, storage, tau, bc, sponge, sponge_amax, material_per_cell,
                                max_sources, max_receivers, max_steps_traced, u_fp64, fs_order,
-                               kernel)
+                               kernel, store_scale_log2)
         self.nx, self.ny = int(nx), int(ny)
         self.device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
         nbytes = self.L.lbm_elastic_workspace_bytes(ctypes.byref(self.cfg))
@@ -365,15 +367,15 @@ def moment_sums_noalloc(f9, u2, storage="f64", u_fp64=False, nx=None, out=None,
 
 
 def from_workload(w, storage=None, max_steps_traced=None, u_fp64=False, device=None,
-                  stream=None, kernel="auto") -> ElasticLBM:
+                  stream=None, kernel="auto", store_scale_log2=0) -> ElasticLBM:
     """An ElasticLBM set up from a :class:`workloads.Workload`."""
     sim = ElasticLBM(w.nx, w.ny, storage=storage or w.storage, tau=w.tau, bc=tuple(w.bc),
                      sponge=tuple(w.sponge), sponge_amax=w.sponge_amax,
                      material_per_cell=w.per_cell, max_sources=max(1, len(w.sources)),
                      max_receivers=max(1, len(w.receivers)),
                      max_steps_traced=w.nsteps if max_steps_traced is None else max_steps_traced,
-                     u_fp64=u_fp64, fs_order=w.fs_order, kernel=kernel, device=device,
-                     stream=stream)
+                     u_fp64=u_fp64, fs_order=w.fs_order, kernel=kernel,
+                     store_scale_log2=store_scale_log2, device=device, stream=stream)
     if w.rho0 is not None:
         sim.set_material(w.rho0, w.lam, w.mu)
     if len(w.sources):

@@ -48,7 +48,8 @@ bool config_ok(const lbm_elastic_config *c, std::string *why) {
   if (c->nx < 3 || c->ny < 3) return bad("nx and ny must be >= 3");
   {
     // 32-bit element offsets inside the kernels: 9 planes of the padded grid
-    const long long per_line = c->storage == LBM_F64 ? 16 : 32;
+    const long long per_line =
+        c->storage == LBM_F64 ? 16 : (c->storage == LBM_F32 ? 32 : 64);
     const long long pitch = (c->nx + per_line - 1) / per_line * per_line;
     if (c->ny > 500000 || 9 * pitch * c->ny >= (1LL << 31)) return bad("grid too large");
   }
@@ -71,9 +72,9 @@ bool config_ok(const lbm_elastic_config *c, std::string *why) {
     return bad("free_surface_order must be 0 or 1");
   if (c->max_sources < 0 || c->max_receivers < 0 || c->max_steps_traced < 0)
     return bad("capacities must be >= 0");
-  if (c->storage == LBM_F16 || c->storage == LBM_BF16)
-    return bad("FP16/BF16 storage is not built in this library version");
   if (c->kernel_variant < 0 || c->kernel_variant > 2) return bad("unknown kernel_variant");
+  if (c->store_scale_log2 < -60 || c->store_scale_log2 > 60)
+    return bad("store_scale_log2 must lie in [-60, 60]");
   return true;
 }
 
@@ -159,31 +160,47 @@ __global__ void fill_kernel(C *p, long long n, C v) {
     p[k] = v;
 }
 
+template <class T> __device__ __forceinline__ double to_d(T v) { return (double)v; }
+template <> __device__ __forceinline__ double to_d<__half>(__half v) {
+  return (double)__half2float(v);
+}
+template <> __device__ __forceinline__ double to_d<__nv_bfloat16>(__nv_bfloat16 v) {
+  return (double)__bfloat162float(v);
+}
+template <class T> __device__ __forceinline__ T from_d(double v) { return T(v); }
+template <> __device__ __forceinline__ __half from_d<__half>(double v) {
+  return __double2half(v);
+}
+template <> __device__ __forceinline__ __nv_bfloat16 from_d<__nv_bfloat16>(double v) {
+  return __double2bfloat16(v);
+}
+
 // State <-> dense FP64 rows [row0, row0 + nrows).  dst/src planes are
 // [nplanes][rows][nx] with a plane stride of dplane elements.
 template <class T>
 __global__ void to_f64_kernel(const T *s, long long splane, int pitch, int nx, int row0,
-                              int nrows, int nplanes, double *d, long long dplane) {
+                              int nrows, int nplanes, double *d, long long dplane,
+                              double scale) {
   const long long n = (long long)nrows * nx;
   for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n * nplanes;
        k += (long long)gridDim.x * blockDim.x) {
     const int pl = (int)(k / n);
     const long long r = k % n;
     const long long y = row0 + r / nx, x = r % nx;
-    d[pl * dplane + r] = (double)s[pl * splane + y * pitch + x];
+    d[pl * dplane + r] = to_d<T>(s[pl * splane + y * pitch + x]) * scale;
   }
 }
 
 template <class T>
 __global__ void from_f64_kernel(T *s, long long splane, int pitch, int nx, int row0, int nrows,
-                                int nplanes, const double *d, long long dplane) {
+                                int nplanes, const double *d, long long dplane, double scale) {
   const long long n = (long long)nrows * nx;
   for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n * nplanes;
        k += (long long)gridDim.x * blockDim.x) {
     const int pl = (int)(k / n);
     const long long r = k % n;
     const long long y = row0 + r / nx, x = r % nx;
-    s[pl * splane + y * pitch + x] = T(d ? d[pl * dplane + r] : 0.0);
+    s[pl * splane + y * pitch + x] = from_d<T>(d ? d[pl * dplane + r] * scale : 0.0);
   }
 }
 
@@ -208,7 +225,8 @@ __device__ void block_reduce7(double *v, double *out) {
 template <class T, class U>
 __global__ void __launch_bounds__(kRedThreads)
     moments_partial_kernel(const T *f, const U *u, long long plane, int pitch, long long fplane,
-                           long long frow, int nx, int ny, double *partials) {
+                           long long frow, int nx, int ny, double *partials,
+                           double fscale = 1.0) {
   double v[7] = {0, 0, 0, 0, 0, 0, 0};
   const long long n = (long long)nx * ny;
   for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n;
@@ -217,7 +235,7 @@ __global__ void __launch_bounds__(kRedThreads)
     const long long cf = (k / nx) * frow + k % nx;
     double q[9];
 #pragma unroll
-    for (int i = 0; i < 9; ++i) q[i] = (double)f[i * fplane + cf];
+    for (int i = 0; i < 9; ++i) q[i] = to_d<T>(f[i * fplane + cf]) * fscale;
     v[0] += q[0] + q[1] + q[2] + q[3] + q[4] + q[5] + q[6] + q[7] + q[8];
     v[1] += q[1] - q[3] + q[5] - q[6] - q[7] + q[8];
     v[2] += q[2] - q[4] + q[5] + q[6] - q[7] - q[8];
@@ -312,6 +330,11 @@ lbm_status sync_flags(lbm_elastic_t *h) {
   return LBM_OK;
 }
 
+double store_scale(const lbm_elastic_config &c) {
+  return (c.storage == LBM_F16 || c.storage == LBM_BF16) ? std::ldexp(1.0, c.store_scale_log2)
+                                                         : 1.0;
+}
+
 StepParams base_params(lbm_elastic_t *h) {
   const lbm_elastic_config &c = h->cfg;
   const Layout &L = h->L;
@@ -346,6 +369,8 @@ StepParams base_params(lbm_elastic_t *h) {
     p.spA[s] = a;
     p.spA_f[s] = (float)a;
   }
+  p.scale_f = (float)store_scale(c);
+  p.iscale_f = (float)(1.0 / store_scale(c));
   p.omega = 1.0 / c.tau;
   p.fcoef = 1.0 - 1.0 / (2.0 * c.tau);
   p.omega_f = (float)p.omega;
@@ -383,14 +408,20 @@ lbm_status launch_step(lbm_elastic_t *h, const StepParams &p, int mode, int rows
   dim3 grid((h->cfg.nx + kBX - 1) / kBX, (rows + kBY - 1) / kBY);
   if (h->cfg.storage == LBM_F64)
     launch_step_f64(p, h->lambda_nonzero, mode, grid, block, h->stream);
-  else
+  else if (h->cfg.storage == LBM_F32)
     launch_step_f32(p, h->lambda_nonzero, h->cfg.u_fp64 != 0, mode, grid, block, h->stream);
+  else
+    launch_step_16(p, h->cfg.storage == LBM_BF16, h->lambda_nonzero, h->cfg.u_fp64 != 0, mode,
+                   grid, block, h->stream);
   return check_launch(h, "step kernel launch");
 }
 
 template <class T>
 lbm_status state_io(lbm_elastic_t *h, T *planes, long long splane, int srow, int nplanes,
-                    double *dst, const double *src, int on_device, long long dense_plane) {
+                    double *dst, const double *src, int on_device, long long dense_plane,
+                    double scale = 1.0) {
+  // dst receives stored values / scale; src values are stored times scale
+  const double iscale = 1.0 / scale;
   // dst (to f64) or src (from f64): [nplanes][ny][nx]
   const lbm_elastic_config &c = h->cfg;
   const Layout &L = h->L;
@@ -398,10 +429,12 @@ lbm_status state_io(lbm_elastic_t *h, T *planes, long long splane, int srow, int
     const long long n = (long long)c.nx * c.ny * nplanes;
     if (dst)
       to_f64_kernel<T><<<grid1d(n, 256), 256, 0, h->stream>>>(planes, splane, srow, c.nx, 0,
-                                                               c.ny, nplanes, dst, dense_plane);
+                                                               c.ny, nplanes, dst, dense_plane,
+                                                               iscale);
     else
       from_f64_kernel<T><<<grid1d(n, 256), 256, 0, h->stream>>>(planes, splane, srow, c.nx, 0,
-                                                                 c.ny, nplanes, src, dense_plane);
+                                                                 c.ny, nplanes, src, dense_plane,
+                                                                 scale);
     return check_launch(h, "state conversion launch");
   }
   double *stage = at<double>(h, L.stage);
@@ -411,7 +444,7 @@ lbm_status state_io(lbm_elastic_t *h, T *planes, long long splane, int srow, int
     const long long n = chunk * nplanes;
     if (dst) {
       to_f64_kernel<T><<<grid1d(n, 256), 256, 0, h->stream>>>(planes, splane, srow, c.nx, r0,
-                                                               nr, nplanes, stage, chunk);
+                                                               nr, nplanes, stage, chunk, iscale);
       lbm_status s = check_launch(h, "state conversion launch");
       if (s) return s;
       for (int pl = 0; pl < nplanes; ++pl)
@@ -425,7 +458,7 @@ lbm_status state_io(lbm_elastic_t *h, T *planes, long long splane, int srow, int
                                       src + pl * dense_plane + (long long)r0 * c.nx,
                                       chunk * sizeof(double), cudaMemcpyHostToDevice, h->stream));
       from_f64_kernel<T><<<grid1d(n, 256), 256, 0, h->stream>>>(
-          planes, splane, srow, c.nx, r0, nr, nplanes, src ? stage : nullptr, chunk);
+          planes, splane, srow, c.nx, r0, nr, nplanes, src ? stage : nullptr, chunk, scale);
       lbm_status s = check_launch(h, "state conversion launch");
       if (s) return s;
     }
@@ -438,6 +471,13 @@ lbm_status state_io(lbm_elastic_t *h, T *planes, long long splane, int srow, int
 lbm_status f_io(lbm_elastic_t *h, double *dst, const double *src, int on_device) {
   void *f = h->ws + h->L.f[h->cur];
   const long long dp = (long long)h->cfg.nx * h->cfg.ny;
+  const double sc = store_scale(h->cfg);
+  if (h->cfg.storage == LBM_F16)
+    return state_io<__half>(h, (__half *)f, h->L.fplane, (int)h->L.frow, 9, dst, src, on_device,
+                            dp, sc);
+  if (h->cfg.storage == LBM_BF16)
+    return state_io<__nv_bfloat16>(h, (__nv_bfloat16 *)f, h->L.fplane, (int)h->L.frow, 9, dst,
+                                   src, on_device, dp, sc);
   if (h->cfg.storage == LBM_F64)
     return state_io<double>(h, (double *)f, h->L.fplane, (int)h->L.frow, 9, dst, src, on_device,
                             dp);
@@ -896,7 +936,7 @@ lbm_status lbm_elastic_save(lbm_elastic_t *h, void *buf, int on_device) {
   if (!h) return LBM_ERR_ARG;
   if (!buf) return fail(h, LBM_ERR_ARG, "buffer is NULL");
   long long hdr[8] = {(long long)kMagic, h->cfg.nx, h->cfg.ny, h->cfg.storage,
-                      (long long)h->L.usize, h->step, 0, 0};
+                      (long long)h->L.usize, h->step, h->cfg.store_scale_log2, 0};
   char *b = (char *)buf;
   const cudaMemcpyKind k = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
   const size_t fb = 9 * (size_t)h->L.plane * h->L.tsize;
@@ -922,7 +962,8 @@ lbm_status lbm_elastic_load(lbm_elastic_t *h, const void *buf, int on_device) {
     memcpy(hdr, b, sizeof(hdr));
   }
   if (hdr[0] != (long long)kMagic || hdr[1] != h->cfg.nx || hdr[2] != h->cfg.ny ||
-      hdr[3] != h->cfg.storage || hdr[4] != (long long)h->L.usize || hdr[5] < 0)
+      hdr[3] != h->cfg.storage || hdr[4] != (long long)h->L.usize || hdr[5] < 0 ||
+      hdr[6] != h->cfg.store_scale_log2)
     return fail(h, LBM_ERR_ARG, "checkpoint does not match this configuration");
   const cudaMemcpyKind k = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
   const size_t fb = 9 * (size_t)h->L.plane * h->L.tsize;
@@ -943,7 +984,25 @@ lbm_status lbm_elastic_moment_sums(lbm_elastic_t *h, double out[7]) {
   double *partials = at<double>(h, L.partials);
   const void *f = h->ws + L.f[h->cur];
   const void *u = h->ws + L.u;
-  if (h->cfg.storage == LBM_F64)
+  const double isc = 1.0 / store_scale(h->cfg);
+  if (h->cfg.storage == LBM_F16 || h->cfg.storage == LBM_BF16) {
+    if (h->cfg.storage == LBM_F16 && L.usize == 8)
+      moments_partial_kernel<__half, double><<<kRedBlocks, kRedThreads, 0, h->stream>>>(
+          (const __half *)f, (const double *)u, L.plane, L.pitch, L.fplane, L.frow, h->cfg.nx,
+          h->cfg.ny, partials, isc);
+    else if (h->cfg.storage == LBM_F16)
+      moments_partial_kernel<__half, float><<<kRedBlocks, kRedThreads, 0, h->stream>>>(
+          (const __half *)f, (const float *)u, L.plane, L.pitch, L.fplane, L.frow, h->cfg.nx,
+          h->cfg.ny, partials, isc);
+    else if (L.usize == 8)
+      moments_partial_kernel<__nv_bfloat16, double><<<kRedBlocks, kRedThreads, 0, h->stream>>>(
+          (const __nv_bfloat16 *)f, (const double *)u, L.plane, L.pitch, L.fplane, L.frow,
+          h->cfg.nx, h->cfg.ny, partials, isc);
+    else
+      moments_partial_kernel<__nv_bfloat16, float><<<kRedBlocks, kRedThreads, 0, h->stream>>>(
+          (const __nv_bfloat16 *)f, (const float *)u, L.plane, L.pitch, L.fplane, L.frow,
+          h->cfg.nx, h->cfg.ny, partials, isc);
+  } else if (h->cfg.storage == LBM_F64)
     moments_partial_kernel<double, double><<<kRedBlocks, kRedThreads, 0, h->stream>>>(
         (const double *)f, (const double *)u, L.plane, L.pitch, L.fplane, L.frow, h->cfg.nx,
         h->cfg.ny, partials);

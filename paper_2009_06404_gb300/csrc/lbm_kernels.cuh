@@ -46,6 +46,7 @@ struct StepParams {
   int nx, ny, pitch; // pitch: elements between rows of those arrays
   int fplane, frow;  // populations: elements between planes i and i+1, rows y and y+1
   int finter;        // 1: rows of the nine planes interleaved (frow = 9 fplane)
+  float scale_f, iscale_f;  // 16-bit storage keeps populations times scale_f (2^k)
   int bc_top, bc_bottom, bc_left, bc_right;
   int sp_top, sp_bottom, sp_left, sp_right;
   int fs_order;      // free-surface extrapolation: 1 linear, 0 constant
@@ -111,6 +112,20 @@ template <> __device__ __forceinline__ void st<__nv_bfloat16, float>(__nv_bfloat
   *p = __float2bfloat16_rn(v);
 }
 
+// Population loads and stores through the storage scale: 16-bit storage keeps
+// f * 2^k (an exact power of two, so scaling adds no rounding); wider types
+// are stored as they are.
+template <class T, class C>
+__device__ __forceinline__ C ldp(const T *ptr, const StepParams &p) {
+  if (sizeof(T) == 2) return ld<T, C>(ptr) * C(p.iscale_f);
+  return ld<T, C>(ptr);
+}
+template <class T, class C>
+__device__ __forceinline__ void stp(T *ptr, C v, const StepParams &p) {
+  if (sizeof(T) == 2) st<T, C>(ptr, v * C(p.scale_f));
+  else st<T, C>(ptr, v);
+}
+
 // ------------------------------------------------------------ wall rules
 
 // Moments rho and the diagonal stress components of the post-collision
@@ -122,7 +137,7 @@ __device__ void cell_rho_pdiag(const StepParams &p, const T *f, int x, int y, C 
   const int c = y * p.frow + x;
   C v[9];
 #pragma unroll
-  for (int i = 0; i < 9; ++i) v[i] = ld<T, C>(f + i * p.fplane + c);
+  for (int i = 0; i < 9; ++i) v[i] = ldp<T, C>(f + i * p.fplane + c, p);
   rho = v[0] + v[1] + v[2] + v[3] + v[4] + v[5] + v[6] + v[7] + v[8];
   pxx = v[1] + v[3] + v[5] + v[6] + v[7] + v[8];
   pyy = v[2] + v[4] + v[5] + v[6] + v[7] + v[8];
@@ -137,7 +152,7 @@ template <class T, class C>
 __device__ C wall_value(const StepParams &p, const T *f, int bc, int nxo, int nyo, int i,
                         int x, int y) {
   const int k = oppd(i);
-  const C fk = ld<T, C>(f + k * p.fplane + y * p.frow + x);
+  const C fk = ldp<T, C>(f + k * p.fplane + y * p.frow + x, p);
   if (bc == BC_RIGID) return fk;
   C rb, pxxb, pyyb, ri, pxxi, pyyi;
   cell_rho_pdiag<T, C>(p, f, x, y, rb, pxxb, pyyb);
@@ -181,7 +196,7 @@ __device__ __noinline__ C pull_general(const StepParams &p, const T *f, int i, i
       return wall_value<T, C>(p, f, p.bc_right, 1, 0, i, x, y);
     }
   }
-  return ld<T, C>(f + i * p.fplane + sy * p.frow + sx);
+  return ldp<T, C>(f + i * p.fplane + sy * p.frow + sx, p);
 }
 
 // All nine streamed populations of (x, y).
@@ -190,7 +205,7 @@ __device__ __forceinline__ void gather(const StepParams &p, const T *f, int x, i
   if (x > 0 && x < p.nx - 1 && y > 0 && y < p.ny - 1) {
     const T *b = f + (y * p.frow + x);
 #pragma unroll
-    for (int i = 0; i < 9; ++i) fo[i] = ld<T, C>(b + (i * p.fplane - cyd(i) * p.frow - cxd(i)));
+    for (int i = 0; i < 9; ++i) fo[i] = ldp<T, C>(b + (i * p.fplane - cyd(i) * p.frow - cxd(i)), p);
   } else {
 #pragma unroll
     for (int i = 0; i < 9; ++i) fo[i] = pull_general<T, C>(p, f, i, x, y);
@@ -341,7 +356,7 @@ __device__ __forceinline__ C rho_direct(const StepParams &p, const T *f, int x, 
   const T *b = f + (y * p.frow + x);
   C r = C(0);
 #pragma unroll
-  for (int i = 0; i < 9; ++i) r += ld<T, C>(b + (i * p.fplane - cyd(i) * p.frow - cxd(i)));
+  for (int i = 0; i < 9; ++i) r += ldp<T, C>(b + (i * p.fplane - cyd(i) * p.frow - cxd(i)), p);
   return r;
 }
 
@@ -478,7 +493,7 @@ __device__ __forceinline__ void finish_cell(const StepParams &p, const C *f, C g
   const int c = y * p.pitch + x;
   T *fout = (T *)p.fout + (y * p.frow + x);
 #pragma unroll
-  for (int i = 0; i < 9; ++i) st<T, C>(fout + i * p.fplane, fs[i]);
+  for (int i = 0; i < 9; ++i) stp<T, C>(fout + i * p.fplane, fs[i], p);
   U *u = (U *)p.u;
   const U vx = U(jx * irho), vy = U(jy * irho);
   const U ux = (UIN ? ux0 : u[c]) + vx, uy = (UIN ? uy0 : u[p.plane + c]) + vy;
@@ -567,7 +582,7 @@ __device__ __noinline__ void general_cell(const StepParams &p, int x, int y, int
   {
     const T *b = fin + (yc * p.frow + xc);
 #pragma unroll
-    for (int i = 0; i < 9; ++i) f[i] = ld<T, C>(b + (i * p.fplane - cyd(i) * p.frow - cxd(i)));
+    for (int i = 0; i < 9; ++i) f[i] = ldp<T, C>(b + (i * p.fplane - cyd(i) * p.frow - cxd(i)), p);
   }
   const U *u = (const U *)p.u;
   const int c = yc * p.pitch + xc;
@@ -647,7 +662,7 @@ __global__ void __launch_bounds__(256, LBM_STEP_MIN_BLOCKS) step_kernel(const St
   {
     const T *b = fin + (y * p.frow + x);
 #pragma unroll
-    for (int i = 0; i < 9; ++i) f[i] = ld<T, C>(b + (i * p.fplane - cyd(i) * p.frow - cxd(i)));
+    for (int i = 0; i < 9; ++i) f[i] = ldp<T, C>(b + (i * p.fplane - cyd(i) * p.frow - cxd(i)), p);
   }
   const int c = y * p.pitch + x;
   U *u = (U *)p.u;
@@ -695,7 +710,7 @@ __global__ void __launch_bounds__(256, LBM_STEP_MIN_BLOCKS) step_kernel(const St
   collide_cell<C>(M, jx, jy, Sx, Sy, par<C>(p.omega, p.omega_f), par<C>(p.fcoef, p.fcoef_f), fs);
   T *fout = (T *)p.fout + (y * p.frow + x);
 #pragma unroll
-  for (int i = 0; i < 9; ++i) st<T, C>(fout + i * p.fplane, fs[i]);
+  for (int i = 0; i < 9; ++i) stp<T, C>(fout + i * p.fplane, fs[i], p);
   u[c] = ux0 + U(jx * irho);
   u[p.plane + c] = uy0 + U(jy * irho);
   if (!((M.rho + jx + jy) * C(0) == C(0))) atomicOr(p.err, 1);
@@ -706,6 +721,8 @@ void launch_step_f64(const StepParams &p, bool lam, int mode, dim3 grid, dim3 bl
                      cudaStream_t s);
 void launch_step_f32(const StepParams &p, bool lam, bool u64, int mode, dim3 grid, dim3 block,
                      cudaStream_t s);
+void launch_step_16(const StepParams &p, bool bf16, bool lam, bool u64, int mode, dim3 grid,
+                    dim3 block, cudaStream_t s);
 
 // Launches kernel k with programmatic stream serialization when LBM_PDL is
 // set (the kernel then starts with griddepcontrol.wait), else plainly.

@@ -410,3 +410,70 @@ def test_tma_kernel_equals_simple_kernel_layered(nu):
 def test_tma_kernel_needs_fp32():
     with pytest.raises(_pkg().LBMError):
         _pkg().ElasticLBM(64, 32, storage="f64", kernel="tma")
+
+
+# ------------------------------------------------------------ 16-bit storage
+
+TOL_16 = {"f16": 3e-3, "bf16": 3e-2}  # a few roundings at 2^-11 and 2^-8
+
+
+@pytest.mark.parametrize("storage,k", [("f16", 10), ("bf16", 0)])
+@pytest.mark.parametrize("bcname", ["periodic", "halfspace_sponges", "free_box", "rigid_box"])
+def test_16bit_storage_random_state(storage, k, bcname):
+    """FP16/BF16 population storage (deviations from rest times 2^k, FP32
+    arithmetic): five steps from a random state on a 70 x 45 grid match the
+    FP64 oracle to a few 16-bit roundings."""
+    bc, sponge = BCS[bcname]
+    nx, ny = 70, 45
+    rng = np.random.default_rng(11)
+    nu_rows = rng.uniform(0.15, 0.33, size=ny)
+    w = _random_case(nx, ny, bc, sponge, nu_rows, False, 3, storage)
+    fs0, u0 = _wl().random_state(nx, ny, seed=5)
+    sim = _pkg().from_workload(w, store_scale_log2=k)
+    sim.set_state(fs0, u0, step=3)
+    sim.step(w.nsteps)
+    fs, u = sim.get_state()
+    prob = oracle_problem(w)
+    st, _ = oracle.run(prob, w.nsteps, oracle.State(prob, fs=fs0, u=u0, n=3), traces=False)
+    assert max_rel(fs, st.fs) <= TOL_16[storage]
+    assert max_rel(u, st.u) <= TOL_16[storage]
+
+
+@pytest.mark.parametrize("storage,k,tol", [("f16", 10, 2e-3), ("bf16", 0, 5e-2)])
+def test_16bit_halfspace_traces_first_1000_steps(storage, k, tol):
+    """The full half-space with 16-bit storage: surface traces of the first
+    1000 steps against the stored oracle samples (measured: FP16 5.5e-4,
+    BF16 1.8e-2 rel-L2)."""
+    g = np.load(os.path.join(ROOT, "tests", "golden", "halfspace_2048x1024_4000.npz"))
+    w = _wl().halfspace(nsteps=1000, storage=storage)
+    sim = _pkg().from_workload(w, store_scale_log2=k, max_steps_traced=1000)
+    sim.step(1000)
+    ss, rs = int(g["step_stride"]), int(g["rec_stride"])
+    tr = sim.read_traces()[ss - 1::ss, ::rs, :]
+    assert rel_l2(tr, g["traces"][:tr.shape[0]]) <= tol
+
+
+@pytest.mark.parametrize("storage,k", [("f16", 7), ("bf16", 0)])
+def test_16bit_checkpoint_and_sums(storage, k):
+    wl = _wl()
+    w = wl.layered_halfspace(140, 60, 20, seed=2, sponge=8, nrec=4, storage=storage)
+    sim = _pkg().from_workload(w, store_scale_log2=k)
+    sim.step(10)
+    ck = sim.save()
+    sim.step(10)
+    a, ua = sim.get_state()
+    sim.load(ck)
+    sim.step(10)
+    b, ub = sim.get_state()
+    assert np.array_equal(a, b) and np.array_equal(ua, ub)
+    m = sim.moment_sums()
+    cx = np.array([0, 1, 0, -1, 0, 1, -1, -1, 1])
+    cy = np.array([0, 0, 1, 0, -1, 1, 1, -1, -1])
+    want = [b.sum(), np.einsum("iyx,i->", b, cx), np.einsum("iyx,i->", b, cy),
+            np.einsum("iyx,i->", b, cx * cx), np.einsum("iyx,i->", b, cx * cy),
+            np.einsum("iyx,i->", b, cy * cy), (ub ** 2).sum()]
+    np.testing.assert_allclose(m, want, rtol=1e-10, atol=1e-12)
+    # a checkpoint of another scale does not load
+    other = _pkg().from_workload(w, store_scale_log2=k + 1)
+    with pytest.raises(_pkg().LBMError):
+        other.load(ck)
