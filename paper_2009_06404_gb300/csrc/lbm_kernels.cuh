@@ -219,43 +219,44 @@ __device__ C rho_at(const StepParams &p, const T *f, int x, int y) {
   return v[0] + v[1] + v[2] + v[3] + v[4] + v[5] + v[6] + v[7] + v[8];
 }
 
-// Centred density gradient (Eq. 10) with wall ghosts: free surface
-// 2 rho_b - rho_in (linear extrapolation) or rho_b (constant), rigid wall
-// rho_b; periodic axes wrap.
+// Streamed density at grid coordinate (x, y) with periodic axes wrapped;
+// zero beyond a non-periodic edge (the wall rules below replace it there).
+template <class T, class C>
+__device__ C rho_wrapped(const StepParams &p, const T *f, int x, int y) {
+  if (x < 0 || x >= p.nx) {
+    if (p.bc_left != BC_PERIODIC) return C(0);
+    x = ((x % p.nx) + p.nx) % p.nx;
+  }
+  if (y < 0 || y >= p.ny) {
+    if (p.bc_top != BC_PERIODIC) return C(0);
+    y = ((y % p.ny) + p.ny) % p.ny;
+  }
+  return rho_at<T, C>(p, f, x, y);
+}
+
+// Ghost densities of the centred gradient (Eq. 10) on a non-periodic edge of
+// one axis: free surface 2 rho_b - rho_in (linear extrapolation) or rho_b
+// (constant), rigid wall rho_b.  lo / hi: the cell is the first / last of
+// the axis; rm, rp: the neighbours' densities (zero beyond the edge).
+__device__ __forceinline__ bool edge_linear(const StepParams &p, int bc) {
+  return bc == BC_FREE && p.fs_order == 1;
+}
+template <class C>
+__device__ __forceinline__ void wall_ghosts(const StepParams &p, bool lo, bool hi, int bc_lo,
+                                            int bc_hi, C rho, C &rm, C &rp) {
+  if (bc_lo == BC_PERIODIC) return;
+  if (lo) rm = edge_linear(p, bc_lo) ? C(2) * rho - rp : rho;
+  if (hi) rp = edge_linear(p, bc_hi) ? C(2) * rho - rm : rho;
+}
+
+// Centred density gradient (Eq. 10) of one cell from its neighbours'
+// streamed densities, with the wall ghosts on non-periodic edges.
 template <class T, class C>
 __device__ void grad_rho(const StepParams &p, const T *f, int x, int y, C rho, C &gx, C &gy) {
-  C rxm, rxp, rym, ryp;
-  // x direction
-  {
-    const bool lo = x == 0, hi = x == p.nx - 1;
-    int xm = x - 1, xp = x + 1;
-    if (p.bc_left == BC_PERIODIC) {
-      if (lo) xm = p.nx - 1;
-      if (hi) xp = 0;
-    }
-    rxp = (hi && p.bc_left != BC_PERIODIC) ? C(0) : rho_at<T, C>(p, f, xp, y);
-    rxm = (lo && p.bc_left != BC_PERIODIC) ? C(0) : rho_at<T, C>(p, f, xm, y);
-    const bool lin = p.fs_order == 1;
-    if (lo && p.bc_left != BC_PERIODIC)
-      rxm = (p.bc_left == BC_FREE && lin) ? C(2) * rho - rxp : rho;
-    if (hi && p.bc_right != BC_PERIODIC)
-      rxp = (p.bc_right == BC_FREE && lin) ? C(2) * rho - rxm : rho;
-  }
-  {
-    const bool lo = y == 0, hi = y == p.ny - 1;
-    int ym = y - 1, yp = y + 1;
-    if (p.bc_top == BC_PERIODIC) {
-      if (lo) ym = p.ny - 1;
-      if (hi) yp = 0;
-    }
-    ryp = (hi && p.bc_top != BC_PERIODIC) ? C(0) : rho_at<T, C>(p, f, x, yp);
-    rym = (lo && p.bc_top != BC_PERIODIC) ? C(0) : rho_at<T, C>(p, f, x, ym);
-    const bool lin = p.fs_order == 1;
-    if (lo && p.bc_top != BC_PERIODIC)
-      rym = (p.bc_top == BC_FREE && lin) ? C(2) * rho - ryp : rho;
-    if (hi && p.bc_bottom != BC_PERIODIC)
-      ryp = (p.bc_bottom == BC_FREE && lin) ? C(2) * rho - rym : rho;
-  }
+  C rxm = rho_wrapped<T, C>(p, f, x - 1, y), rxp = rho_wrapped<T, C>(p, f, x + 1, y);
+  C rym = rho_wrapped<T, C>(p, f, x, y - 1), ryp = rho_wrapped<T, C>(p, f, x, y + 1);
+  wall_ghosts<C>(p, x == 0, x == p.nx - 1, p.bc_left, p.bc_right, rho, rxm, rxp);
+  wall_ghosts<C>(p, y == 0, y == p.ny - 1, p.bc_top, p.bc_bottom, rho, rym, ryp);
   gx = C(0.5) * (rxp - rxm);
   gy = C(0.5) * (ryp - rym);
 }
@@ -562,19 +563,18 @@ __device__ __forceinline__ bool block_is_special(const StepParams &p, int x0, in
   return __ballot_sync(0xffffffffu, hit) != 0u;
 }
 
-// Full update of one cell with every feature (walls, layers, sources,
-// receivers): the path of blocks that are special, kept out of line so the
-// bulk path carries none of its registers.
-template <class T, class C, class U, bool LAM, int MODE>
+// Full update of one cell without the gradient force but with every other
+// feature (walls, sources, receivers): the path of blocks that are special,
+// kept out of line so the bulk path carries none of its registers.
+template <class T, class C, class U, int MODE>
 __device__ __noinline__ void general_cell(const StepParams &p, int x, int y, int yend) {
-  const int m = LAM ? 2 : 1;
   const bool active = x < p.nx && y < yend;
   const int xc = x < p.nx ? x : p.nx - 1;
   const int yc = y < yend ? y : yend - 1;
   C Fx, Fy;
   body_force<C>(p, xc, yc, Fx, Fy);  // all lanes of the warp take part
-  if (!(xc >= m && xc < p.nx - m && yc >= m && yc < p.ny - m)) {
-    boundary_cell<T, C, U, LAM, MODE>(p, Fx, Fy, x, y, xc, yc, active);
+  if (!(xc >= 1 && xc < p.nx - 1 && yc >= 1 && yc < p.ny - 1)) {
+    boundary_cell<T, C, U, false, MODE>(p, Fx, Fy, x, y, xc, yc, active);
     return;
   }
   const T *fin = (const T *)p.fin;
@@ -587,12 +587,59 @@ __device__ __noinline__ void general_cell(const StepParams &p, int x, int y, int
   const U *u = (const U *)p.u;
   const int c = yc * p.pitch + xc;
   const U ux0 = u[c], uy0 = u[p.plane + c];  // before any store
-  C gx = C(0), gy = C(0);
-  if (LAM) {
-    gx = C(0.5) * (rho_direct<T, C>(p, fin, xc + 1, yc) - rho_direct<T, C>(p, fin, xc - 1, yc));
-    gy = C(0.5) * (rho_direct<T, C>(p, fin, xc, yc + 1) - rho_direct<T, C>(p, fin, xc, yc - 1));
+  finish_cell<T, C, U, false, MODE, true>(p, f, C(0), C(0), Fx, Fy, x, y, xc, yc, active, ux0,
+                                          uy0);
+}
+
+// Ring cell t (0 <= t < 80) around a block of 32 x 8 cells, as an offset from
+// the block's first cell: the rows above and below (64 cells), then the
+// columns left and right (16).
+__device__ __forceinline__ void ring_cell(int t, int &hx, int &hy) {
+  if (t < 64) {
+    hx = t & 31;
+    hy = t < 32 ? -1 : 8;
+  } else {
+    hx = (t & 1) ? 32 : -1;
+    hy = (t - 64) >> 1;
   }
-  finish_cell<T, C, U, LAM, MODE, true>(p, f, gx, gy, Fx, Fy, x, y, xc, yc, active, ux0, uy0);
+}
+
+// Update of a block of 32 x 8 cells with the density-gradient force that
+// needs the general path (walls, periodic seams, sources, receivers).  The
+// streamed densities of the block and of the ring around it (periodic axes
+// wrapped) go to shared memory first, so a cell pulls its populations once
+// rather than once for itself and once per neighbour; the wall rules then
+// supply the ghosts on non-periodic edges.  Every thread of the block calls
+// it (one barrier).
+template <class T, class C, class U, int MODE>
+__device__ __noinline__ void general_block_lam(const StepParams &p, int x0, int y0, int yend) {
+  __shared__ C rho_s[10][34];
+  const int tx = threadIdx.x, ty = threadIdx.y, t = ty * 32 + tx;
+  const int x = x0 + tx, y = y0 + ty;
+  const bool active = x < p.nx && y < yend;
+  const int xc = x < p.nx ? x : p.nx - 1;
+  const int yc = y < yend ? y : yend - 1;
+  C Fx, Fy;
+  body_force<C>(p, xc, yc, Fx, Fy);  // all lanes of the warp take part
+  const T *fin = (const T *)p.fin;
+  C f[9];
+  gather<T, C>(p, fin, xc, yc, f);
+  const C rho = f[0] + f[1] + f[2] + f[3] + f[4] + f[5] + f[6] + f[7] + f[8];
+  // a cell of the block outside the updated range holds the density of its
+  // own (wrapped) coordinate, as a neighbour of the cells that are updated
+  rho_s[ty + 1][tx + 1] = active ? rho : rho_wrapped<T, C>(p, fin, x, y);
+  if (t < 80) {
+    int hx, hy;
+    ring_cell(t, hx, hy);
+    rho_s[hy + 1][hx + 1] = rho_wrapped<T, C>(p, fin, x0 + hx, y0 + hy);
+  }
+  __syncthreads();
+  C rxm = rho_s[ty + 1][tx], rxp = rho_s[ty + 1][tx + 2];
+  C rym = rho_s[ty][tx + 1], ryp = rho_s[ty + 2][tx + 1];
+  wall_ghosts<C>(p, xc == 0, xc == p.nx - 1, p.bc_left, p.bc_right, rho, rxm, rxp);
+  wall_ghosts<C>(p, yc == 0, yc == p.ny - 1, p.bc_top, p.bc_bottom, rho, rym, ryp);
+  finish_cell<T, C, U, true, MODE>(p, f, C(0.5) * (rxp - rxm), C(0.5) * (ryp - rym), Fx, Fy, x, y,
+                                   xc, yc, active);
 }
 
 // One thread per cell, blocks of 32 x 8 threads (a warp is 32 consecutive
@@ -618,9 +665,13 @@ __device__ __noinline__ void general_cell(const StepParams &p, int x, int y, int
 #ifndef LBM_STEP_MIN_BLOCKS
 #define LBM_STEP_MIN_BLOCKS 6
 #endif
+#ifndef LBM_STEP_MIN_BLOCKS_LAM
+#define LBM_STEP_MIN_BLOCKS_LAM 5
+#endif
 
 template <class T, class C, class U, bool LAM, int MODE>
-__global__ void __launch_bounds__(256, LBM_STEP_MIN_BLOCKS) step_kernel(const StepParams p) {
+__global__ void __launch_bounds__(256, LAM ? LBM_STEP_MIN_BLOCKS_LAM : LBM_STEP_MIN_BLOCKS)
+    step_kernel(const StepParams p) {
 #if LBM_PDL
   // programmatic dependent launch: wait for the previous step to complete
   // (its populations are this step's input), then let the next step's
@@ -650,7 +701,10 @@ __global__ void __launch_bounds__(256, LBM_STEP_MIN_BLOCKS) step_kernel(const St
   const int yend = MODE == 1 ? p.row0 + p.nrows : p.ny;
   const int m = LAM ? 2 : 1;
   if (MODE == 1 || block_is_special(p, x0, y0, blockDim.y, m)) {
-    general_cell<T, C, U, LAM, MODE>(p, x, y, yend);
+    // the same for every thread of the block (block_is_special depends on
+    // the block's position only)
+    if (LAM) general_block_lam<T, C, U, MODE>(p, x0, y0, yend);
+    else general_cell<T, C, U, MODE>(p, x, y, yend);
     return;
   }
   // bulk cell: every upstream cell (and every neighbour's) is inside the
@@ -664,6 +718,20 @@ __global__ void __launch_bounds__(256, LBM_STEP_MIN_BLOCKS) step_kernel(const St
 #pragma unroll
     for (int i = 0; i < 9; ++i) f[i] = ldp<T, C>(b + (i * p.fplane - cyd(i) * p.frow - cxd(i)), p);
   }
+  // the first 80 threads of a block with the gradient force also pull the
+  // populations of one cell of the ring around the block: rows above and
+  // below (64), columns left and right (16).  They are loaded together with
+  // the cell's own, so both wait for one memory latency, not two.
+  const int t = threadIdx.y * 32 + threadIdx.x;
+  int hx = 0, hy = 0;
+  C hf[LAM ? 9 : 1];
+  if (LAM && t < 80) {
+    ring_cell(t, hx, hy);
+    const T *b = fin + ((y0 + hy) * p.frow + x0 + hx);
+#pragma unroll
+    for (int i = 0; i < (LAM ? 9 : 1); ++i)
+      hf[i] = ldp<T, C>(b + (i * p.fplane - cyd(i) * p.frow - cxd(i)), p);
+  }
   const int c = y * p.pitch + x;
   U *u = (U *)p.u;
   const U ux0 = u[c], uy0 = u[p.plane + c];
@@ -671,21 +739,15 @@ __global__ void __launch_bounds__(256, LBM_STEP_MIN_BLOCKS) step_kernel(const St
   const Moments<C> M = cell_moments<C>(f);
   C Gx = C(0), Gy = C(0);
   if (LAM) {
-    // streamed density of the block and a one-cell ring in shared memory
-    // (every block in this branch is bulk: the barrier is uniform)
+    // streamed density of the block and its ring in shared memory (every
+    // block in this branch is bulk: the barrier is uniform)
     __shared__ C rho_s[10][34];
     rho_s[threadIdx.y + 1][threadIdx.x + 1] = M.rho;
-    const int t = threadIdx.y * 32 + threadIdx.x;
     if (t < 80) {
-      int hx, hy;  // ring cell: rows above/below (64), columns left/right (16)
-      if (t < 64) {
-        hx = t & 31;
-        hy = t < 32 ? -1 : 8;
-      } else {
-        hx = (t & 1) ? 32 : -1;
-        hy = (t - 64) >> 1;
-      }
-      rho_s[hy + 1][hx + 1] = rho_direct<T, C>(p, fin, x0 + hx, y0 + hy);
+      C r = C(0);
+#pragma unroll
+      for (int i = 0; i < (LAM ? 9 : 1); ++i) r += hf[i];
+      rho_s[hy + 1][hx + 1] = r;
     }
     __syncthreads();
     // elastic force Lambda b^2 grad rho with the centred difference (Eqs. 9-10)
