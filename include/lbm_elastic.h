@@ -259,6 +259,92 @@ lbm_status lbm_elastic_moment_sums_noalloc(const void *f9, const void *u2, int s
                                            double *out7, int out_on_device,
                                            void *cuda_stream);
 
+
+/* ------------------------------------------------------------------------
+ * Batches: many independent grids ("shots") advanced together.
+ *
+ * A batch references existing handles (each keeps its own workspace,
+ * material, sources, receivers and traces) and advances all of them by the
+ * same number of steps with one launch per step, or with one persistent
+ * launch for many steps.  The step of every cell is the single-grid step
+ * (Sec. 2, Eq. 18, with the boundaries of Sec. 6 and the sources of Sec. 5),
+ * so a shot advanced in a batch gives the same result as the shot advanced
+ * alone.  Each step is split into tiles of 32 x rows cells of all shots;
+ * how the tiles are launched is the batch's launch configuration, which
+ * lbm_batch_autotune chooses by timing the candidates on the batch itself.
+ *
+ * Requirements: every shot has the same storage type and u_fp64 setting.
+ * The shots must not be stepped or changed by other calls while a batched
+ * call is in flight; changes made between batched calls (sources, material,
+ * receivers, state) are picked up by the next batched call.  The caller owns
+ * the batch workspace (lbm_batch_workspace_bytes, 256-byte aligned) and
+ * keeps it and the shots alive until lbm_batch_destroy.
+ * ------------------------------------------------------------------------ */
+typedef struct lbm_batch lbm_batch_t;
+
+typedef enum {
+  LBM_BATCH_AUTO = 0,       /* tune on the first lbm_batch_step of >= 64 steps */
+  LBM_BATCH_STREAM = 1,     /* one launch per step (programmatic dependent launch) */
+  LBM_BATCH_GRAPH = 2,      /* the same launches captured in a CUDA graph   */
+  LBM_BATCH_PERSISTENT = 3  /* one cooperative launch for steps_per_launch steps:
+                               blocks claim tiles from an atomic queue and meet at a
+                               grid barrier after every step */
+} lbm_batch_mode;
+
+typedef struct {
+  int mode;              /* lbm_batch_mode                                    */
+  int rows;              /* tile height: 4 or 8 (tiles are 32 cells wide)     */
+  int order;             /* 0: tiles shot by shot, row-major; 1: tiles near an
+                            edge, a source or a receiver first (the expensive
+                            ones), then the rest                               */
+  int graph_steps;       /* GRAPH: steps per captured graph, >= 1             */
+  int steps_per_launch;  /* PERSISTENT: steps per cooperative launch, >= 1    */
+  int ctas_per_sm;       /* PERSISTENT: resident blocks per SM, 0 = all that fit */
+  long long barrier_cycles; /* PERSISTENT: grid-barrier wait limit in SM clock
+                               cycles (0 = 4e9); past it the kernel stops and
+                               lbm_batch_sync returns LBM_ERR_TIMEOUT           */
+  int barrier_extra;     /* PERSISTENT, for tests of the time-out: arrivals each
+                            barrier waits for beyond the grid size (> 0: every
+                            wait runs out).  Normally 0.                        */
+} lbm_batch_launch;
+
+/* Workspace bytes for a batch of these n shots. */
+size_t lbm_batch_workspace_bytes(lbm_elastic_t *const *shots, int n);
+
+/* Creates a batch of n >= 1 shots.  d_workspace: device memory of at least
+ * lbm_batch_workspace_bytes bytes, 256-byte aligned.  cuda_stream: the
+ * stream every batched call uses (0 = legacy default).  Errors: LBM_ERR_ARG
+ * (null shot, n < 1, mixed storage types), LBM_ERR_WORKSPACE; the message is
+ * then in lbm_batch_last_error(NULL). */
+lbm_status lbm_batch_create(lbm_elastic_t *const *shots, int n, void *d_workspace, size_t bytes,
+                            void *cuda_stream, lbm_batch_t **out);
+
+/* Sets / reads the launch configuration (LBM_ERR_ARG for values outside the
+ * ranges above). */
+lbm_status lbm_batch_set_launch(lbm_batch_t *b, const lbm_batch_launch *l);
+lbm_status lbm_batch_get_launch(const lbm_batch_t *b, lbm_batch_launch *l);
+
+/* Times each candidate configuration (the three modes x rows 4, 8 x both
+ * orders) for 1 + steps_per_trial steps of the batch itself and keeps the
+ * fastest.  This ADVANCES every shot by (1 + steps_per_trial) x the number
+ * of candidates steps.  *us_per_step (may be NULL) receives the best time
+ * per step in microseconds.  Synchronises the stream. */
+lbm_status lbm_batch_autotune(lbm_batch_t *b, int steps_per_trial, double *us_per_step);
+
+/* Advances every shot by nsteps >= 0 steps (asynchronous). */
+lbm_status lbm_batch_step(lbm_batch_t *b, int nsteps);
+
+/* Synchronises the stream; reports a grid-barrier time-out (LBM_ERR_TIMEOUT)
+ * or a non-finite value met in any shot (LBM_ERR_NONFINITE). */
+lbm_status lbm_batch_sync(lbm_batch_t *b);
+
+/* Kernel launches made by batched calls so far, and cells over all shots. */
+long long lbm_batch_kernel_launches(const lbm_batch_t *b);
+long long lbm_batch_cells(const lbm_batch_t *b);
+
+lbm_status lbm_batch_destroy(lbm_batch_t *b);
+const char *lbm_batch_last_error(const lbm_batch_t *b);
+
 #ifdef __cplusplus
 }
 #endif

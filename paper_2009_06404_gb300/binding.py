@@ -35,6 +35,10 @@ SYMBOLS = [
     "lbm_elastic_load", "lbm_elastic_moment_sums", "lbm_elastic_sync",
     "lbm_elastic_destroy", "lbm_elastic_last_error", "lbm_elastic_status_string",
     "lbm_elastic_kernel_launches", "lbm_elastic_moment_sums_noalloc",
+    "lbm_batch_workspace_bytes", "lbm_batch_create", "lbm_batch_set_launch",
+    "lbm_batch_get_launch", "lbm_batch_autotune", "lbm_batch_step", "lbm_batch_sync",
+    "lbm_batch_kernel_launches", "lbm_batch_cells", "lbm_batch_destroy",
+    "lbm_batch_last_error",
 ]
 
 
@@ -62,6 +66,18 @@ class Config(ctypes.Structure):
         ("max_steps_traced", ctypes.c_int), ("kernel_variant", ctypes.c_int),
         ("store_scale_log2", ctypes.c_int),
     ]
+
+
+class BatchLaunch(ctypes.Structure):
+    _fields_ = [
+        ("mode", ctypes.c_int), ("rows", ctypes.c_int), ("order", ctypes.c_int),
+        ("graph_steps", ctypes.c_int), ("steps_per_launch", ctypes.c_int),
+        ("ctas_per_sm", ctypes.c_int), ("barrier_cycles", ctypes.c_longlong),
+        ("barrier_extra", ctypes.c_int),
+    ]
+
+
+BATCH_MODE = {"auto": 0, "stream": 1, "graph": 2, "persistent": 3}
 
 
 class Source(ctypes.Structure):
@@ -116,6 +132,18 @@ def load_library(build_if_missing: bool = False):
             "lbm_elastic_status_string": (ctypes.c_char_p, [ip]),
             "lbm_elastic_kernel_launches": (ctypes.c_longlong, [vp]),
             "lbm_elastic_moment_sums_noalloc": (ip, [vp, vp, ip, ip, ip, ip, ip, vp, ip, vp]),
+            "lbm_batch_workspace_bytes": (ctypes.c_size_t, [ctypes.POINTER(vp), ip]),
+            "lbm_batch_create": (ip, [ctypes.POINTER(vp), ip, vp, ctypes.c_size_t, vp,
+                                      ctypes.POINTER(vp)]),
+            "lbm_batch_set_launch": (ip, [vp, ctypes.POINTER(BatchLaunch)]),
+            "lbm_batch_get_launch": (ip, [vp, ctypes.POINTER(BatchLaunch)]),
+            "lbm_batch_autotune": (ip, [vp, ip, dp]),
+            "lbm_batch_step": (ip, [vp, ip]),
+            "lbm_batch_sync": (ip, [vp]),
+            "lbm_batch_kernel_launches": (ctypes.c_longlong, [vp]),
+            "lbm_batch_cells": (ctypes.c_longlong, [vp]),
+            "lbm_batch_destroy": (ip, [vp]),
+            "lbm_batch_last_error": (ctypes.c_char_p, [vp]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)
@@ -342,6 +370,99 @@ class ElasticLBM:
         out = (ctypes.c_double * 7)()
         self._check(self.L.lbm_elastic_moment_sums(self.h, out))
         return np.array(out[:])
+
+
+class Batch:
+    """Many ElasticLBM shots advanced together (one launch per step over the
+    tiles of every shot, or one persistent launch for many steps).
+
+    The shots keep their own state; after ``step`` each shot's fields, traces
+    and step index are read through the shot as usual.  All work runs on
+    ``stream`` (default: torch's current stream)."""
+
+    def __init__(self, shots: Sequence["ElasticLBM"], stream=None):
+        import torch
+        self._torch = torch
+        self.L = load_library()
+        self.shots = list(shots)
+        if not self.shots:
+            raise LBMError(-1, "a batch needs at least one shot")
+        dev = self.shots[0].device
+        arr = (ctypes.c_void_p * len(self.shots))(*[s.h.value for s in self.shots])
+        self._arr = arr
+        nbytes = self.L.lbm_batch_workspace_bytes(arr, len(self.shots))
+        if nbytes == 0:
+            raise LBMError(-1, "invalid shots")
+        with torch.cuda.device(dev):
+            self.stream = stream if stream is not None else torch.cuda.current_stream(dev)
+            self.workspace = torch.empty(nbytes + 256, dtype=torch.uint8, device=dev)
+        base = self.workspace.data_ptr()
+        off = (-base) % 256
+        h = ctypes.c_void_p()
+        st = self.L.lbm_batch_create(arr, len(self.shots), base + off, nbytes,
+                                     self.stream.cuda_stream, ctypes.byref(h))
+        if st != LBM_OK:
+            raise LBMError(st, self.L.lbm_batch_last_error(None).decode())
+        self.h = h
+
+    def _check(self, st):
+        if st == LBM_OK:
+            return st
+        msg = self.L.lbm_batch_last_error(self.h).decode()
+        if st == -5:
+            raise NonFiniteError(st, msg)
+        raise LBMError(st, msg)
+
+    def close(self):
+        if getattr(self, "h", None) is not None and self.h.value:
+            self.L.lbm_batch_destroy(self.h)
+            self.h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def launch(self) -> Dict:
+        l = BatchLaunch()
+        self._check(self.L.lbm_batch_get_launch(self.h, ctypes.byref(l)))
+        inv = {v: k for k, v in BATCH_MODE.items()}
+        return {"mode": inv[l.mode], "rows": l.rows, "order": l.order,
+                "graph_steps": l.graph_steps, "steps_per_launch": l.steps_per_launch,
+                "ctas_per_sm": l.ctas_per_sm, "barrier_cycles": l.barrier_cycles,
+                "barrier_extra": l.barrier_extra}
+
+    def set_launch(self, **kw):
+        cur = self.launch
+        cur.update(kw)
+        l = BatchLaunch(BATCH_MODE[cur["mode"]], int(cur["rows"]), int(cur["order"]),
+                        int(cur["graph_steps"]), int(cur["steps_per_launch"]),
+                        int(cur["ctas_per_sm"]), int(cur["barrier_cycles"]),
+                        int(cur["barrier_extra"]))
+        self._check(self.L.lbm_batch_set_launch(self.h, ctypes.byref(l)))
+
+    def autotune(self, steps_per_trial: int = 3) -> float:
+        """Times every launch candidate on the batch itself (this advances
+        the shots) and keeps the fastest; returns its microseconds per step."""
+        us = ctypes.c_double()
+        self._check(self.L.lbm_batch_autotune(self.h, int(steps_per_trial), ctypes.byref(us)))
+        return us.value
+
+    def step(self, nsteps: int = 1):
+        self._check(self.L.lbm_batch_step(self.h, int(nsteps)))
+
+    def sync(self):
+        self._check(self.L.lbm_batch_sync(self.h))
+
+    @property
+    def kernel_launches(self) -> int:
+        return int(self.L.lbm_batch_kernel_launches(self.h))
+
+    @property
+    def cells(self) -> int:
+        return int(self.L.lbm_batch_cells(self.h))
 
 
 def moment_sums_noalloc(f9, u2, storage="f64", u_fp64=False, nx=None, out=None,

@@ -1,0 +1,26 @@
+// Batched step, FP16 or BF16 populations with FP32 arithmetic (FP32 or FP64
+// displacement).
+#include "batch_kernels.cuh"
+
+namespace lbm {
+
+cudaError_t batch_launch_16(bool bf16, bool u64, int R, bool persistent, const BatchArgs &a,
+                            int count, int grid, bool pdl, cudaStream_t s) {
+  if (bf16) {
+    if (u64)
+      return batch_launch_r<__nv_bfloat16, float, double>(R, persistent, a, count, grid, pdl, s);
+    return batch_launch_r<__nv_bfloat16, float, float>(R, persistent, a, count, grid, pdl, s);
+  }
+  if (u64) return batch_launch_r<__half, float, double>(R, persistent, a, count, grid, pdl, s);
+  return batch_launch_r<__half, float, float>(R, persistent, a, count, grid, pdl, s);
+}
+
+int batch_occupancy_16(bool bf16, bool u64, int R) {
+  if (bf16)
+    return u64 ? batch_occupancy_r<__nv_bfloat16, float, double>(R)
+               : batch_occupancy_r<__nv_bfloat16, float, float>(R);
+  return u64 ? batch_occupancy_r<__half, float, double>(R)
+             : batch_occupancy_r<__half, float, float>(R);
+}
+
+}  // namespace lbm

@@ -11,9 +11,7 @@
 #include <string>
 #include <vector>
 
-#include "lbm_elastic.h"
-#include "lbm_kernels.cuh"
-#include "step_tma.cuh"
+#include "lbm_internal.h"
 
 using namespace lbm;
 
@@ -27,17 +25,6 @@ constexpr unsigned kMagic = 0x4c424d45u;  // checkpoint header tag
 
 size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
-struct Layout {
-  int pitch = 0;
-  long long plane = 0;
-  int finter = 1;                 // population rows interleaved ([y][i][x])
-  long long fplane = 0, frow = 0; // population strides (elements)
-  size_t tsize = 0, usize = 0, csize = 0;
-  size_t f[2] = {0, 0}, u = 0, lam = 0, irho = 0, src = 0, rec_ptr = 0, rec_xy = 0,
-         rec_id = 0, traces = 0, partials = 0, flags = 0, stage = 0, total = 0;
-  int rec_tiles_x = 0, rec_tiles = 0, stage_rows = 0;
-  long long mat_count = 0;
-};
 
 bool config_ok(const lbm_elastic_config *c, std::string *why) {
   auto bad = [&](const char *m) {
@@ -261,26 +248,6 @@ __global__ void __launch_bounds__(kRedThreads) moments_final_kernel(const double
 
 // ------------------------------------------------------------ the handle
 
-struct lbm_elastic {
-  TmaMaps maps;                // tensor maps of the TMA-staged kernel
-  bool use_tma = false;
-  int nsm = 0;                 // multiprocessors of the device
-  lbm_elastic_config cfg;
-  Layout L;
-  char *ws = nullptr;
-  cudaStream_t stream = nullptr;
-  int cur = 0;                 // buffer holding the latest post-collision state
-  long long step = 0;
-  int traced = 0;
-  int nsrc = 0, nrec = 0;
-  bool lambda_nonzero = false;
-  long long launches = 0;
-  std::vector<SourceDev> src_host;
-  int src_box[4] = {0, -1, 0, -1};  // x0, x1, y0, y1 of all source footprints
-  int rec_box[4] = {0, -1, 0, -1};  // x0, x1, y0, y1 of all receivers
-  std::string err;
-};
-
 namespace {
 
 std::string g_create_error;
@@ -404,8 +371,9 @@ StepParams base_params(lbm_elastic_t *h) {
 constexpr int kBX = 32, kBY = 8;
 
 lbm_status launch_step(lbm_elastic_t *h, const StepParams &p, int mode, int rows) {
-  dim3 block(kBX, kBY);
-  dim3 grid((h->cfg.nx + kBX - 1) / kBX, (rows + kBY - 1) / kBY);
+  const int by = h->lambda_nonzero ? kLamRows : kBY;
+  dim3 block(kBX, by);
+  dim3 grid((h->cfg.nx + kBX - 1) / kBX, (rows + by - 1) / by);
   if (h->cfg.storage == LBM_F64)
     launch_step_f64(p, h->lambda_nonzero, mode, grid, block, h->stream);
   else if (h->cfg.storage == LBM_F32)
@@ -598,6 +566,8 @@ bool setup_tma(lbm_elastic_t *h, std::string *why) {
 }  // namespace
 
 // ------------------------------------------------------------ C ABI
+
+StepParams lbm::handle_step_params(lbm_elastic_t *h) { return base_params(h); }
 
 extern "C" {
 

@@ -25,6 +25,14 @@ enum { BC_PERIODIC = 0, BC_FREE = 1, BC_RIGID = 2 };
 constexpr int kRecTileX = 64;
 constexpr int kRecTileY = 4;
 
+// Rows of the 32-wide blocks of the single-grid step with the
+// density-gradient force (the others have 8).
+#ifndef LBM_LAM_ROWS
+#define LBM_LAM_ROWS 8
+#endif
+constexpr int kLamRows = LBM_LAM_ROWS;
+static_assert(64 + 2 * kLamRows <= 32 * kLamRows, "one ring cell per thread at most");
+
 // One body-force source, prepared on the host from an lbm_source.
 struct SourceDev {
   double x, y;      // position (cells)
@@ -261,6 +269,11 @@ __device__ void grad_rho(const StepParams &p, const T *f, int x, int y, C rho, C
   gy = C(0.5) * (ryp - rym);
 }
 
+// Product rounded on its own (never fused with a following addition), so
+// that every path of the step rounds u += j / rho0 the same way.
+__device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
+
 // Scalar parameter in the compute type (FP32 kernels read the FP32 copy, so
 // no FP64 conversion runs per cell).
 template <class C> __device__ __forceinline__ C par(double d, float f);
@@ -479,8 +492,8 @@ __device__ __forceinline__ void finish_cell(const StepParams &p, const C *f, C g
     const U *u = (const U *)p.u;
     if (p.out[0]) p.out[0][o] = (double)u[c];
     if (p.out[1]) p.out[1][o] = (double)u[p.plane + c];
-    if (p.out[2]) p.out[2][o] = (double)(jx * irho);
-    if (p.out[3]) p.out[3][o] = (double)(jy * irho);
+    if (p.out[2]) p.out[2][o] = (double)mul_rn(jx, irho);
+    if (p.out[3]) p.out[3][o] = (double)mul_rn(jy, irho);
     if (p.out[4]) p.out[4][o] = (double)M.rho;
     if (p.out[5]) p.out[5][o] = (double)M.pxx;
     if (p.out[6]) p.out[6][o] = (double)M.pxy;
@@ -496,7 +509,7 @@ __device__ __forceinline__ void finish_cell(const StepParams &p, const C *f, C g
 #pragma unroll
   for (int i = 0; i < 9; ++i) stp<T, C>(fout + i * p.fplane, fs[i], p);
   U *u = (U *)p.u;
-  const U vx = U(jx * irho), vy = U(jy * irho);
+  const U vx = U(mul_rn(jx, irho)), vy = U(mul_rn(jy, irho));
   const U ux = (UIN ? ux0 : u[c]) + vx, uy = (UIN ? uy0 : u[p.plane + c]) + vy;
   u[c] = ux;
   u[p.plane + c] = uy;
@@ -591,29 +604,30 @@ __device__ __noinline__ void general_cell(const StepParams &p, int x, int y, int
                                           uy0);
 }
 
-// Ring cell t (0 <= t < 80) around a block of 32 x 8 cells, as an offset from
-// the block's first cell: the rows above and below (64 cells), then the
-// columns left and right (16).
+// Ring cell t (0 <= t < 64 + 2 R) around a block of 32 x R cells, as an
+// offset from the block's first cell: the rows above and below (64 cells),
+// then the columns left and right (2 R).
+template <int R>
 __device__ __forceinline__ void ring_cell(int t, int &hx, int &hy) {
   if (t < 64) {
     hx = t & 31;
-    hy = t < 32 ? -1 : 8;
+    hy = t < 32 ? -1 : R;
   } else {
     hx = (t & 1) ? 32 : -1;
     hy = (t - 64) >> 1;
   }
 }
 
-// Update of a block of 32 x 8 cells with the density-gradient force that
+// Update of a block of 32 x R cells with the density-gradient force that
 // needs the general path (walls, periodic seams, sources, receivers).  The
 // streamed densities of the block and of the ring around it (periodic axes
 // wrapped) go to shared memory first, so a cell pulls its populations once
 // rather than once for itself and once per neighbour; the wall rules then
 // supply the ghosts on non-periodic edges.  Every thread of the block calls
 // it (one barrier).
-template <class T, class C, class U, int MODE>
+template <class T, class C, class U, int MODE, int R>
 __device__ __noinline__ void general_block_lam(const StepParams &p, int x0, int y0, int yend) {
-  __shared__ C rho_s[10][34];
+  __shared__ C rho_s[R + 2][34];
   const int tx = threadIdx.x, ty = threadIdx.y, t = ty * 32 + tx;
   const int x = x0 + tx, y = y0 + ty;
   const bool active = x < p.nx && y < yend;
@@ -628,9 +642,9 @@ __device__ __noinline__ void general_block_lam(const StepParams &p, int x0, int 
   // a cell of the block outside the updated range holds the density of its
   // own (wrapped) coordinate, as a neighbour of the cells that are updated
   rho_s[ty + 1][tx + 1] = active ? rho : rho_wrapped<T, C>(p, fin, x, y);
-  if (t < 80) {
+  if (t < 64 + 2 * R) {
     int hx, hy;
-    ring_cell(t, hx, hy);
+    ring_cell<R>(t, hx, hy);
     rho_s[hy + 1][hx + 1] = rho_wrapped<T, C>(p, fin, x0 + hx, y0 + hy);
   }
   __syncthreads();
@@ -666,11 +680,15 @@ __device__ __noinline__ void general_block_lam(const StepParams &p, int x0, int 
 #define LBM_STEP_MIN_BLOCKS 6
 #endif
 #ifndef LBM_STEP_MIN_BLOCKS_LAM
-#define LBM_STEP_MIN_BLOCKS_LAM 5
+#define LBM_STEP_MIN_BLOCKS_LAM 6
 #endif
 
+template <class T, class C, class U, bool LAM, int MODE, int R>
+__device__ __forceinline__ void step_block(const StepParams &p, int bx, int by);
+
 template <class T, class C, class U, bool LAM, int MODE>
-__global__ void __launch_bounds__(256, LAM ? LBM_STEP_MIN_BLOCKS_LAM : LBM_STEP_MIN_BLOCKS)
+__global__ void __launch_bounds__(LAM ? 32 * kLamRows : 256,
+                                  LAM ? LBM_STEP_MIN_BLOCKS_LAM : LBM_STEP_MIN_BLOCKS)
     step_kernel(const StepParams p) {
 #if LBM_PDL
   // programmatic dependent launch: wait for the previous step to complete
@@ -694,16 +712,22 @@ __global__ void __launch_bounds__(256, LAM ? LBM_STEP_MIN_BLOCKS_LAM : LBM_STEP_
     by = gridDim.y - 1 - by;
 #endif
   }
-  const int x0 = bx * blockDim.x;
+  step_block<T, C, U, LAM, MODE, LAM ? kLamRows : 8>(p, bx, by);
+}
+
+// The update of block (bx, by) of 32 x R cells by 32 x R threads.
+template <class T, class C, class U, bool LAM, int MODE, int R>
+__device__ __forceinline__ void step_block(const StepParams &p, int bx, int by) {
+  const int x0 = bx * 32;
   const int x = x0 + threadIdx.x;
-  const int y0 = by * blockDim.y + (MODE == 1 ? p.row0 : 0);
+  const int y0 = by * R + (MODE == 1 ? p.row0 : 0);
   const int y = y0 + threadIdx.y;
   const int yend = MODE == 1 ? p.row0 + p.nrows : p.ny;
   const int m = LAM ? 2 : 1;
-  if (MODE == 1 || block_is_special(p, x0, y0, blockDim.y, m)) {
+  if (MODE == 1 || block_is_special(p, x0, y0, R, m)) {
     // the same for every thread of the block (block_is_special depends on
     // the block's position only)
-    if (LAM) general_block_lam<T, C, U, MODE>(p, x0, y0, yend);
+    if (LAM) general_block_lam<T, C, U, MODE, R>(p, x0, y0, yend);
     else general_cell<T, C, U, MODE>(p, x, y, yend);
     return;
   }
@@ -718,15 +742,15 @@ __global__ void __launch_bounds__(256, LAM ? LBM_STEP_MIN_BLOCKS_LAM : LBM_STEP_
 #pragma unroll
     for (int i = 0; i < 9; ++i) f[i] = ldp<T, C>(b + (i * p.fplane - cyd(i) * p.frow - cxd(i)), p);
   }
-  // the first 80 threads of a block with the gradient force also pull the
-  // populations of one cell of the ring around the block: rows above and
-  // below (64), columns left and right (16).  They are loaded together with
-  // the cell's own, so both wait for one memory latency, not two.
+  // the first 64 + 2 R threads of a block with the gradient force also pull
+  // the populations of one cell of the ring around the block.  They are
+  // loaded together with the cell's own, so both wait for one memory
+  // latency, not two.
   const int t = threadIdx.y * 32 + threadIdx.x;
   int hx = 0, hy = 0;
   C hf[LAM ? 9 : 1];
-  if (LAM && t < 80) {
-    ring_cell(t, hx, hy);
+  if (LAM && t < 64 + 2 * R) {
+    ring_cell<R>(t, hx, hy);
     const T *b = fin + ((y0 + hy) * p.frow + x0 + hx);
 #pragma unroll
     for (int i = 0; i < (LAM ? 9 : 1); ++i)
@@ -741,9 +765,13 @@ __global__ void __launch_bounds__(256, LAM ? LBM_STEP_MIN_BLOCKS_LAM : LBM_STEP_
   if (LAM) {
     // streamed density of the block and its ring in shared memory (every
     // block in this branch is bulk: the barrier is uniform)
-    __shared__ C rho_s[10][34];
-    rho_s[threadIdx.y + 1][threadIdx.x + 1] = M.rho;
-    if (t < 80) {
+    // (every density that enters a gradient is the plain sum f_0 + ... + f_8
+    // of the pulled populations, on every path, so the result of a cell does
+    // not depend on which path its block takes)
+    __shared__ C rho_s[R + 2][34];
+    rho_s[threadIdx.y + 1][threadIdx.x + 1] =
+        f[0] + f[1] + f[2] + f[3] + f[4] + f[5] + f[6] + f[7] + f[8];
+    if (t < 64 + 2 * R) {
       C r = C(0);
 #pragma unroll
       for (int i = 0; i < (LAM ? 9 : 1); ++i) r += hf[i];
@@ -759,7 +787,7 @@ __global__ void __launch_bounds__(256, LAM ? LBM_STEP_MIN_BLOCKS_LAM : LBM_STEP_
   }
   C jx, jy, Sx, Sy;
   if (x0 < p.sp_left || x0 + 32 > p.nx - p.sp_right || y0 < p.sp_top ||
-      y0 + (int)blockDim.y > p.ny - p.sp_bottom) {
+      y0 + R > p.ny - p.sp_bottom) {
     flux_and_source<C>(M.mx, M.my, Gx, Gy, C(0), C(0), sponge_A<C>(p, x, y), jx, jy, Sx, Sy);
   } else {
     // no absorbing layer: j = m + G/2, S = G
@@ -773,8 +801,8 @@ __global__ void __launch_bounds__(256, LAM ? LBM_STEP_MIN_BLOCKS_LAM : LBM_STEP_
   T *fout = (T *)p.fout + (y * p.frow + x);
 #pragma unroll
   for (int i = 0; i < 9; ++i) stp<T, C>(fout + i * p.fplane, fs[i], p);
-  u[c] = ux0 + U(jx * irho);
-  u[p.plane + c] = uy0 + U(jy * irho);
+  u[c] = ux0 + U(mul_rn(jx, irho));
+  u[p.plane + c] = uy0 + U(mul_rn(jy, irho));
   if (!((M.rho + jx + jy) * C(0) == C(0))) atomicOr(p.err, 1);
 }
 

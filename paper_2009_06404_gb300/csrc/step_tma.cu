@@ -268,7 +268,7 @@ __global__ void __launch_bounds__(kTmaThreads, 2)
 #pragma unroll
       for (int i = 0; i < 9; ++i) st<T, float>(fout + i * p.fplane, fs[i]);
       const float irho = p.mat_per_cell ? ((const float *)p.irho)[c] : irho_row;
-      const U vx = U(jx * irho), vy = U(jy * irho);
+      const U vx = U(mul_rn(jx, irho)), vy = U(mul_rn(jy, irho));
       const U ux = su[row * kTileW + lx] + vx, uy = su[(TH + row) * kTileW + lx] + vy;
       U *u = (U *)p.u;
       u[c] = ux;

@@ -183,3 +183,21 @@ def random_state(nx: int, ny: int, seed: int, scale: float = 1e-3):
     fs = scale * rng.standard_normal((9, ny, nx))
     u = scale * rng.standard_normal((2, ny, nx))
     return fs, u
+
+
+#: grid sizes of the uneven multi-shot batch, by shot index mod 4
+BATCH_SIZES = ((512, 512), (1024, 512), (1536, 768), (2048, 1024))
+
+
+def batch_shots(nshots: int = 64, nsteps: int = 2000, seed: int = 3, storage: str = "f32",
+                sizes=BATCH_SIZES, nrec: int = 64) -> list:
+    """The uneven multi-shot batch: shot s has grid size sizes[s % len(sizes)]
+    and is a 3-5-layer half-space (rho0 in [1, 3], nu in [0.2, 0.35], seeded
+    per shot) with a free top, absorbing layers of 32 cells elsewhere and one
+    source in the top quarter."""
+    out = []
+    for s in range(nshots):
+        nx, ny = sizes[s % len(sizes)]
+        out.append(layered_halfspace(nx, ny, nsteps, seed=seed * 1000 + s, sponge=32,
+                                     nrec=nrec, storage=storage))
+    return out
