@@ -345,6 +345,69 @@ long long lbm_batch_cells(const lbm_batch_t *b);
 lbm_status lbm_batch_destroy(lbm_batch_t *b);
 const char *lbm_batch_last_error(const lbm_batch_t *b);
 
+
+/* ------------------------------------------------------------------------
+ * Adjoint (reverse mode): gradients of a function J of the receiver traces
+ * with respect to Lambda = (mu - lambda)/(rho0 b^2) per cell (hence lambda
+ * and mu, Eq. 32; rho0 held fixed) and to each source amplitude (Sec. 5).
+ *
+ * The adjoint step is the exact transpose of the step's linear part (pull
+ * streaming with the wall rules of Sec. 6, the centred density gradient of
+ * Eq. 10 with its wall ghosts, the absorbing layer of Eq. 44, the collision
+ * with forcing of Eqs. 11-18 and u += j/rho0).  lbm_adjoint_forward runs
+ * nsteps steps from the handle's current state and saves a checkpoint every
+ * checkpoint_every steps; lbm_adjoint_backward walks the segments backwards,
+ * recomputes each one from its checkpoint (storing its density gradients)
+ * and runs its adjoint steps in reverse.  Supported for F32 and F64 storage
+ * (u in the storage precision); the adjoint state is in the storage
+ * precision, the gradient sums in FP64.
+ *
+ * All array arguments of the lbm_adjoint_* calls are DEVICE pointers.  Trace
+ * adjoints: [nsteps][nrec][4], the derivative of J with respect to the
+ * traces the forward run recorded (u_x, u_y after the step, v_x, v_y of the
+ * step), by receiver index.  Output fields are dense [ny][nx] FP64.  The
+ * calls run on the handle's stream; the handle must not be used by other
+ * calls meanwhile.  After lbm_adjoint_backward the handle is back in the
+ * state lbm_adjoint_forward left it in.
+ * ------------------------------------------------------------------------ */
+typedef struct lbm_adjoint lbm_adjoint_t;
+
+/* Workspace bytes: three adjoint population sets and a few planes, the
+ * density gradients of one segment, and ceil(nsteps / checkpoint_every) + 1
+ * state checkpoints.  0 for invalid arguments. */
+size_t lbm_adjoint_workspace_bytes(const lbm_elastic_t *h, int nsteps, int checkpoint_every);
+
+/* Errors: LBM_ERR_ARG, LBM_ERR_UNSUPPORTED (F16/BF16 storage, or FP64 u with
+ * FP32 populations), LBM_ERR_WORKSPACE (too small or not 256-byte aligned);
+ * message in lbm_adjoint_last_error(NULL). */
+lbm_status lbm_adjoint_create(lbm_elastic_t *h, int nsteps, int checkpoint_every,
+                              void *d_workspace, size_t bytes, lbm_adjoint_t **out);
+
+/* nsteps forward steps with checkpoints; the handle records traces as
+ * lbm_elastic_step does. */
+lbm_status lbm_adjoint_forward(lbm_adjoint_t *a);
+
+/* The reverse sweep for trace adjoints d_dtraces (may be NULL without
+ * receivers).  Accumulates the gradients read by lbm_adjoint_gradients. */
+lbm_status lbm_adjoint_backward(lbm_adjoint_t *a, const double *d_dtraces);
+
+/* dJ/dlambda, dJ/dmu, dJ/dLambda per cell and dJ/d amplitude per source
+ * (any output may be NULL).  Synchronises the stream. */
+lbm_status lbm_adjoint_gradients(lbm_adjoint_t *a, double *d_g_lambda, double *d_g_mu,
+                                 double *d_g_Lambda, double *d_g_amp);
+
+/* For tests of the transpose: the adjoint state (adjoint of the
+ * post-collision populations [9][ny][nx] and of u [2][ny][nx]; NULL reads
+ * as zero), and one adjoint step of the linear part at the handle's step
+ * index (no trace adjoint, no gradient sums). */
+lbm_status lbm_adjoint_set_state(lbm_adjoint_t *a, const double *d_abar9, const double *d_ubar2);
+lbm_status lbm_adjoint_get_state(lbm_adjoint_t *a, double *d_abar9, double *d_ubar2);
+lbm_status lbm_adjoint_step_linear(lbm_adjoint_t *a);
+
+long long lbm_adjoint_kernel_launches(const lbm_adjoint_t *a);
+lbm_status lbm_adjoint_destroy(lbm_adjoint_t *a);
+const char *lbm_adjoint_last_error(const lbm_adjoint_t *a);
+
 #ifdef __cplusplus
 }
 #endif

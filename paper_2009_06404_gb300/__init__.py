@@ -6,8 +6,8 @@ The time step runs in the CUDA library built from ``csrc/`` (C ABI declared in
 only for device memory and streams.  ``workloads`` builds seeded synthetic
 inputs.
 """
-from .binding import (SYMBOLS, Batch, ElasticLBM, LBMError, NonFiniteError, from_workload,
+from .binding import (SYMBOLS, Adjoint, Batch, ElasticLBM, LBMError, NonFiniteError, from_workload,
                       load_library, make_config)
 
-__all__ = ["Batch", "ElasticLBM", "LBMError", "NonFiniteError", "from_workload",
+__all__ = ["Adjoint", "Batch", "ElasticLBM", "LBMError", "NonFiniteError", "from_workload",
            "load_library", "make_config", "SYMBOLS"]

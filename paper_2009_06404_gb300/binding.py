@@ -39,6 +39,10 @@ SYMBOLS = [
     "lbm_batch_get_launch", "lbm_batch_autotune", "lbm_batch_step", "lbm_batch_sync",
     "lbm_batch_kernel_launches", "lbm_batch_cells", "lbm_batch_destroy",
     "lbm_batch_last_error",
+    "lbm_adjoint_workspace_bytes", "lbm_adjoint_create", "lbm_adjoint_forward",
+    "lbm_adjoint_backward", "lbm_adjoint_gradients", "lbm_adjoint_set_state",
+    "lbm_adjoint_get_state", "lbm_adjoint_step_linear", "lbm_adjoint_kernel_launches",
+    "lbm_adjoint_destroy", "lbm_adjoint_last_error",
 ]
 
 
@@ -144,6 +148,17 @@ def load_library(build_if_missing: bool = False):
             "lbm_batch_cells": (ctypes.c_longlong, [vp]),
             "lbm_batch_destroy": (ip, [vp]),
             "lbm_batch_last_error": (ctypes.c_char_p, [vp]),
+            "lbm_adjoint_workspace_bytes": (ctypes.c_size_t, [vp, ip, ip]),
+            "lbm_adjoint_create": (ip, [vp, ip, ip, vp, ctypes.c_size_t, ctypes.POINTER(vp)]),
+            "lbm_adjoint_forward": (ip, [vp]),
+            "lbm_adjoint_backward": (ip, [vp, vp]),
+            "lbm_adjoint_gradients": (ip, [vp, vp, vp, vp, vp]),
+            "lbm_adjoint_set_state": (ip, [vp, vp, vp]),
+            "lbm_adjoint_get_state": (ip, [vp, vp, vp]),
+            "lbm_adjoint_step_linear": (ip, [vp]),
+            "lbm_adjoint_kernel_launches": (ctypes.c_longlong, [vp]),
+            "lbm_adjoint_destroy": (ip, [vp]),
+            "lbm_adjoint_last_error": (ctypes.c_char_p, [vp]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)
@@ -210,6 +225,8 @@ class ElasticLBM:
             raise LBMError(st, self.L.lbm_elastic_last_error(None).decode())
         self.h = h
         self.workspace_bytes = nbytes
+        self.nsrc = 0
+        self.nrec = 0
 
     # ------------------------------------------------------------ helpers
     def _check(self, st, allow_warn=False):
@@ -260,6 +277,7 @@ class ElasticLBM:
         """sources: array [n][9] = (x, y, sigma, dir_x, dir_y, amplitude,
         f_peak, t0, r_cut)."""
         s = np.asarray(sources, np.float64).reshape(-1, 9)
+        self.nsrc = len(s)
         arr = (Source * max(1, len(s)))()
         for k, row in enumerate(s):
             arr[k] = Source(*[float(v) for v in row])
@@ -463,6 +481,107 @@ class Batch:
     @property
     def cells(self) -> int:
         return int(self.L.lbm_batch_cells(self.h))
+
+
+class Adjoint:
+    """Reverse-mode gradients of a function of the receiver traces of one
+    ElasticLBM (FP32 or FP64 storage): ``forward`` runs ``nsteps`` steps
+    from the simulation's current state with a checkpoint every
+    ``checkpoint_every`` steps and returns the traces it recorded;
+    ``backward(dtraces)`` runs the adjoint for the trace derivatives;
+    ``gradients`` returns dJ/dlambda, dJ/dmu, dJ/dLambda per cell and dJ/d
+    amplitude per source.  Arrays are torch CUDA tensors (FP64)."""
+
+    def __init__(self, sim: "ElasticLBM", nsteps: int, checkpoint_every: int = 100):
+        import torch
+        self._torch = torch
+        self.sim = sim
+        self.L = sim.L
+        self.nsteps = int(nsteps)
+        nbytes = self.L.lbm_adjoint_workspace_bytes(sim.h, self.nsteps, int(checkpoint_every))
+        if nbytes == 0:
+            raise LBMError(-1, "invalid adjoint arguments")
+        with torch.cuda.device(sim.device):
+            self.workspace = torch.empty(nbytes + 256, dtype=torch.uint8, device=sim.device)
+        base = self.workspace.data_ptr()
+        off = (-base) % 256
+        h = ctypes.c_void_p()
+        st = self.L.lbm_adjoint_create(sim.h, self.nsteps, int(checkpoint_every), base + off,
+                                       nbytes, ctypes.byref(h))
+        if st != LBM_OK:
+            raise LBMError(st, self.L.lbm_adjoint_last_error(None).decode())
+        self.h = h
+        self.traced_start = 0
+
+    def _check(self, st):
+        if st != LBM_OK:
+            raise LBMError(st, self.L.lbm_adjoint_last_error(self.h).decode())
+
+    def close(self):
+        if getattr(self, "h", None) is not None and self.h.value:
+            self.L.lbm_adjoint_destroy(self.h)
+            self.h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def forward(self):
+        """Runs the forward steps; returns the traces they recorded
+        ([nsteps][nrec][4] FP64 CUDA tensor, or None without receivers)."""
+        self.traced_start = self.sim.traces_recorded()
+        self._check(self.L.lbm_adjoint_forward(self.h))
+        if self.sim.traces_recorded() == 0:
+            return None
+        tr = self.sim.read_traces(on_device=True)
+        return tr[self.traced_start:self.traced_start + self.nsteps]
+
+    def backward(self, dtraces=None):
+        p = None
+        if dtraces is not None:
+            dtraces = dtraces.to(dtype=self._torch.float64).contiguous()
+            p = dtraces.data_ptr()
+        self._keep = dtraces
+        self._check(self.L.lbm_adjoint_backward(self.h, p))
+
+    def gradients(self) -> Dict:
+        t = self._torch
+        ny, nx = self.sim.ny, self.sim.nx
+        dev = self.sim.device
+        g = {k: t.zeros((ny, nx), dtype=t.float64, device=dev)
+             for k in ("lambda", "mu", "Lambda")}
+        nsrc = self.sim.nsrc
+        g["amplitude"] = t.zeros(max(nsrc, 1), dtype=t.float64, device=dev)
+        self._check(self.L.lbm_adjoint_gradients(self.h, g["lambda"].data_ptr(),
+                                                 g["mu"].data_ptr(), g["Lambda"].data_ptr(),
+                                                 g["amplitude"].data_ptr()))
+        g["amplitude"] = g["amplitude"][:nsrc]
+        return g
+
+    def set_state(self, abar9, ubar2=None):
+        t = self._torch
+        a = abar9.to(dtype=t.float64).contiguous()
+        u = None if ubar2 is None else ubar2.to(dtype=t.float64).contiguous()
+        self._check(self.L.lbm_adjoint_set_state(self.h, a.data_ptr(),
+                                                 None if u is None else u.data_ptr()))
+        self.sim.sync()
+
+    def get_state(self):
+        t = self._torch
+        ny, nx = self.sim.ny, self.sim.nx
+        a = t.empty((9, ny, nx), dtype=t.float64, device=self.sim.device)
+        u = t.empty((2, ny, nx), dtype=t.float64, device=self.sim.device)
+        self._check(self.L.lbm_adjoint_get_state(self.h, a.data_ptr(), u.data_ptr()))
+        return a, u
+
+    def step_linear(self):
+        self._check(self.L.lbm_adjoint_step_linear(self.h))
+
+    @property
+    def kernel_launches(self) -> int:
+        return int(self.L.lbm_adjoint_kernel_launches(self.h))
 
 
 def moment_sums_noalloc(f9, u2, storage="f64", u_fp64=False, nx=None, out=None,

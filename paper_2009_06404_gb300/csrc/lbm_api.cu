@@ -569,6 +569,32 @@ bool setup_tma(lbm_elastic_t *h, std::string *why) {
 
 StepParams lbm::handle_step_params(lbm_elastic_t *h) { return base_params(h); }
 
+lbm_status lbm::handle_step(lbm_elastic_t *h, void *grad_out) {
+  StepParams p = base_params(h);
+  if (h->nrec > 0 && h->traced < h->cfg.max_steps_traced) p.trace_slot = h->traced;
+  lbm_status st;
+  if (grad_out) {
+    // the gradient-force path, whatever Lambda is, storing grad rho
+    p.grad_out = grad_out;
+    const bool keep = h->lambda_nonzero;
+    h->lambda_nonzero = true;
+    st = launch_step(h, p, 0, h->cfg.ny);
+    h->lambda_nonzero = keep;
+  } else if (h->use_tma) {
+    const cudaError_t e = launch_step_tma(p, h->maps, h->cur, h->cfg.storage, h->L.usize == 8,
+                                          h->lambda_nonzero, h->nsm, h->stream);
+    st = e != cudaSuccess ? cuda_fail(h, e, "TMA step kernel launch")
+                          : check_launch(h, "TMA step kernel launch");
+  } else {
+    st = launch_step(h, p, 0, h->cfg.ny);
+  }
+  if (st) return st;
+  if (p.trace_slot >= 0) h->traced++;
+  h->cur ^= 1;
+  h->step++;
+  return LBM_OK;
+}
+
 extern "C" {
 
 size_t lbm_elastic_workspace_bytes(const lbm_elastic_config *cfg) {
@@ -706,6 +732,8 @@ lbm_status lbm_elastic_set_sources(lbm_elastic_t *h, const lbm_source *src, int 
     q.pad = 0;
     q.ax = s.amplitude * s.dir_x;
     q.ay = s.amplitude * s.dir_y;
+    q.dirx = s.dir_x;
+    q.diry = s.dir_y;
     q.pif2 = M_PI * M_PI * s.f_peak * s.f_peak;
     q.t0 = s.t0;
   }
@@ -797,23 +825,8 @@ lbm_status lbm_elastic_reset(lbm_elastic_t *h) {
 lbm_status lbm_elastic_step(lbm_elastic_t *h, int nsteps) {
   if (!h) return LBM_ERR_ARG;
   if (nsteps < 0) return fail(h, LBM_ERR_ARG, "nsteps < 0");
-  for (int s = 0; s < nsteps; ++s) {
-    StepParams p = base_params(h);
-    if (h->nrec > 0 && h->traced < h->cfg.max_steps_traced) p.trace_slot = h->traced;
-    lbm_status st;
-    if (h->use_tma) {
-      const cudaError_t e = launch_step_tma(p, h->maps, h->cur, h->cfg.storage,
-                                            h->L.usize == 8, h->lambda_nonzero, h->nsm, h->stream);
-      st = e != cudaSuccess ? cuda_fail(h, e, "TMA step kernel launch")
-                            : check_launch(h, "TMA step kernel launch");
-    } else {
-      st = launch_step(h, p, 0, h->cfg.ny);
-    }
-    if (st) return st;
-    if (p.trace_slot >= 0) h->traced++;
-    h->cur ^= 1;
-    h->step++;
-  }
+  for (int s = 0; s < nsteps; ++s)
+    if (lbm_status st = handle_step(h, nullptr)) return st;
   return LBM_OK;
 }
 

@@ -51,4 +51,8 @@ namespace lbm {
 // Step parameters of the handle's next step (current buffers, step index,
 // no trace slot).
 StepParams handle_step_params(lbm_elastic_t *h);
+// One step of the handle.  With grad_out set, the step takes the
+// gradient-force path (whatever Lambda is; the result is the same) and
+// stores the centred density gradient of every cell there.
+lbm_status handle_step(lbm_elastic_t *h, void *grad_out);
 }  // namespace lbm

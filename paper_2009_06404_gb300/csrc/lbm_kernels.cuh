@@ -44,6 +44,7 @@ struct SourceDev {
   int xc, yc;       // nearest cell of the position
   int rb;           // integer bound: ceil(r_cut) + 1 cells around (xc, yc)
   int pad;
+  double dirx, diry;  // direction (the force per unit amplitude)
 };
 
 struct StepParams {
@@ -82,6 +83,10 @@ struct StepParams {
   int rec_x0, rec_x1, rec_y0, rec_y1;
   int src_x0, src_x1, src_y0, src_y1;
   int reverse;              // 1: blocks visit the grid in reverse order
+  // when set (gradient-force path only): the centred density gradient of
+  // every cell is stored here, x component then y component plane
+  // ([2][ny][pitch], compute type)
+  void *grad_out;
   // fields mode only
   int row0, nrows;
   double *out[8];           // ux uy vx vy rho pxx pxy pyy, [nrows][nx] each
@@ -305,16 +310,23 @@ __device__ __forceinline__ C sponge_A(const StepParams &p, int x, int y) {
 // Force of one source at (x, y) for step n, in FP64 (only called for the
 // few cells of warps near a source; out of line so that the compiler cannot
 // hoist its FP64 conversions into the path every cell takes).
-static __device__ __noinline__ double2 source_term(const SourceDev &q, int x, int y, long long n, int nx,
-                                            int ny, int wrap_x, int wrap_y) {
+// Gaussian x Ricker factor of one source at (x, y) for step n (zero beyond
+// r_cut).
+__device__ __forceinline__ double source_shape(const SourceDev &q, int x, int y, long long n,
+                                               int nx, int ny, int wrap_x, int wrap_y) {
   double dx = (double)x - q.x, dy = (double)y - q.y;
   if (wrap_x) dx -= nx * floor(dx / nx + 0.5);
   if (wrap_y) dy -= ny * floor(dy / ny + 0.5);
   const double r2 = dx * dx + dy * dy;
-  if (!(r2 <= q.rcut2)) return make_double2(0.0, 0.0);
+  if (!(r2 <= q.rcut2)) return 0.0;
   const double tt = (double)n - q.t0;
   const double a = q.pif2 * tt * tt;
-  const double g = exp(-r2 * q.inv2s2) * (1.0 - 2.0 * a) * exp(-a);
+  return exp(-r2 * q.inv2s2) * (1.0 - 2.0 * a) * exp(-a);
+}
+
+static __device__ __noinline__ double2 source_term(const SourceDev &q, int x, int y, long long n, int nx,
+                                            int ny, int wrap_x, int wrap_y) {
+  const double g = source_shape(q, x, y, n, nx, ny, wrap_x, wrap_y);
   return make_double2(q.ax * g, q.ay * g);
 }
 
@@ -652,8 +664,12 @@ __device__ __noinline__ void general_block_lam(const StepParams &p, int x0, int 
   C rym = rho_s[ty][tx + 1], ryp = rho_s[ty + 2][tx + 1];
   wall_ghosts<C>(p, xc == 0, xc == p.nx - 1, p.bc_left, p.bc_right, rho, rxm, rxp);
   wall_ghosts<C>(p, yc == 0, yc == p.ny - 1, p.bc_top, p.bc_bottom, rho, rym, ryp);
-  finish_cell<T, C, U, true, MODE>(p, f, C(0.5) * (rxp - rxm), C(0.5) * (ryp - rym), Fx, Fy, x, y,
-                                   xc, yc, active);
+  const C gx = C(0.5) * (rxp - rxm), gy = C(0.5) * (ryp - rym);
+  if (MODE == 0 && p.grad_out && active) {
+    ((C *)p.grad_out)[y * p.pitch + x] = gx;
+    ((C *)p.grad_out)[p.plane + y * p.pitch + x] = gy;
+  }
+  finish_cell<T, C, U, true, MODE>(p, f, gx, gy, Fx, Fy, x, y, xc, yc, active);
 }
 
 // One thread per cell, blocks of 32 x 8 threads (a warp is 32 consecutive
@@ -781,6 +797,10 @@ __device__ __forceinline__ void step_block(const StepParams &p, int bx, int by) 
     // elastic force Lambda b^2 grad rho with the centred difference (Eqs. 9-10)
     const C gx = C(0.5) * (rho_s[threadIdx.y + 1][threadIdx.x + 2] - rho_s[threadIdx.y + 1][threadIdx.x]);
     const C gy = C(0.5) * (rho_s[threadIdx.y + 2][threadIdx.x + 1] - rho_s[threadIdx.y][threadIdx.x + 1]);
+    if (p.grad_out) {
+      ((C *)p.grad_out)[c] = gx;
+      ((C *)p.grad_out)[p.plane + c] = gy;
+    }
     const C lb2 = mat_at<C>(p.lam, p.mat_per_cell, x, y, p.pitch) * C(1.0 / 3.0);
     Gx = lb2 * gx;
     Gy = lb2 * gy;
