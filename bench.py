@@ -332,6 +332,11 @@ def run_gpu(args):
                "sample": f"{args.cpu_sample_steps} time steps of the {w.nx}x{w.ny} half-space "
                          f"(FP64 oracle, OpenMP over rows), {dt:.1f} s"}
 
+    forms = None
+    if world == 1 and not args.no_forms:
+        forms = measure_forms(torch, pkg, wl)
+        forms["plain"] = {"workload": "halfspace_2048x1024, FP32", "mlups": value}
+
     clocks = clk.summary()
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -353,12 +358,160 @@ def run_gpu(args):
                 "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
         "clocks": clocks,
         "gpu_launches": int(gpu_launches),
+        "forms": forms,
     }
     print(json.dumps(line), flush=True)
     sim.close()
     if dist is not None:
         dist.destroy_process_group()
     return 0
+
+
+def _ev(torch):
+    return torch.cuda.Event(enable_timing=True)
+
+
+def _timed(torch, fn) -> float:
+    """Milliseconds of fn() on the current stream (synchronised both sides)."""
+    torch.cuda.synchronize()
+    a, b = _ev(torch), _ev(torch)
+    a.record()
+    fn()
+    b.record()
+    torch.cuda.synchronize()
+    return a.elapsed_time(b)
+
+
+def _rel_l2(a, b) -> float:
+    a = np.asarray(a, np.float64)
+    b = np.asarray(b, np.float64)
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+def form_precision(torch, pkg, wl, n=8192, steps=2000, time_steps=200, err_n=1024):
+    """FP16 / BF16 population storage (FP32 arithmetic) against FP32 storage
+    on the periodic 8-layer, 16-source grid: MLUPS over time_steps steps at
+    n x n, and the relative L2 error of u and v after `steps` steps against
+    an FP64 run of the same generator at err_n x err_n."""
+    scale = {"f32": 0, "f16": 10, "bf16": 0, "f64": 0}
+    w = wl.periodic_layered_multisource(n=n, nsteps=time_steps)
+    mlups = {}
+    for st in ("f32", "f16", "bf16"):
+        sim = pkg.from_workload(w, storage=st, store_scale_log2=scale[st], max_steps_traced=0)
+        sim.step(20)
+        ms = _timed(torch, lambda: sim.step(time_steps))
+        mlups[st] = w.cells * time_steps / ms / 1e3
+        sim.sync()
+        sim.close()
+        del sim
+    we = wl.periodic_layered_multisource(n=err_n, nsteps=steps)
+    fields = {}
+    for st in ("f64", "f32", "f16", "bf16"):
+        sim = pkg.from_workload(we, storage=st, store_scale_log2=scale[st], max_steps_traced=0)
+        sim.step(steps)
+        f = sim.read_fields(("ux", "uy", "vx", "vy"), on_device=False)
+        fields[st] = (np.stack([f["ux"], f["uy"]]), np.stack([f["vx"], f["vy"]]))
+        sim.close()
+    err_u = {st: _rel_l2(fields[st][0], fields["f64"][0]) for st in ("f32", "f16", "bf16")}
+    err_v = {st: _rel_l2(fields[st][1], fields["f64"][1]) for st in ("f32", "f16", "bf16")}
+    return {"workload": f"periodic_layered_{n}x{n}_8layers_16src", "time_steps": time_steps,
+            "mlups": mlups,
+            "speedup_vs_f32": {k: mlups[k] / mlups["f32"] for k in ("f16", "bf16")},
+            "error": {"vs": f"FP64 GPU run, same generator at {err_n}x{err_n}, {steps} steps",
+                      "rel_l2_u": err_u, "rel_l2_v": err_v},
+            "store_scale_log2": {k: scale[k] for k in ("f16", "bf16")}}
+
+
+def form_batched(torch, pkg, wl, nshots=64, time_steps=50):
+    """64 uneven layered shots (65.0 M cells) advanced together, against the
+    same shots stepped one after another."""
+    ws = wl.batch_shots(nshots, nsteps=2000)
+    shots = [pkg.from_workload(w, max_steps_traced=0) for w in ws]
+    cells = sum(w.cells for w in ws)
+
+    def plain():
+        for sh in shots:
+            sh.step(time_steps)
+
+    plain()
+    plain_ms = _timed(torch, plain)
+    b = pkg.Batch(shots)
+    best_us = b.autotune(3)
+    launch = b.launch
+    b.step(time_steps)
+    batch_ms = _timed(torch, lambda: b.step(time_steps))
+    b.sync()
+    launches = b.kernel_launches
+    plain_m = cells * time_steps / plain_ms / 1e3
+    batch_m = cells * time_steps / batch_ms / 1e3
+    out = {"workload": f"{nshots} layered half-space shots, sizes 512^2..2048x1024, "
+                       f"{cells} cells, FP32", "time_steps": time_steps,
+           "mlups": batch_m, "plain_mlups": plain_m, "speedup_vs_plain": batch_m / plain_m,
+           "launch": {k: launch[k] for k in ("mode", "rows", "order")},
+           "autotune_best_us_per_step": best_us, "kernel_launches": launches,
+           "error": "bit-identical to the shots stepped alone (tested)"}
+    b.close()
+    for sh in shots:
+        sh.close()
+    return out
+
+
+def form_adjoint(torch, pkg, wl, nx=1024, ny=512, steps=3000, every=100):
+    """Gradient of the trace misfit of the blob model against the layered
+    model with respect to lambda, mu per cell and the source amplitude:
+    forward with checkpoints plus reverse sweep, FP32 states with FP64
+    gradient sums, against the plain FP32 forward; error of the FP32 lambda
+    gradient against the FP64 one."""
+    from paper_2009_06404_gb300.autograd import SimulationSetup, simulate_traces
+    base, pert = wl.fwi_blob(nx, ny, steps)
+    res = {}
+    grads = {}
+    # FP64 first: it also loads torch's backward kernels for the misfit, so
+    # the FP32 timing sees no one-time module loading
+    for st in ("f64", "f32"):
+        setup = SimulationSetup(pert, steps, every, st)
+        dev = "cuda"
+        amp = torch.ones(1, dtype=torch.float64, device=dev)
+        with torch.no_grad():
+            d = simulate_traces(torch.as_tensor(base.lam, device=dev),
+                                torch.as_tensor(base.mu, device=dev), amp, setup)
+        lam = torch.as_tensor(pert.lam, device=dev).requires_grad_(True)
+        mu = torch.as_tensor(pert.mu, device=dev).requires_grad_(True)
+        tr = [None]
+
+        def fwd():
+            tr[0] = simulate_traces(lam, mu, amp, setup)
+
+        t_f = _timed(torch, fwd)
+        J = 0.5 * ((tr[0][..., :2] - d[..., :2]) ** 2).sum()
+        t_b = _timed(torch, J.backward)
+        grads[st] = lam.grad.cpu().numpy()
+        res[st] = (t_f, t_b)
+    sim = pkg.from_workload(pert, storage="f32", max_steps_traced=steps)
+    sim.step(100)
+    plain_ms = _timed(torch, lambda: sim.step(steps))
+    sim.close()
+    cells = nx * ny
+    t_f, t_b = res["f32"]
+    adj_m = cells * steps / (t_f + t_b) / 1e3
+    plain_m = cells * steps / plain_ms / 1e3
+    return {"workload": f"fwi_blob_{nx}x{ny}, {steps} steps, checkpoints every {every}, "
+                        "128 receivers, FP32 states, FP64 gradient sums",
+            "mlups": adj_m, "plain_mlups": plain_m, "speedup_vs_plain": adj_m / plain_m,
+            "forward_ms": t_f, "backward_ms": t_b,
+            "error": {"rel_l2_grad_lambda_f32_vs_f64": _rel_l2(grads["f32"], grads["f64"])}}
+
+
+def measure_forms(torch, pkg, wl):
+    out = {}
+    for name, fn in (("batched", form_batched), ("precision", form_precision),
+                     ("adjoint", form_adjoint)):
+        try:
+            out[name] = fn(torch, pkg, wl)
+        except Exception as e:  # a failing form must not cost the headline line
+            out[name] = {"error": f"{type(e).__name__}: {e}"}
+        torch.cuda.empty_cache()
+    return out
 
 
 def main():
@@ -372,6 +525,8 @@ def main():
     ap.add_argument("--cpu-sample-steps", type=int, default=100)
     ap.add_argument("--ref-sample-steps", type=int, default=10)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-forms", action="store_true",
+                    help="skip the batched / 16-bit / adjoint form measurements")
     args = ap.parse_args()
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3")

@@ -36,8 +36,9 @@ struct AdjParams {
   void *abar_out;      // adjoint of f* of step n - 1
   void *gbar;          // adjoint of the pulled populations (scratch, same layout)
   void *wbar;          // Lambda b^2 H_b / 2, 2 planes (scratch)
-  void *ubar;          // adjoint of u, 2 planes
-  void *vbar;          // adjoint of v = j / rho0 of step n, 2 planes
+  void *rbar;          // adjoint of the streamed density, 1 plane (scratch)
+  const void *ufield;  // adjoint of u as 2 full planes (transpose tests), or null
+  const void *jrec;    // else: per receiver (sorted order), the adjoint of j/rho0 there
   const void *grad;    // the forward's centred density gradient of step n, 2 planes
   double *g_lam;       // dJ/dLambda, one plane (FP64)
   double *g_amp;       // dJ/d amplitude, per source (FP64)
@@ -62,8 +63,22 @@ __global__ void __launch_bounds__(256) adj_local_kernel(const AdjParams a) {
 #pragma unroll
   for (int i = 0; i < 9; ++i) av[i] = cp<C>(a.abar)[cf + i * p.fplane];
   const C irho = mat_at<C>(p.irho, p.mat_per_cell, xc, yc, p.pitch);
-  const C jbx0 = (cp<C>(a.ubar)[c] + cp<C>(a.vbar)[c]) * irho;
-  const C jby0 = (cp<C>(a.ubar)[p.plane + c] + cp<C>(a.vbar)[p.plane + c]) * irho;
+  // adjoint of j from u' = u + j/rho0 and v = j/rho0
+  C jbx0 = C(0), jby0 = C(0);
+  if (a.ufield) {
+    jbx0 = cp<C>(a.ufield)[c] * irho;
+    jby0 = cp<C>(a.ufield)[p.plane + c] * irho;
+  } else if (p.nrec > 0 && active && x >= p.rec_x0 && x <= p.rec_x1 && y >= p.rec_y0 &&
+             y <= p.rec_y1) {
+    const int tile = (y / kRecTileY) * p.rec_tiles_x + x / kRecTileX;
+    for (int r = p.rec_tile_ptr[tile]; r < p.rec_tile_ptr[tile + 1]; ++r)
+      if (p.rec_xy[2 * r] == x && p.rec_xy[2 * r + 1] == y) {
+        jbx0 += cp<C>(a.jrec)[2 * r];
+        jby0 += cp<C>(a.jrec)[2 * r + 1];
+      }
+    jbx0 *= irho;
+    jby0 *= irho;
+  }
   const C om = par<C>(p.omega, p.omega_f), kap = par<C>(p.fcoef, p.fcoef_f);
   const C A = sponge_A<C>(p, xc, yc);
   const C sig = C(1) / (C(1) + C(0.5) * A);
@@ -143,7 +158,7 @@ __global__ void __launch_bounds__(256) adj_local_kernel(const AdjParams a) {
 }
 
 // Adjoint of the density through the centred gradient (Eq. 10) and its wall
-// ghosts, added to every pulled population of the cell (rho = sum g_i).
+// ghosts.
 template <class C>
 __device__ __forceinline__ C div_axis(const C *w, int n, int k, int stride, bool per, int bc_lo,
                                       int bc_hi, int fs_order) {
@@ -177,13 +192,20 @@ __global__ void __launch_bounds__(256) adj_div_kernel(const AdjParams a) {
   if (x >= p.nx || y >= p.ny) return;
   const int c = y * p.pitch + x;
   const C *wx = cp<C>(a.wbar) + c, *wy = cp<C>(a.wbar) + p.plane + c;
-  const C rb = div_axis<C>(wx, p.nx, x, 1, p.bc_left == BC_PERIODIC, p.bc_left, p.bc_right,
-                           p.fs_order) +
-               div_axis<C>(wy, p.ny, y, p.pitch, p.bc_top == BC_PERIODIC, p.bc_top,
-                           p.bc_bottom, p.fs_order);
-  C *gb = (C *)a.gbar + (long long)y * p.frow + x;
-#pragma unroll
-  for (int i = 0; i < 9; ++i) gb[i * p.fplane] += rb;
+  ((C *)a.rbar)[c] =
+      div_axis<C>(wx, p.nx, x, 1, p.bc_left == BC_PERIODIC, p.bc_left, p.bc_right, p.fs_order) +
+      div_axis<C>(wy, p.ny, y, p.pitch, p.bc_top == BC_PERIODIC, p.bc_top, p.bc_bottom,
+                  p.fs_order);
+}
+
+// The adjoint of pulled population i at cell (x, y): its local part plus
+// the density adjoint (rho = sum of the pulled populations).
+template <class C>
+__device__ __forceinline__ C gtot(const AdjParams &a, int x, int y, int i) {
+  const StepParams &p = a.p;
+  C g = cp<C>(a.gbar)[(long long)y * p.frow + x + i * p.fplane];
+  if (a.lam_any) g += cp<C>(a.rbar)[y * p.pitch + x];
+  return g;
 }
 
 // Which wall, if any, supplies population i = opp(j) at (x, y): the link
@@ -241,14 +263,13 @@ __device__ __forceinline__ void spread_moments(C *out, C rb, C tb, int hz, C s) 
 template <class C>
 __device__ __forceinline__ void inner_contrib(const AdjParams &a, int xb, int yb, int hz, C *out) {
   const StepParams &p = a.p;
-  const C *gb = cp<C>(a.gbar) + (long long)yb * p.frow + xb;
   for (int j = 1; j < 9; ++j) {
     int tx, ty, bc, h;
     if (!link_wall(p, xb, yb, j, tx, ty, bc, h)) continue;
+    // only the links through the wall between (xb, yb) and the inner cell
     if (bc != BC_FREE || h != hz) continue;
-    // the wall must be the one between (xb, yb) and the inner cell
     C rb, tb;
-    abb_moments<C>(gb[oppd(j) * p.fplane], j, hz, rb, tb);
+    abb_moments<C>(gtot<C>(a, xb, yb, oppd(j)), j, hz, rb, tb);
     spread_moments<C>(out, rb, tb, hz, C(-0.5));
   }
 }
@@ -259,7 +280,6 @@ __global__ void __launch_bounds__(256) adj_pull_kernel(const AdjParams a) {
   const StepParams &p = a.p;
   const int x = blockIdx.x * 32 + threadIdx.x, y = blockIdx.y * 8 + threadIdx.y;
   if (x >= p.nx || y >= p.ny) return;
-  const C *gb = cp<C>(a.gbar);
   const long long cf = (long long)y * p.frow + x;
   const bool lin = p.fs_order == 1;
   C out[9];
@@ -268,10 +288,10 @@ __global__ void __launch_bounds__(256) adj_pull_kernel(const AdjParams a) {
   for (int j = 0; j < 9; ++j) {
     int tx, ty, bc, hz;
     if (!link_wall(p, x, y, j, tx, ty, bc, hz)) {
-      out[j] = gb[(long long)ty * p.frow + tx + j * p.fplane];
+      out[j] = gtot<C>(a, tx, ty, j);
     } else {
       wall_cell = true;
-      const C gi = gb[cf + oppd(j) * p.fplane];
+      const C gi = gtot<C>(a, x, y, oppd(j));
       out[j] = bc == BC_RIGID ? gi : -gi;
     }
   }
@@ -281,7 +301,7 @@ __global__ void __launch_bounds__(256) adj_pull_kernel(const AdjParams a) {
       int tx, ty, bc, hz;
       if (!link_wall(p, x, y, j, tx, ty, bc, hz) || bc != BC_FREE) continue;
       C rb, tb;
-      abb_moments<C>(gb[cf + oppd(j) * p.fplane], j, hz, rb, tb);
+      abb_moments<C>(gtot<C>(a, x, y, oppd(j)), j, hz, rb, tb);
       spread_moments<C>(out, rb, tb, hz, lin ? C(1.5) : C(1));
     }
   }
@@ -297,34 +317,29 @@ __global__ void __launch_bounds__(256) adj_pull_kernel(const AdjParams a) {
   for (int j = 0; j < 9; ++j) o[j * p.fplane] = out[j];
 }
 
-// Receiver adjoints of step n: ubar += du (the adjoint of u^{n+1}, which
-// every later u carries), vbar = dv (the adjoint of v^n).  d: [nrec][4] of
-// this step by original receiver index.  One block.
+// Receiver adjoints of step n (receivers in the sorted order of the
+// receiver table): ubar_r += du (the adjoint of u^{n+1}, carried by every
+// later u), jrec_r = ubar_r + dv (with dv the adjoint of v^n; both enter as
+// j / rho0).  d: [nrec][4] of this step by original receiver index.
 template <class C>
-__global__ void adj_inject_kernel(C *ubar, C *vbar, int plane, int pitch, const int *rec_xy,
-                                  const int *rec_id, int nrec, const double *d) {
-  for (int r = threadIdx.x; r < nrec; r += blockDim.x) {
-    const int c = rec_xy[2 * r + 1] * pitch + rec_xy[2 * r];
-    vbar[c] = C(0);
-    vbar[plane + c] = C(0);
-  }
-  __syncthreads();
-  for (int r = threadIdx.x; r < nrec; r += blockDim.x) {
-    const int c = rec_xy[2 * r + 1] * pitch + rec_xy[2 * r];
+__global__ void adj_inject_kernel(C *ubar_r, C *jrec, const int *rec_id, int nrec,
+                                  const double *d) {
+  for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < nrec; r += gridDim.x * blockDim.x) {
     const double *q = d + 4 * (long long)rec_id[r];
-    atomicAdd(&ubar[c], C(q[0]));
-    atomicAdd(&ubar[plane + c], C(q[1]));
-    atomicAdd(&vbar[c], C(q[2]));
-    atomicAdd(&vbar[plane + c], C(q[3]));
+    const C ux = ubar_r[2 * r] + C(q[0]), uy = ubar_r[2 * r + 1] + C(q[1]);
+    ubar_r[2 * r] = ux;
+    ubar_r[2 * r + 1] = uy;
+    jrec[2 * r] = ux + C(q[2]);
+    jrec[2 * r + 1] = uy + C(q[3]);
   }
 }
 
 // Launchers (one translation unit per compute type).
 cudaError_t adj_step_f32(const AdjParams &a, cudaStream_t s);
 cudaError_t adj_step_f64(const AdjParams &a, cudaStream_t s);
-cudaError_t adj_inject_f32(const AdjParams &a, const int *rec_xy, const int *rec_id, int nrec,
+cudaError_t adj_inject_f32(void *ubar_r, void *jrec, const int *rec_id, int nrec,
                            const double *d, cudaStream_t s);
-cudaError_t adj_inject_f64(const AdjParams &a, const int *rec_xy, const int *rec_id, int nrec,
+cudaError_t adj_inject_f64(void *ubar_r, void *jrec, const int *rec_id, int nrec,
                            const double *d, cudaStream_t s);
 
 template <class C>
@@ -337,10 +352,9 @@ cudaError_t adj_step_t(const AdjParams &a, cudaStream_t s) {
 }
 
 template <class C>
-cudaError_t adj_inject_t(const AdjParams &a, const int *rec_xy, const int *rec_id, int nrec,
-                         const double *d, cudaStream_t s) {
-  adj_inject_kernel<C><<<1, 256, 0, s>>>((C *)a.ubar, (C *)a.vbar, a.p.plane, a.p.pitch, rec_xy,
-                                         rec_id, nrec, d);
+cudaError_t adj_inject_t(void *ubar_r, void *jrec, const int *rec_id, int nrec, const double *d,
+                         cudaStream_t s) {
+  adj_inject_kernel<C><<<(nrec + 127) / 128, 128, 0, s>>>((C *)ubar_r, (C *)jrec, rec_id, nrec, d);
   return cudaGetLastError();
 }
 

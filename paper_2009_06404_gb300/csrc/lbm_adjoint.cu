@@ -19,8 +19,8 @@ constexpr size_t kAdjAlign = 256;
 size_t aup(size_t v) { return (v + kAdjAlign - 1) / kAdjAlign * kAdjAlign; }
 
 struct AdjLayout {
-  size_t abar[2] = {0, 0}, gbar = 0, wbar = 0, ubar = 0, vbar = 0, glam = 0, gamp = 0, grad = 0,
-         ckpt = 0, total = 0;
+  size_t abar[2] = {0, 0}, gbar = 0, wbar = 0, rbar = 0, ubar = 0, urec = 0, jrec = 0, glam = 0,
+         gamp = 0, grad = 0, ckpt = 0, total = 0;
   size_t state_f = 0, state_u = 0, ckpt_bytes = 0, csize = 0;
   int nck = 0;
 };
@@ -44,8 +44,11 @@ AdjLayout adj_layout(const lbm_elastic_t *h, int nsteps, int K) {
   A.abar[1] = take(9 * pl * A.csize);
   A.gbar = take(9 * pl * A.csize);
   A.wbar = take(2 * pl * A.csize);
+  A.rbar = take(pl * A.csize);
   A.ubar = take(2 * pl * A.csize);
-  A.vbar = take(2 * pl * A.csize);
+  const size_t nr = (size_t)std::max(1, h->cfg.max_receivers);
+  A.urec = take(2 * nr * A.csize);
+  A.jrec = take(2 * nr * A.csize);
   A.glam = take(pl * sizeof(double));
   A.gamp = take((size_t)std::max(1, h->cfg.max_sources) * sizeof(double));
   A.grad = take((size_t)K * 2 * pl * A.csize);
@@ -142,8 +145,9 @@ AdjParams params_of(lbm_adjoint_t *a, long long n) {
   P.abar_out = a->ws + a->A.abar[a->cur_a ^ 1];
   P.gbar = a->ws + a->A.gbar;
   P.wbar = a->ws + a->A.wbar;
-  P.ubar = a->ws + a->A.ubar;
-  P.vbar = a->ws + a->A.vbar;
+  P.rbar = a->ws + a->A.rbar;
+  P.ufield = nullptr;
+  P.jrec = a->ws + a->A.jrec;
   P.grad = nullptr;
   P.g_lam = (double *)(a->ws + a->A.glam);
   P.g_amp = nullptr;
@@ -243,8 +247,8 @@ lbm_status lbm_adjoint_backward(lbm_adjoint_t *a, const double *d_dtraces) {
   cudaStream_t s = h->stream;
   a->cur_a = 0;
   ADJ_CUDA(a, cudaMemsetAsync(a->ws + a->A.abar[0], 0, 9 * pl * a->A.csize, s));
-  ADJ_CUDA(a, cudaMemsetAsync(a->ws + a->A.ubar, 0, 2 * pl * a->A.csize, s));
-  ADJ_CUDA(a, cudaMemsetAsync(a->ws + a->A.vbar, 0, 2 * pl * a->A.csize, s));
+  ADJ_CUDA(a, cudaMemsetAsync(a->ws + a->A.urec, 0,
+                              2 * (size_t)std::max(1, h->cfg.max_receivers) * a->A.csize, s));
   ADJ_CUDA(a, cudaMemsetAsync(a->ws + a->A.glam, 0, pl * sizeof(double), s));
   ADJ_CUDA(a, cudaMemsetAsync(a->ws + a->A.gamp, 0,
                               std::max(1, h->cfg.max_sources) * sizeof(double), s));
@@ -260,10 +264,10 @@ lbm_status lbm_adjoint_backward(lbm_adjoint_t *a, const double *d_dtraces) {
       AdjParams P = params_of(a, a->n_start + n);
       if (h->nrec > 0) {
         const double *d = d_dtraces + (size_t)n * h->nrec * 4;
-        const int *rxy = (const int *)(h->ws + h->L.rec_xy);
         const int *rid = (const int *)(h->ws + h->L.rec_id);
-        const cudaError_t e = a->f64 ? adj_inject_f64(P, rxy, rid, h->nrec, d, s)
-                                     : adj_inject_f32(P, rxy, rid, h->nrec, d, s);
+        void *ur = a->ws + a->A.urec, *jr = a->ws + a->A.jrec;
+        const cudaError_t e = a->f64 ? adj_inject_f64(ur, jr, rid, h->nrec, d, s)
+                                     : adj_inject_f32(ur, jr, rid, h->nrec, d, s);
         if (e != cudaSuccess) {
           st = afail(a, LBM_ERR_CUDA, std::string("adjoint inject: ") + cudaGetErrorString(e));
           break;
@@ -320,7 +324,6 @@ lbm_status lbm_adjoint_set_state(lbm_adjoint_t *a, const double *d_abar9, const 
     dense_in_kernel<float><<<g, 256, 0, h->stream>>>(d_ubar2, 2, nx, ny, (float *)(a->ws + a->A.ubar), L.plane, L.pitch);
   }
   ADJ_CUDA(a, cudaGetLastError());
-  ADJ_CUDA(a, cudaMemsetAsync(a->ws + a->A.vbar, 0, 2 * (size_t)L.plane * a->A.csize, h->stream));
   a->launches += 2;
   return LBM_OK;
 }
@@ -348,6 +351,7 @@ lbm_status lbm_adjoint_step_linear(lbm_adjoint_t *a) {
   if (!a) return LBM_ERR_ARG;
   AdjParams P = params_of(a, a->h->step);
   P.p.nsrc = 0;
+  P.ufield = a->ws + a->A.ubar;
   return adj_launch(a, P);
 }
 

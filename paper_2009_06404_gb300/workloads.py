@@ -201,3 +201,28 @@ def batch_shots(nshots: int = 64, nsteps: int = 2000, seed: int = 3, storage: st
         out.append(layered_halfspace(nx, ny, nsteps, seed=seed * 1000 + s, sponge=32,
                                      nrec=nrec, storage=storage))
     return out
+
+
+def fwi_blob(nx: int = 1024, ny: int = 512, nsteps: int = 3000, seed: int = 4,
+             sigma: float = 25.0, dmu: float = 0.05, dlam: float = -0.05, sponge: int = 64,
+             nrec: int = 128, storage: str = "f32"):
+    """The inversion set-up: a 4-layer half-space (nu in [0.2, 0.3], seeded)
+    with a free top, absorbing layers elsewhere, a vertical source at
+    (nx / 2, 10) and nrec receivers on the surface row, and the same model
+    with a Gaussian blob (width sigma, centre seeded in the interior) scaling
+    mu by (1 + dmu) and lambda by (1 + dlam) at its peak.  Returns
+    (base, perturbed) workloads with per-cell material."""
+    rng = np.random.default_rng(seed)
+    base = layered_halfspace(nx, ny, nsteps, seed=seed, nlayers=(4, 4), nu_range=(0.2, 0.3),
+                             sponge=sponge, nrec=nrec, storage=storage, src_x=nx / 2,
+                             src_y=10.0)
+    cells = lambda a: np.repeat(np.asarray(a, np.float64)[:, None], nx, axis=1)
+    rho0, lam, mu = cells(base.rho0), cells(base.lam), cells(base.mu)
+    cx = rng.uniform(sponge + 2 * sigma, nx - sponge - 2 * sigma)
+    cy = rng.uniform(2 * sigma, ny - sponge - 2 * sigma)
+    Y, X = np.mgrid[0:ny, 0:nx]
+    g = np.exp(-((X - cx) ** 2 + (Y - cy) ** 2) / (2 * sigma * sigma))
+    base = base.with_(rho0=rho0, lam=lam, mu=mu, name=f"fwi_base_{nx}x{ny}")
+    pert = base.with_(lam=lam * (1 + dlam * g), mu=mu * (1 + dmu * g),
+                      name=f"fwi_blob_{nx}x{ny}")
+    return base, pert
