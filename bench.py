@@ -312,7 +312,7 @@ def run_gpu(args):
             with open(prof) as f:
                 d = json.load(f)
             key = f"step_{storage}_{w.nx}x{w.ny}"
-            if key in d and d[key].get("kernel_hash") == _build.source_hash():
+            if key in d and d[key].get("kernel_hash") == _build.source_hash(_build.STEP_SOURCES):
                 traffic = d[key]["dram_bytes_per_launch"]
         except Exception:
             traffic = None
@@ -514,6 +514,27 @@ def measure_forms(torch, pkg, wl):
     return out
 
 
+def run_form(args):
+    """One form alone (its JSON object), e.g. for a profiler capture."""
+    import torch
+    import paper_2009_06404_gb300 as pkg
+    from paper_2009_06404_gb300 import workloads as wl
+    from paper_2009_06404_gb300 import build as _build
+    if not _build.up_to_date():
+        _build.build()
+    pkg.load_library()
+    if args.form == "batched":
+        out = form_batched(torch, pkg, wl, nshots=args.nshots, time_steps=args.form_steps or 50)
+    elif args.form == "precision":
+        out = form_precision(torch, pkg, wl, n=args.prec_n, steps=args.prec_err_steps,
+                             time_steps=args.form_steps or 200, err_n=args.prec_err_n)
+    else:
+        out = form_adjoint(torch, pkg, wl, nx=args.adj_nx, ny=args.adj_ny,
+                           steps=args.form_steps or 3000, every=args.adj_every)
+    print(json.dumps({"form": args.form, **out}), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -527,11 +548,24 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-forms", action="store_true",
                     help="skip the batched / 16-bit / adjoint form measurements")
+    ap.add_argument("--form", choices=["batched", "precision", "adjoint"],
+                    help="measure only this form and print its JSON object")
+    ap.add_argument("--form-steps", type=int, default=0,
+                    help="time steps of the form (0: its default)")
+    ap.add_argument("--nshots", type=int, default=64)
+    ap.add_argument("--prec-n", type=int, default=8192)
+    ap.add_argument("--prec-err-n", type=int, default=1024)
+    ap.add_argument("--prec-err-steps", type=int, default=2000)
+    ap.add_argument("--adj-nx", type=int, default=1024)
+    ap.add_argument("--adj-ny", type=int, default=512)
+    ap.add_argument("--adj-every", type=int, default=100)
     args = ap.parse_args()
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3")
     if args.impl == "reference":
         return run_reference(args)
+    if args.form:
+        return run_form(args)
     return run_gpu(args)
 
 

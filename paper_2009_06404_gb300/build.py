@@ -41,11 +41,19 @@ def _deps():
             + glob.glob(os.path.join(INCLUDE, "*.h")))
 
 
-def source_hash() -> str:
-    """Short hash of the kernel sources (ties profiler counters to a build)."""
+#: the sources the single-grid step kernel is built from (its launch geometry
+#: is set in lbm_api.cu)
+STEP_SOURCES = ("lbm_kernels.cuh", "step_f32.cu", "lbm_api.cu")
+
+
+def source_hash(names=None) -> str:
+    """Short hash of the kernel sources, or of the files among them whose
+    base names are in ``names`` (ties profiler counters to a build)."""
     import hashlib
     h = hashlib.sha256()
     for d in sorted(_deps()):
+        if names is not None and os.path.basename(d) not in names:
+            continue
         with open(d, "rb") as f:
             h.update(os.path.basename(d).encode())
             h.update(f.read())
