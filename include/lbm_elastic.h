@@ -404,6 +404,12 @@ lbm_status lbm_adjoint_set_state(lbm_adjoint_t *a, const double *d_abar9, const 
 lbm_status lbm_adjoint_get_state(lbm_adjoint_t *a, double *d_abar9, double *d_ubar2);
 lbm_status lbm_adjoint_step_linear(lbm_adjoint_t *a);
 
+/* 1 (default): each adjoint step is one fused kernel that stages the local
+ * transposes of a tile and a two-cell ring in shared memory; 0: three
+ * kernels (local transpose, density adjoint, push) through global memory.
+ * Both compute the same transpose. */
+lbm_status lbm_adjoint_set_fused(lbm_adjoint_t *a, int fused);
+
 long long lbm_adjoint_kernel_launches(const lbm_adjoint_t *a);
 lbm_status lbm_adjoint_destroy(lbm_adjoint_t *a);
 const char *lbm_adjoint_last_error(const lbm_adjoint_t *a);

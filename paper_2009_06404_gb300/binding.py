@@ -41,7 +41,8 @@ SYMBOLS = [
     "lbm_batch_last_error",
     "lbm_adjoint_workspace_bytes", "lbm_adjoint_create", "lbm_adjoint_forward",
     "lbm_adjoint_backward", "lbm_adjoint_gradients", "lbm_adjoint_set_state",
-    "lbm_adjoint_get_state", "lbm_adjoint_step_linear", "lbm_adjoint_kernel_launches",
+    "lbm_adjoint_get_state", "lbm_adjoint_step_linear", "lbm_adjoint_set_fused",
+    "lbm_adjoint_kernel_launches",
     "lbm_adjoint_destroy", "lbm_adjoint_last_error",
 ]
 
@@ -156,6 +157,7 @@ def load_library(build_if_missing: bool = False):
             "lbm_adjoint_set_state": (ip, [vp, vp, vp]),
             "lbm_adjoint_get_state": (ip, [vp, vp, vp]),
             "lbm_adjoint_step_linear": (ip, [vp]),
+            "lbm_adjoint_set_fused": (ip, [vp, ip]),
             "lbm_adjoint_kernel_launches": (ctypes.c_longlong, [vp]),
             "lbm_adjoint_destroy": (ip, [vp]),
             "lbm_adjoint_last_error": (ctypes.c_char_p, [vp]),
@@ -578,6 +580,10 @@ class Adjoint:
 
     def step_linear(self):
         self._check(self.L.lbm_adjoint_step_linear(self.h))
+
+    def set_fused(self, fused: bool):
+        """True (default): one fused kernel per adjoint step; False: three."""
+        self._check(self.L.lbm_adjoint_set_fused(self.h, int(bool(fused))))
 
     @property
     def kernel_launches(self) -> int:

@@ -3,11 +3,13 @@
 
 namespace lbm {
 
-cudaError_t adj_step_f64(const AdjParams &a, cudaStream_t s) { return adj_step_t<double>(a, s); }
+cudaError_t adj_step_f64(const AdjParams &a, bool fused, cudaStream_t s) {
+  return adj_step_t<double>(a, fused, s);
+}
 
-cudaError_t adj_inject_f64(void *ubar_r, void *jrec, const int *rec_id, int nrec,
-                           const double *d, cudaStream_t s) {
-  return adj_inject_t<double>(ubar_r, jrec, rec_id, nrec, d, s);
+cudaError_t adj_jrec_f64(const double *d, const int *rec_id, int nrec, int T, void *jrec,
+                         cudaStream_t s) {
+  return adj_jrec_t<double>(d, rec_id, nrec, T, jrec, s);
 }
 
 }  // namespace lbm

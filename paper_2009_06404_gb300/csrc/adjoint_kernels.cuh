@@ -41,12 +41,100 @@ struct AdjParams {
   const void *jrec;    // else: per receiver (sorted order), the adjoint of j/rho0 there
   const void *grad;    // the forward's centred density gradient of step n, 2 planes
   double *g_lam;       // dJ/dLambda, one plane (FP64)
+  void *g_part;        // the last steps' share of dJ/dLambda, one plane (compute type)
+  int flush;           // 1: move g_part into g_lam after this step's share
   double *g_amp;       // dJ/d amplitude, per source (FP64)
   int lam_any;         // some Lambda != 0
 };
 
 template <class C>
 __device__ __forceinline__ const C *cp(const void *v) { return (const C *)v; }
+
+// dJ/dLambda += H_b . b^2 grad rho at plane index c: the product and a
+// partial sum over a few steps in the compute type, moved into the FP64
+// sum when a.flush is set (keeps FP64 arithmetic, slow on this GPU, off
+// most steps).
+template <class C>
+__device__ __forceinline__ void add_lambda_grad(const AdjParams &a, int c, C hbx, C hby) {
+  const C gx = cp<C>(a.grad)[c], gy = cp<C>(a.grad)[a.p.plane + c];
+  C *part = (C *)a.g_part;
+  const C v = part[c] + (hbx * gx + hby * gy) * C(1.0 / 3.0);
+  if (a.flush) {
+    a.g_lam[c] += (double)v;
+    part[c] = C(0);
+  } else {
+    part[c] = v;
+  }
+}
+
+// Adjoint of j / rho0 at cell (x, y) (in the grid): from the full u-adjoint
+// planes (transpose tests) or from the receivers there.
+template <class C>
+__device__ __forceinline__ void jbar_at(const AdjParams &a, int x, int y, C irho, C &jx, C &jy) {
+  const StepParams &p = a.p;
+  jx = C(0);
+  jy = C(0);
+  if (a.ufield) {
+    const int c = y * p.pitch + x;
+    jx = cp<C>(a.ufield)[c] * irho;
+    jy = cp<C>(a.ufield)[p.plane + c] * irho;
+  } else if (p.nrec > 0 && x >= p.rec_x0 && x <= p.rec_x1 && y >= p.rec_y0 && y <= p.rec_y1) {
+    const int tile = (y / kRecTileY) * p.rec_tiles_x + x / kRecTileX;
+    for (int r = p.rec_tile_ptr[tile]; r < p.rec_tile_ptr[tile + 1]; ++r)
+      if (p.rec_xy[2 * r] == x && p.rec_xy[2 * r + 1] == y) {
+        jx += cp<C>(a.jrec)[2 * r];
+        jy += cp<C>(a.jrec)[2 * r + 1];
+      }
+    jx *= irho;
+    jy *= irho;
+  }
+}
+
+// The local transpose at one cell: from the adjoint av of its post-collision
+// populations and jb0 of j, the adjoint g of its pulled populations (without
+// the density-gradient part) and hb of the force H = G + F.
+template <class C>
+__device__ __forceinline__ void local_transpose(const StepParams &p, const C *av, C jbx0, C jby0,
+                                                C A, C *g, C &hbx, C &hby) {
+  const C om = par<C>(p.omega, p.omega_f), kap = par<C>(p.fcoef, p.fcoef_f);
+  const C sig = C(1) / (C(1) + C(0.5) * A);
+  // weighted moments of the adjoint, sum_i w_i a_i (.), with w = 4/9, 1/9,
+  // 1/36 written out (no products with zero lattice components)
+  const C s13 = av[1] + av[3], s24 = av[2] + av[4];
+  const C d13 = av[1] - av[3], d24 = av[2] - av[4];
+  const C s58 = (av[5] + av[7]) + (av[6] + av[8]);
+  const C d5768x = (av[5] - av[7]) + (av[8] - av[6]);  // sum c_x a over 5..8
+  const C d5768y = (av[5] - av[7]) + (av[6] - av[8]);  // sum c_y a over 5..8
+  const C d5768xy = (av[5] + av[7]) - (av[6] + av[8]); // sum c_x c_y a over 5..8
+  // rho: w_i (2 - 1.5 |c_i|^2) = 8/9, 1/18, -1/36
+  const C rs = C(8.0 / 9.0) * av[0] + C(1.0 / 18.0) * (s13 + s24) - C(1.0 / 36.0) * s58;
+  const C jx = C(1.0 / 9.0) * d13 + C(1.0 / 36.0) * d5768x;
+  const C jy = C(1.0 / 9.0) * d24 + C(1.0 / 36.0) * d5768y;
+  // w_i (c_x^2 - 1/3): -4/27, 2/27 (x links), -1/27 (y links), 1/54 (diagonals)
+  const C pxx = C(-4.0 / 27.0) * av[0] + C(2.0 / 27.0) * s13 - C(1.0 / 27.0) * s24 +
+                C(1.0 / 54.0) * s58;
+  const C pyy = C(-4.0 / 27.0) * av[0] + C(2.0 / 27.0) * s24 - C(1.0 / 27.0) * s13 +
+                C(1.0 / 54.0) * s58;
+  const C pxy = C(1.0 / 36.0) * d5768xy;
+  const C rho_b = om * rs;
+  const C jbx = jbx0 + om * C(3) * jx, jby = jby0 + om * C(3) * jy;
+  const C sbx = kap * C(3) * jx, sby = kap * C(3) * jy;
+  const C pbxx = om * C(4.5) * pxx, pbyy = om * C(4.5) * pyy, pbxy = om * C(9) * pxy;
+  hbx = sig * sbx + C(0.5) * sig * jbx;
+  hby = sig * sby + C(0.5) * sig * jby;
+  const C mbx = sig * jbx - A * sig * sbx, mby = sig * jby - A * sig * sby;
+  const C k1 = C(1) - om;
+  const C dd = rho_b + pbxx + pbyy;  // diagonal links: rho, P_xx and P_yy
+  g[0] = k1 * av[0] + rho_b;
+  g[1] = k1 * av[1] + (rho_b + pbxx) + mbx;
+  g[3] = k1 * av[3] + (rho_b + pbxx) - mbx;
+  g[2] = k1 * av[2] + (rho_b + pbyy) + mby;
+  g[4] = k1 * av[4] + (rho_b + pbyy) - mby;
+  g[5] = k1 * av[5] + (dd + pbxy) + (mbx + mby);
+  g[7] = k1 * av[7] + (dd + pbxy) - (mbx + mby);
+  g[6] = k1 * av[6] + (dd - pbxy) + (mby - mbx);
+  g[8] = k1 * av[8] + (dd - pbxy) - (mby - mbx);
+}
 
 // Local transpose of the collision, forcing, sponge and displacement update,
 // and the gradient accumulation.  Blocks of 32 x 8 cells; inactive lanes of
@@ -64,61 +152,23 @@ __global__ void __launch_bounds__(256) adj_local_kernel(const AdjParams a) {
   for (int i = 0; i < 9; ++i) av[i] = cp<C>(a.abar)[cf + i * p.fplane];
   const C irho = mat_at<C>(p.irho, p.mat_per_cell, xc, yc, p.pitch);
   // adjoint of j from u' = u + j/rho0 and v = j/rho0
-  C jbx0 = C(0), jby0 = C(0);
-  if (a.ufield) {
-    jbx0 = cp<C>(a.ufield)[c] * irho;
-    jby0 = cp<C>(a.ufield)[p.plane + c] * irho;
-  } else if (p.nrec > 0 && active && x >= p.rec_x0 && x <= p.rec_x1 && y >= p.rec_y0 &&
-             y <= p.rec_y1) {
-    const int tile = (y / kRecTileY) * p.rec_tiles_x + x / kRecTileX;
-    for (int r = p.rec_tile_ptr[tile]; r < p.rec_tile_ptr[tile + 1]; ++r)
-      if (p.rec_xy[2 * r] == x && p.rec_xy[2 * r + 1] == y) {
-        jbx0 += cp<C>(a.jrec)[2 * r];
-        jby0 += cp<C>(a.jrec)[2 * r + 1];
-      }
-    jbx0 *= irho;
-    jby0 *= irho;
-  }
-  const C om = par<C>(p.omega, p.omega_f), kap = par<C>(p.fcoef, p.fcoef_f);
-  const C A = sponge_A<C>(p, xc, yc);
-  const C sig = C(1) / (C(1) + C(0.5) * A);
-  C rs = C(0), jx = C(0), jy = C(0), pxx = C(0), pyy = C(0), pxy = C(0);
-#pragma unroll
-  for (int i = 0; i < 9; ++i) {
-    const int cx = cxd(i), cy = cyd(i), cc = cx * cx + cy * cy;
-    const C wa = wd<C>(i) * av[i];
-    rs += wa * (C(2) - C(1.5) * C(cc));
-    jx += wa * C(cx);
-    jy += wa * C(cy);
-    pxx += wa * (C(cx * cx) - C(1.0 / 3.0));
-    pyy += wa * (C(cy * cy) - C(1.0 / 3.0));
-    pxy += wa * C(cx * cy);
-  }
-  const C rho_b = om * rs;
-  const C jbx = jbx0 + om * C(3) * jx, jby = jby0 + om * C(3) * jy;
-  const C sbx = kap * C(3) * jx, sby = kap * C(3) * jy;
-  const C pbxx = om * C(4.5) * pxx, pbyy = om * C(4.5) * pyy, pbxy = om * C(9) * pxy;
-  const C hbx = sig * sbx + C(0.5) * sig * jbx, hby = sig * sby + C(0.5) * sig * jby;
-  const C mbx = sig * jbx - A * sig * sbx, mby = sig * jby - A * sig * sby;
+  C jbx0, jby0;
+  jbar_at<C>(a, xc, yc, irho, jbx0, jby0);
+  if (!active) jbx0 = jby0 = C(0);
+  C g[9], hbx, hby;
+  local_transpose<C>(p, av, jbx0, jby0, sponge_A<C>(p, xc, yc), g, hbx, hby);
   if (active) {
     C *gb = (C *)a.gbar;
 #pragma unroll
-    for (int i = 0; i < 9; ++i) {
-      const int cx = cxd(i), cy = cyd(i);
-      gb[cf + i * p.fplane] = (C(1) - om) * av[i] + rho_b + C(cx) * mbx + C(cy) * mby +
-                              C(cx * cx) * pbxx + C(cy * cy) * pbyy + C(cx * cy) * pbxy;
-    }
+    for (int i = 0; i < 9; ++i) gb[cf + i * p.fplane] = g[i];
     const C lam = mat_at<C>(p.lam, p.mat_per_cell, xc, yc, p.pitch);
     if (a.lam_any) {
       C *wb = (C *)a.wbar;
       wb[c] = lam * C(1.0 / 3.0) * C(0.5) * hbx;
       wb[p.plane + c] = lam * C(1.0 / 3.0) * C(0.5) * hby;
     }
-    if (a.grad) {
-      // dG/dLambda = b^2 grad rho of the forward step
-      const double gx = (double)cp<C>(a.grad)[c], gy = (double)cp<C>(a.grad)[p.plane + c];
-      a.g_lam[c] += ((double)hbx * gx + (double)hby * gy) * (1.0 / 3.0);
-    }
+    // dG/dLambda = b^2 grad rho of the forward step
+    if (a.grad) add_lambda_grad<C>(a, c, hbx, hby);
   }
   // amplitude gradient: dF/dA_s = dir_s g_s(x) r_s(n); warps cull sources
   // like the forward's body force (all lanes of a warp share one row)
@@ -317,44 +367,260 @@ __global__ void __launch_bounds__(256) adj_pull_kernel(const AdjParams a) {
   for (int j = 0; j < 9; ++j) o[j * p.fplane] = out[j];
 }
 
-// Receiver adjoints of step n (receivers in the sorted order of the
-// receiver table): ubar_r += du (the adjoint of u^{n+1}, carried by every
-// later u), jrec_r = ubar_r + dv (with dv the adjoint of v^n; both enter as
-// j / rho0).  d: [nrec][4] of this step by original receiver index.
+// ------------------------------------------------------------ fused form
+//
+// The whole adjoint step in one kernel: a block of 32 x 8 cells computes the
+// local transposes of its cells and of a two-cell ring around them (36 x 12
+// cells; periodic axes wrapped, cells beyond a non-periodic edge zero) into
+// shared memory, then the density adjoint of the inner 34 x 10 cells, then
+// the push of its own cells.  Each population adjoint is read once from
+// HBM by its own block (the ring comes from L2) and written once.
+constexpr int kAdjTW = 32, kAdjTH = 8;
+#ifndef LBM_ADJ_MIN_BLOCKS
+#define LBM_ADJ_MIN_BLOCKS 4
+#endif
+constexpr int kAdjW2 = kAdjTW + 4, kAdjH2 = kAdjTH + 4;
+constexpr int kAdjW1 = kAdjTW + 2, kAdjH1 = kAdjTH + 2;
+
+// div_axis on a shared-memory row or column: the neighbours sit at +-stride
+// (the ring holds the wrapped cells of periodic axes); k is the global index.
 template <class C>
-__global__ void adj_inject_kernel(C *ubar_r, C *jrec, const int *rec_id, int nrec,
-                                  const double *d) {
-  for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < nrec; r += gridDim.x * blockDim.x) {
-    const double *q = d + 4 * (long long)rec_id[r];
-    const C ux = ubar_r[2 * r] + C(q[0]), uy = ubar_r[2 * r + 1] + C(q[1]);
-    ubar_r[2 * r] = ux;
-    ubar_r[2 * r + 1] = uy;
-    jrec[2 * r] = ux + C(q[2]);
-    jrec[2 * r + 1] = uy + C(q[3]);
+__device__ __forceinline__ C div_axis_s(const C *w, int stride, int n, int k, bool per, int bc_lo,
+                                        int bc_hi, int fs_order) {
+  const bool lin_lo = bc_lo == BC_FREE && fs_order == 1;
+  const bool lin_hi = bc_hi == BC_FREE && fs_order == 1;
+  C r = C(0);
+  if (k > 0 || per) {
+    const C v = w[-stride];
+    r += v;
+    if (!per && k == 1 && lin_lo) r += v;
+  }
+  if (k < n - 1 || per) {
+    const C v = w[stride];
+    r -= v;
+    if (!per && k == n - 2 && lin_hi) r -= v;
+  }
+  if (!per) {
+    const C v = w[0];
+    if (k == 0) r += lin_lo ? C(-2) * v : -v;
+    if (k == n - 1) r += lin_hi ? C(2) * v : v;
+  }
+  return r;
+}
+
+template <class C>
+struct AdjSmem {
+  C g[9][kAdjH1][kAdjW1];  // local adjoint of the pulled populations
+  C r[kAdjH1][kAdjW1];     // density adjoint
+  C w[2][kAdjH2][kAdjW2];  // Lambda b^2 H_b / 2
+};
+
+// Total adjoint of pulled population i at tile-relative cell (hx, hy),
+// -1 <= hx <= 32, -1 <= hy <= 8.
+template <class C>
+__device__ __forceinline__ C gtot_s(const AdjSmem<C> &S, bool lam_any, int hx, int hy, int i) {
+  C g = S.g[i][hy + 1][hx + 1];
+  if (lam_any) g += S.r[hy + 1][hx + 1];
+  return g;
+}
+
+template <class C>
+__global__ void __launch_bounds__(256, LBM_ADJ_MIN_BLOCKS) adj_fused_kernel(const AdjParams a) {
+  const StepParams &p = a.p;
+  __shared__ AdjSmem<C> S;
+  const int t = threadIdx.y * 32 + threadIdx.x;
+  const int x0 = blockIdx.x * kAdjTW, y0 = blockIdx.y * kAdjTH;
+  const bool perx = p.bc_left == BC_PERIODIC, pery = p.bc_top == BC_PERIODIC;
+  const bool src_blk = a.g_amp != nullptr && p.nsrc > 0 && x0 <= p.src_x1 &&
+                       x0 + kAdjTW - 1 >= p.src_x0 && y0 <= p.src_y1 &&
+                       y0 + kAdjTH - 1 >= p.src_y0;
+  // ---- local transposes of the block and its two-cell ring
+  for (int k = t; k < kAdjW2 * kAdjH2; k += 256) {
+    const int hx = k % kAdjW2 - 2, hy = k / kAdjW2 - 2;
+    int gx = x0 + hx, gy = y0 + hy;
+    bool ex = true;
+    if (gx < 0 || gx >= p.nx) {
+      if (perx) gx = ((gx % p.nx) + p.nx) % p.nx;
+      else ex = false;
+    }
+    if (gy < 0 || gy >= p.ny) {
+      if (pery) gy = ((gy % p.ny) + p.ny) % p.ny;
+      else ex = false;
+    }
+    C g[9], hbx = C(0), hby = C(0), lam = C(0);
+#pragma unroll
+    for (int i = 0; i < 9; ++i) g[i] = C(0);
+    if (ex) {
+      const long long cf = (long long)gy * p.frow + gx;
+      C av[9];
+#pragma unroll
+      for (int i = 0; i < 9; ++i) av[i] = cp<C>(a.abar)[cf + i * p.fplane];
+      const C irho = mat_at<C>(p.irho, p.mat_per_cell, gx, gy, p.pitch);
+      lam = mat_at<C>(p.lam, p.mat_per_cell, gx, gy, p.pitch);
+      C jbx0, jby0;
+      jbar_at<C>(a, gx, gy, irho, jbx0, jby0);
+      local_transpose<C>(p, av, jbx0, jby0, sponge_A<C>(p, gx, gy), g, hbx, hby);
+      // the block's own cells (unwrapped, inside the grid): gradient sums
+      const bool own = hx >= 0 && hx < kAdjTW && hy >= 0 && hy < kAdjTH &&
+                       x0 + hx < p.nx && y0 + hy < p.ny;
+      if (own && a.grad) add_lambda_grad<C>(a, gy * p.pitch + gx, hbx, hby);
+      if (own && src_blk) {
+        // dF/dA_s = dir_s g_s(x) r_s(n) (integer footprint test first)
+        for (int s = 0; s < p.nsrc; ++s) {
+          const SourceDev &q = p.src[s];
+          int dy = gy - q.yc, dx = gx - q.xc;
+          if (pery) {
+            if (dy > p.ny / 2) dy -= p.ny;
+            else if (dy < -(p.ny / 2)) dy += p.ny;
+          }
+          if (perx) {
+            if (dx > p.nx / 2) dx -= p.nx;
+            else if (dx < -(p.nx / 2)) dx += p.nx;
+          }
+          if (abs(dy) > q.rb || abs(dx) > q.rb) continue;
+          const double v = ((double)hbx * q.dirx + (double)hby * q.diry) *
+                           source_shape(q, gx, gy, p.n, p.nx, p.ny, perx, pery);
+          if (v != 0.0) atomicAdd(&a.g_amp[s], v);
+        }
+      }
+    }
+    S.w[0][hy + 2][hx + 2] = lam * C(1.0 / 3.0) * C(0.5) * hbx;
+    S.w[1][hy + 2][hx + 2] = lam * C(1.0 / 3.0) * C(0.5) * hby;
+    if (hx >= -1 && hx <= kAdjTW && hy >= -1 && hy <= kAdjTH) {
+#pragma unroll
+      for (int i = 0; i < 9; ++i) S.g[i][hy + 1][hx + 1] = g[i];
+    }
+  }
+  __syncthreads();
+  // ---- density adjoint of the block and its one-cell ring
+  if (a.lam_any) {
+    for (int k = t; k < kAdjW1 * kAdjH1; k += 256) {
+      const int hx = k % kAdjW1 - 1, hy = k / kAdjW1 - 1;
+      int gx = x0 + hx, gy = y0 + hy;
+      bool ex = true;
+      if (gx < 0 || gx >= p.nx) {
+        if (perx) gx = ((gx % p.nx) + p.nx) % p.nx;
+        else ex = false;
+      }
+      if (gy < 0 || gy >= p.ny) {
+        if (pery) gy = ((gy % p.ny) + p.ny) % p.ny;
+        else ex = false;
+      }
+      C r = C(0);
+      if (ex) {
+        r = div_axis_s<C>(&S.w[0][hy + 2][hx + 2], 1, p.nx, gx, perx, p.bc_left, p.bc_right,
+                          p.fs_order) +
+            div_axis_s<C>(&S.w[1][hy + 2][hx + 2], kAdjW2, p.ny, gy, pery, p.bc_top,
+                          p.bc_bottom, p.fs_order);
+      }
+      S.r[hy + 1][hx + 1] = r;
+    }
+  }
+  __syncthreads();
+  // ---- the push, gathered per own cell
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  const int x = x0 + tx, y = y0 + ty;
+  if (x >= p.nx || y >= p.ny) return;
+  const bool lin = p.fs_order == 1;
+  const bool la = a.lam_any != 0;
+  C out[9];
+  if (x0 >= 2 && x0 + kAdjTW <= p.nx - 2 && y0 >= 2 && y0 + kAdjTH <= p.ny - 2) {
+    // no cell of the block is within two cells of an edge: every link is a
+    // plain pull and no wall rule involves the block
+#pragma unroll
+    for (int j = 0; j < 9; ++j) out[j] = gtot_s<C>(S, la, tx + cxd(j), ty + cyd(j), j);
+    C *o = (C *)a.abar_out + (long long)y * p.frow + x;
+#pragma unroll
+    for (int j = 0; j < 9; ++j) o[j * p.fplane] = out[j];
+    return;
+  }
+  bool wall_cell = false;
+#pragma unroll
+  for (int j = 0; j < 9; ++j) {
+    int wx, wy, bc, hz;
+    if (!link_wall(p, x, y, j, wx, wy, bc, hz)) {
+      out[j] = gtot_s<C>(S, la, tx + cxd(j), ty + cyd(j), j);
+    } else {
+      wall_cell = true;
+      const C gi = gtot_s<C>(S, la, tx, ty, oppd(j));
+      out[j] = bc == BC_RIGID ? gi : -gi;
+    }
+  }
+  if (wall_cell) {
+    for (int j = 1; j < 9; ++j) {
+      int wx, wy, bc, hz;
+      if (!link_wall(p, x, y, j, wx, wy, bc, hz) || bc != BC_FREE) continue;
+      C rb, tb;
+      abb_moments<C>(gtot_s<C>(S, la, tx, ty, oppd(j)), j, hz, rb, tb);
+      spread_moments<C>(out, rb, tb, hz, lin ? C(1.5) : C(1));
+    }
+  }
+  if (lin) {
+    // this cell as the inner cell of a free-surface boundary cell
+    auto inner = [&](int xb, int yb, int rx, int ry, int hzw) {
+      for (int j = 1; j < 9; ++j) {
+        int wx, wy, bc, h;
+        if (!link_wall(p, xb, yb, j, wx, wy, bc, h)) continue;
+        if (bc != BC_FREE || h != hzw) continue;
+        C rb, tb;
+        abb_moments<C>(gtot_s<C>(S, la, rx, ry, oppd(j)), j, hzw, rb, tb);
+        spread_moments<C>(out, rb, tb, hzw, C(-0.5));
+      }
+    };
+    if (p.bc_top == BC_FREE && y == 1) inner(x, 0, tx, ty - 1, 1);
+    if (p.bc_bottom == BC_FREE && y == p.ny - 2) inner(x, p.ny - 1, tx, ty + 1, 1);
+    if (p.bc_left == BC_FREE && x == 1) inner(0, y, tx - 1, ty, 0);
+    if (p.bc_right == BC_FREE && x == p.nx - 2) inner(p.nx - 1, y, tx + 1, ty, 0);
+  }
+  C *o = (C *)a.abar_out + (long long)y * p.frow + x;
+#pragma unroll
+  for (int j = 0; j < 9; ++j) o[j * p.fplane] = out[j];
+}
+
+// The receiver adjoints of every step at once, in the sorted receiver order:
+// jrec[n][r] = sum_{m >= n} du[m][r] + dv[n][r], the adjoint of j / rho0 of
+// step n at receiver r (u^{m+1} carries j^n for every m >= n).  d:
+// [T][nrec][4] by original receiver index.  One thread per receiver.
+template <class C>
+__global__ void adj_jrec_kernel(const double *d, const int *rec_id, int nrec, int T, C *jrec) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= nrec) return;
+  const long long id = rec_id[r];
+  double ux = 0.0, uy = 0.0;
+  for (int n = T - 1; n >= 0; --n) {
+    const double *q = d + ((long long)n * nrec + id) * 4;
+    ux += q[0];
+    uy += q[1];
+    jrec[((long long)n * nrec + r) * 2] = C(ux + q[2]);
+    jrec[((long long)n * nrec + r) * 2 + 1] = C(uy + q[3]);
   }
 }
 
 // Launchers (one translation unit per compute type).
-cudaError_t adj_step_f32(const AdjParams &a, cudaStream_t s);
-cudaError_t adj_step_f64(const AdjParams &a, cudaStream_t s);
-cudaError_t adj_inject_f32(void *ubar_r, void *jrec, const int *rec_id, int nrec,
-                           const double *d, cudaStream_t s);
-cudaError_t adj_inject_f64(void *ubar_r, void *jrec, const int *rec_id, int nrec,
-                           const double *d, cudaStream_t s);
+cudaError_t adj_step_f32(const AdjParams &a, bool fused, cudaStream_t s);
+cudaError_t adj_step_f64(const AdjParams &a, bool fused, cudaStream_t s);
+cudaError_t adj_jrec_f32(const double *d, const int *rec_id, int nrec, int T, void *jrec,
+                         cudaStream_t s);
+cudaError_t adj_jrec_f64(const double *d, const int *rec_id, int nrec, int T, void *jrec,
+                         cudaStream_t s);
 
 template <class C>
-cudaError_t adj_step_t(const AdjParams &a, cudaStream_t s) {
+cudaError_t adj_step_t(const AdjParams &a, bool fused, cudaStream_t s) {
   const dim3 block(32, 8), grid((a.p.nx + 31) / 32, (a.p.ny + 7) / 8);
-  adj_local_kernel<C><<<grid, block, 0, s>>>(a);
-  if (a.lam_any) adj_div_kernel<C><<<grid, block, 0, s>>>(a);
-  adj_pull_kernel<C><<<grid, block, 0, s>>>(a);
+  if (fused) {
+    adj_fused_kernel<C><<<grid, block, 0, s>>>(a);
+  } else {
+    adj_local_kernel<C><<<grid, block, 0, s>>>(a);
+    if (a.lam_any) adj_div_kernel<C><<<grid, block, 0, s>>>(a);
+    adj_pull_kernel<C><<<grid, block, 0, s>>>(a);
+  }
   return cudaGetLastError();
 }
 
 template <class C>
-cudaError_t adj_inject_t(void *ubar_r, void *jrec, const int *rec_id, int nrec, const double *d,
-                         cudaStream_t s) {
-  adj_inject_kernel<C><<<(nrec + 127) / 128, 128, 0, s>>>((C *)ubar_r, (C *)jrec, rec_id, nrec, d);
+cudaError_t adj_jrec_t(const double *d, const int *rec_id, int nrec, int T, void *jrec,
+                       cudaStream_t s) {
+  adj_jrec_kernel<C><<<(nrec + 127) / 128, 128, 0, s>>>(d, rec_id, nrec, T, (C *)jrec);
   return cudaGetLastError();
 }
 

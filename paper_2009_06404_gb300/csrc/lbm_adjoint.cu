@@ -15,11 +15,14 @@ using namespace lbm;
 namespace {
 
 constexpr size_t kAdjAlign = 256;
+// steps whose Lambda-gradient shares are summed in the compute type before
+// they are added to the FP64 sum (step 0 always flushes)
+constexpr int kFlushSteps = 16;
 
 size_t aup(size_t v) { return (v + kAdjAlign - 1) / kAdjAlign * kAdjAlign; }
 
 struct AdjLayout {
-  size_t abar[2] = {0, 0}, gbar = 0, wbar = 0, rbar = 0, ubar = 0, urec = 0, jrec = 0, glam = 0,
+  size_t abar[2] = {0, 0}, gbar = 0, wbar = 0, rbar = 0, ubar = 0, jrec = 0, glam = 0, gpart = 0,
          gamp = 0, grad = 0, ckpt = 0, total = 0;
   size_t state_f = 0, state_u = 0, ckpt_bytes = 0, csize = 0;
   int nck = 0;
@@ -47,9 +50,9 @@ AdjLayout adj_layout(const lbm_elastic_t *h, int nsteps, int K) {
   A.rbar = take(pl * A.csize);
   A.ubar = take(2 * pl * A.csize);
   const size_t nr = (size_t)std::max(1, h->cfg.max_receivers);
-  A.urec = take(2 * nr * A.csize);
-  A.jrec = take(2 * nr * A.csize);
+  A.jrec = take((size_t)nsteps * nr * 2 * A.csize);
   A.glam = take(pl * sizeof(double));
+  A.gpart = take(pl * A.csize);
   A.gamp = take((size_t)std::max(1, h->cfg.max_sources) * sizeof(double));
   A.grad = take((size_t)K * 2 * pl * A.csize);
   A.ckpt = take((size_t)(A.nck + 1) * A.ckpt_bytes);  // + the final state
@@ -117,6 +120,8 @@ struct lbm_adjoint {
   long long n_start = 0;  // step index of the handle when forward began
   int traced_start = 0;
   int cur_a = 0;          // adjoint buffer holding the current adjoint state
+  bool fused = true;      // one fused kernel per adjoint step (else three)
+  int grads_seg = -1;     // segment whose density gradients the slots hold
   long long launches = 0;
   std::string err;
 };
@@ -150,16 +155,19 @@ AdjParams params_of(lbm_adjoint_t *a, long long n) {
   P.jrec = a->ws + a->A.jrec;
   P.grad = nullptr;
   P.g_lam = (double *)(a->ws + a->A.glam);
+  P.g_part = a->ws + a->A.gpart;
+  P.flush = 0;
   P.g_amp = nullptr;
   P.lam_any = a->h->lambda_nonzero ? 1 : 0;
   return P;
 }
 
 lbm_status adj_launch(lbm_adjoint_t *a, const AdjParams &P) {
-  const cudaError_t e = a->f64 ? adj_step_f64(P, a->h->stream) : adj_step_f32(P, a->h->stream);
+  const cudaError_t e = a->f64 ? adj_step_f64(P, a->fused, a->h->stream)
+                               : adj_step_f32(P, a->fused, a->h->stream);
   if (e != cudaSuccess)
     return afail(a, LBM_ERR_CUDA, std::string("adjoint step: ") + cudaGetErrorString(e));
-  a->launches += P.lam_any ? 3 : 2;
+  a->launches += a->fused ? 1 : (P.lam_any ? 3 : 2);
   a->cur_a ^= 1;
   return LBM_OK;
 }
@@ -235,6 +243,7 @@ lbm_status lbm_adjoint_forward(lbm_adjoint_t *a) {
   }
   if (lbm_status st = ckpt_io(a, a->A.nck, true)) return st;
   a->forward_done = true;
+  a->grads_seg = a->A.nck - 1;  // the forward run just stored the last segment's
   return LBM_OK;
 }
 
@@ -247,9 +256,17 @@ lbm_status lbm_adjoint_backward(lbm_adjoint_t *a, const double *d_dtraces) {
   cudaStream_t s = h->stream;
   a->cur_a = 0;
   ADJ_CUDA(a, cudaMemsetAsync(a->ws + a->A.abar[0], 0, 9 * pl * a->A.csize, s));
-  ADJ_CUDA(a, cudaMemsetAsync(a->ws + a->A.urec, 0,
-                              2 * (size_t)std::max(1, h->cfg.max_receivers) * a->A.csize, s));
+  if (h->nrec > 0) {
+    const int *rid = (const int *)(h->ws + h->L.rec_id);
+    const cudaError_t e =
+        a->f64 ? adj_jrec_f64(d_dtraces, rid, h->nrec, a->nsteps, a->ws + a->A.jrec, s)
+               : adj_jrec_f32(d_dtraces, rid, h->nrec, a->nsteps, a->ws + a->A.jrec, s);
+    if (e != cudaSuccess)
+      return afail(a, LBM_ERR_CUDA, std::string("receiver adjoints: ") + cudaGetErrorString(e));
+    a->launches++;
+  }
   ADJ_CUDA(a, cudaMemsetAsync(a->ws + a->A.glam, 0, pl * sizeof(double), s));
+  ADJ_CUDA(a, cudaMemsetAsync(a->ws + a->A.gpart, 0, pl * a->A.csize, s));
   ADJ_CUDA(a, cudaMemsetAsync(a->ws + a->A.gamp, 0,
                               std::max(1, h->cfg.max_sources) * sizeof(double), s));
   const int traced_keep = h->traced;
@@ -257,24 +274,19 @@ lbm_status lbm_adjoint_backward(lbm_adjoint_t *a, const double *d_dtraces) {
   lbm_status st = LBM_OK;
   for (int seg = a->A.nck - 1; seg >= 0 && !st; --seg) {
     const int n0 = seg * a->K, n1 = std::min(a->nsteps, n0 + a->K);
-    if ((st = ckpt_io(a, seg, false))) break;
-    h->step = a->n_start + n0;
-    for (int n = n0; n < n1 && !st; ++n) st = capture_step(a, n - n0);
+    if (seg != a->grads_seg) {
+      // recompute the segment from its checkpoint, storing its gradients
+      if ((st = ckpt_io(a, seg, false))) break;
+      h->step = a->n_start + n0;
+      for (int n = n0; n < n1 && !st; ++n) st = capture_step(a, n - n0);
+      a->grads_seg = seg;
+    }
     for (int n = n1 - 1; n >= n0 && !st; --n) {
       AdjParams P = params_of(a, a->n_start + n);
-      if (h->nrec > 0) {
-        const double *d = d_dtraces + (size_t)n * h->nrec * 4;
-        const int *rid = (const int *)(h->ws + h->L.rec_id);
-        void *ur = a->ws + a->A.urec, *jr = a->ws + a->A.jrec;
-        const cudaError_t e = a->f64 ? adj_inject_f64(ur, jr, rid, h->nrec, d, s)
-                                     : adj_inject_f32(ur, jr, rid, h->nrec, d, s);
-        if (e != cudaSuccess) {
-          st = afail(a, LBM_ERR_CUDA, std::string("adjoint inject: ") + cudaGetErrorString(e));
-          break;
-        }
-        a->launches++;
-      }
+      P.jrec = a->ws + a->A.jrec + (size_t)n * h->nrec * 2 * a->A.csize;
       P.grad = grad_slot(a, n - n0);
+      // the compute-type partial sum spans at most kFlushSteps steps
+      P.flush = (n % kFlushSteps == 0) ? 1 : 0;
       P.g_amp = (double *)(a->ws + a->A.gamp);
       st = adj_launch(a, P);
     }
@@ -353,6 +365,12 @@ lbm_status lbm_adjoint_step_linear(lbm_adjoint_t *a) {
   P.p.nsrc = 0;
   P.ufield = a->ws + a->A.ubar;
   return adj_launch(a, P);
+}
+
+lbm_status lbm_adjoint_set_fused(lbm_adjoint_t *a, int fused) {
+  if (!a) return LBM_ERR_ARG;
+  a->fused = fused != 0;
+  return LBM_OK;
 }
 
 long long lbm_adjoint_kernel_launches(const lbm_adjoint_t *a) { return a ? a->launches : -1; }

@@ -69,16 +69,18 @@ def _sim(nx, ny, storage, bc, sponge, fs_order, seed, tau=0.8, **kw):
     return sim, (rho0, lam, mu)
 
 
+@pytest.mark.parametrize("fused", [True, False])
 @pytest.mark.parametrize("storage,tol", [("f64", 1e-13), ("f32", 2e-5)])
 @pytest.mark.parametrize("bcname", sorted(BCS))
 @pytest.mark.parametrize("nx,ny", [(13, 7), (70, 45)])
 @pytest.mark.parametrize("fs_order", [0, 1])
-def test_adjoint_step_is_the_transpose(storage, tol, bcname, nx, ny, fs_order):
+def test_adjoint_step_is_the_transpose(storage, tol, bcname, nx, ny, fs_order, fused):
     bc, sponge = BCS[bcname]
     if fs_order == 1 and "free" not in bc:
         pytest.skip("extrapolation order only matters at a free surface")
     sim, _ = _sim(nx, ny, storage, bc, sponge, fs_order, seed=nx * 7 + ny)
     adj = _pkg().Adjoint(sim, 1, 1)
+    adj.set_fused(fused)
     g = torch.Generator(device="cpu").manual_seed(nx + 100 * ny + fs_order)
     f = torch.randn((9, ny, nx), generator=g, dtype=torch.float64).cuda()
     u = torch.randn((2, ny, nx), generator=g, dtype=torch.float64).cuda()
@@ -111,13 +113,14 @@ def _tiny_workload(fs_order, bc, sponge, seed=7):
                        sources=src, receivers=rec)
 
 
+@pytest.mark.parametrize("fused", [True, False])
 @pytest.mark.parametrize("fs_order,bc,sponge", [
     (1, ("free", "rigid", "periodic", "periodic"), (0, 2, 0, 0)),
     (0, ("free", "free", "rigid", "rigid"), (0, 0, 2, 0)),
     (1, ("free", "free", "free", "free"), (0, 0, 0, 2)),
     (0, ("periodic",) * 4, (0, 0, 0, 0)),
 ])
-def test_gradients_match_oracle_discrete_adjoint(fs_order, bc, sponge):
+def test_gradients_match_oracle_discrete_adjoint(fs_order, bc, sponge, fused):
     """dJ/dLambda per cell and dJ/dA per source for a misfit against noisy
     data, 12 steps with a checkpoint every 5 (FP64): the CUDA adjoint equals
     the oracle's brute-force reverse mode to 1e-10."""
@@ -130,6 +133,7 @@ def test_gradients_match_oracle_discrete_adjoint(fs_order, bc, sponge):
     pkg = _pkg()
     sim = pkg.from_workload(w, storage="f64", max_steps_traced=T)
     adj = pkg.Adjoint(sim, T, 5)
+    adj.set_fused(fused)
     trg = adj.forward()
     assert np.allclose(trg.cpu().numpy(), tr, rtol=0, atol=1e-12 * np.abs(tr).max())
     adj.backward(torch.as_tensor(oadj.misfit_trace_adjoint(tr, data), device="cuda"))
@@ -145,6 +149,53 @@ def test_gradients_match_oracle_discrete_adjoint(fs_order, bc, sponge):
     f = sim.read_fields(("ux",), on_device=False)
     st, _ = oracle.run(prob, T)
     assert np.allclose(f["ux"], st.u[0], rtol=0, atol=1e-12 * np.abs(st.u).max())
+
+
+@pytest.mark.parametrize("storage", ["f64", "f32"])
+def test_fused_adjoint_equals_three_kernel_form(storage):
+    """The fused adjoint step and the three-kernel form compute the same
+    transpose: identical dJ/dLambda and amplitude gradients (up to the order of
+    the amplitude's atomic sums) on a ragged layered half-space with sources
+    and receivers near the edges, through checkpoints."""
+    wl = _wl()
+    w = wl.layered_halfspace(70, 45, 60, seed=21, sponge=6, nrec=9, storage=storage,
+                             src_x=30.0, src_y=3.0)
+    w = w.with_(fs_order=1)
+    out = {}
+    for fused in (True, False):
+        sim = _pkg().from_workload(w, storage=storage, max_steps_traced=60)
+        adj = _pkg().Adjoint(sim, 60, 16)
+        adj.set_fused(fused)
+        tr = adj.forward()
+        d = tr.clone()
+        d[..., :2] -= 0.1 * tr[..., :2].abs().max()
+        adj.backward(tr - d)
+        g = adj.gradients()
+        out[fused] = (g["Lambda"].cpu().numpy(), g["amplitude"].cpu().numpy())
+    assert np.array_equal(out[True][0], out[False][0])
+    assert np.allclose(out[True][1], out[False][1], rtol=1e-12, atol=0)
+    assert np.abs(out[True][0]).max() > 0
+
+
+def test_backward_twice_is_reproducible():
+    """The first reverse sweep reuses the density gradients the forward run
+    stored for its last segment; the second recomputes every segment.  Both
+    give the same gradients bit for bit, and K = T (no recomputation at all)
+    gives them too."""
+    wl = _wl()
+    w = wl.layered_halfspace(70, 45, 48, seed=22, sponge=6, nrec=9, storage="f32",
+                             src_x=30.0, src_y=3.0)
+    res = []
+    for K in (16, 48):
+        sim = _pkg().from_workload(w, storage="f32", max_steps_traced=48)
+        adj = _pkg().Adjoint(sim, 48, K)
+        tr = adj.forward()
+        dtr = tr * 0.5
+        for _ in range(2):
+            adj.backward(dtr)
+            res.append(adj.gradients()["Lambda"].cpu().numpy())
+    assert all(np.array_equal(res[0], r) for r in res[1:])
+    assert np.abs(res[0]).max() > 0
 
 
 def _blob_setup(nx, ny, nsteps, storage, K):
