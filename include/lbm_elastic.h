@@ -149,6 +149,15 @@ lbm_status lbm_elastic_set_sources(lbm_elastic_t *h, const lbm_source *src, int 
  * taken afterwards are recorded from trace slot 0. */
 lbm_status lbm_elastic_set_receivers(lbm_elastic_t *h, const int *xy, int n);
 
+/* Replaces the absorbing layers (Sec. 6.4, Eq. 44) of a running simulation:
+ * thicknesses in cells (>= 0, each opposite pair at most the grid's extent)
+ * and A_max (<= 0: 12.8 / L per layer).  The state is kept; the next step
+ * uses the new layers.  The boundary kinds of the edges stay as created
+ * (the paper's surface-wave experiment of Sec. 7 removes the lateral layers
+ * of a laterally periodic grid after 400 steps). */
+lbm_status lbm_elastic_set_sponges(lbm_elastic_t *h, int top, int bottom, int left, int right,
+                                   double amax);
+
 /* Back to rest: f* = 0, u = 0, step index 0, traces cleared, error flag
  * cleared.  Material, sources and receivers are kept.  Asynchronous. */
 lbm_status lbm_elastic_reset(lbm_elastic_t *h);

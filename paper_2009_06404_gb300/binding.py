@@ -28,7 +28,8 @@ KERNEL = {"auto": 0, "simple": 1, "tma": 2}
 #: the exported symbols, as declared in include/lbm_elastic.h
 SYMBOLS = [
     "lbm_elastic_workspace_bytes", "lbm_elastic_create", "lbm_elastic_set_material",
-    "lbm_elastic_set_sources", "lbm_elastic_set_receivers", "lbm_elastic_reset",
+    "lbm_elastic_set_sources", "lbm_elastic_set_receivers", "lbm_elastic_set_sponges",
+    "lbm_elastic_reset",
     "lbm_elastic_step", "lbm_elastic_step_index", "lbm_elastic_read_fields",
     "lbm_elastic_traces_recorded", "lbm_elastic_read_traces", "lbm_elastic_set_state",
     "lbm_elastic_get_state", "lbm_elastic_checkpoint_bytes", "lbm_elastic_save",
@@ -119,6 +120,7 @@ def load_library(build_if_missing: bool = False):
             "lbm_elastic_set_material": (ip, [vp, vp, vp, vp, ip]),
             "lbm_elastic_set_sources": (ip, [vp, ctypes.POINTER(Source), ip]),
             "lbm_elastic_set_receivers": (ip, [vp, vp, ip]),
+            "lbm_elastic_set_sponges": (ip, [vp, ip, ip, ip, ip, ctypes.c_double]),
             "lbm_elastic_reset": (ip, [vp]),
             "lbm_elastic_step": (ip, [vp, ip]),
             "lbm_elastic_step_index": (ctypes.c_longlong, [vp]),
@@ -289,6 +291,12 @@ class ElasticLBM:
         a = np.ascontiguousarray(np.asarray(xy, np.int32).reshape(-1, 2))
         self.nrec = len(a)
         return self._check(self.L.lbm_elastic_set_receivers(self.h, a.ctypes.data if len(a) else None, len(a)))
+
+    def set_sponges(self, sponge, amax: float = 0.0):
+        """Replaces the absorbing layers (top, bottom, left, right thickness in
+        cells) of the running simulation; the state is kept."""
+        t, b, l, r = (int(v) for v in sponge)
+        return self._check(self.L.lbm_elastic_set_sponges(self.h, t, b, l, r, float(amax)))
 
     def reset(self):
         return self._check(self.L.lbm_elastic_reset(self.h))

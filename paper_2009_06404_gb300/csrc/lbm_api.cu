@@ -770,6 +770,21 @@ lbm_status lbm_elastic_set_sources(lbm_elastic_t *h, const lbm_source *src, int 
   return LBM_OK;
 }
 
+lbm_status lbm_elastic_set_sponges(lbm_elastic_t *h, int top, int bottom, int left, int right,
+                                   double amax) {
+  if (!h) return LBM_ERR_ARG;
+  lbm_elastic_config c = h->cfg;
+  c.sponge_top = top;
+  c.sponge_bottom = bottom;
+  c.sponge_left = left;
+  c.sponge_right = right;
+  c.sponge_amax = amax;
+  std::string why;
+  if (!config_ok(&c, &why)) return fail(h, LBM_ERR_ARG, why);
+  h->cfg = c;
+  return LBM_OK;
+}
+
 lbm_status lbm_elastic_set_receivers(lbm_elastic_t *h, const int *xy, int n) {
   if (!h) return LBM_ERR_ARG;
   if (n < 0 || (n > 0 && !xy)) return fail(h, LBM_ERR_ARG, "invalid receiver list");

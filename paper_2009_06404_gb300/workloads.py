@@ -226,3 +226,26 @@ def fwi_blob(nx: int = 1024, ny: int = 512, nsteps: int = 3000, seed: int = 4,
     pert = base.with_(lam=lam * (1 + dlam * g), mu=mu * (1 + dmu * g),
                       name=f"fwi_blob_{nx}x{ny}")
     return base, pert
+
+
+#: step after which the surface-wave experiment removes its lateral layers
+RAYLEIGH_SWITCH_STEP = 400
+
+
+def rayleigh_laps(nx: int = 300, ny: int = 100, nsteps: int = 2200, tau: float = 0.55,
+                  sponge: int = 30, fs_order: int = 0, storage: str = "f64") -> Workload:
+    """The paper's surface-wave experiment (Sec. 7): a Poisson solid on an
+    nx-long, ny-deep grid with a free top, absorbing layers of `sponge` cells
+    on the left, right and bottom (periodic lateral edges behind the lateral
+    layers, rigid bottom), a vertical source (sigma = 4, period 20) near the
+    upper left corner and a receiver on every surface cell.  After
+    RAYLEIGH_SWITCH_STEP steps the lateral layers are to be removed
+    (ElasticLBM.set_sponges), leaving the surface wave free to go round."""
+    rho0, lam, mu = homogeneous(ny, 0.25)
+    src = source(sponge + 15.0, 4.0, sigma=4.0, direction=(0.0, 1.0), f_peak=1.0 / 20.0,
+                 t0=30.0, r_cut=32.0)
+    rec = np.array([[x, 0] for x in range(nx)], np.int32)
+    return Workload(name=f"rayleigh_laps_{nx}x{ny}", nx=nx, ny=ny, nsteps=nsteps, tau=tau,
+                    storage=storage, bc=("free", "rigid", "periodic", "periodic"),
+                    sponge=(0, sponge, sponge, sponge), fs_order=fs_order, rho0=rho0, lam=lam,
+                    mu=mu, sources=src[None], receivers=rec)

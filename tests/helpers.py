@@ -28,3 +28,22 @@ def max_rel(a, b):
     b = np.asarray(b, np.float64)
     s = np.max(np.abs(b))
     return float(np.max(np.abs(a - b)) / (s if s > 0 else 1.0))
+
+
+def two_lap_speed(uy, nx, t_from, window=300, guess=0.5308, span=0.05):
+    """Speed of a wave going round an nx-periodic surface from the surface
+    displacement uy [T][nx]: the time lag L (within span of 2 nx / guess)
+    that best aligns the window [t_from, t_from + window) of every receiver
+    with the same receiver two laps later, refined by a parabola through the
+    correlation peak; returns 2 nx / L (the paper's two-turn measurement)."""
+    uy = np.asarray(uy, np.float64)
+    lag0 = 2.0 * nx / guess
+    lags = np.arange(int(lag0 * (1 - span)), int(lag0 * (1 + span)) + 1)
+    a = uy[t_from:t_from + window]
+    corr = np.array([float(np.sum(a * uy[t_from + L:t_from + L + window])) for L in lags])
+    k = int(np.argmax(corr))
+    if not 0 < k < len(lags) - 1:
+        raise ValueError("correlation peak at the edge of the search range")
+    c0, c1, c2 = corr[k - 1], corr[k], corr[k + 1]
+    L = lags[k] + 0.5 * (c0 - c2) / (c0 - 2 * c1 + c2)
+    return 2.0 * nx / L
