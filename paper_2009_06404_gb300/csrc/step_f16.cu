@@ -3,7 +3,7 @@
 #include "lbm_kernels.cuh"
 
 #ifndef LBM_PAIR_16
-#define LBM_PAIR_16 1
+#define LBM_PAIR_16 0
 #endif
 
 namespace lbm {
