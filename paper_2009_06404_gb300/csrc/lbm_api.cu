@@ -493,6 +493,11 @@ EncodeTiledFn encode_tiled() {
 }
 
 // Builds the tensor maps of the TMA-staged kernel; false if TMA cannot be used.
+const CUtensorMapL2promotion kTmaPromotion =
+    LBM_TMA_L2_PROMOTION == 0 ? CU_TENSOR_MAP_L2_PROMOTION_NONE
+    : LBM_TMA_L2_PROMOTION == 1 ? CU_TENSOR_MAP_L2_PROMOTION_L2_128B
+                                : CU_TENSOR_MAP_L2_PROMOTION_L2_256B;
+
 bool setup_tma(lbm_elastic_t *h, std::string *why) {
   const lbm_elastic_config &c = h->cfg;
   const Layout &L = h->L;
@@ -533,7 +538,7 @@ bool setup_tma(lbm_elastic_t *h, std::string *why) {
       const cuuint32_t estr[3] = {1, 1, 1};
       CUresult r = enc(&h->maps.f[b][hh - 1], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, h->ws + L.f[b],
                        dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                       CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                       CU_TENSOR_MAP_SWIZZLE_NONE, kTmaPromotion,
                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
       if (r != CUDA_SUCCESS) {
         *why = "cuTensorMapEncodeTiled failed for the populations";
@@ -549,7 +554,7 @@ bool setup_tma(lbm_elastic_t *h, std::string *why) {
     CUresult r = enc(&h->maps.u, us == 8 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64
                                          : CU_TENSOR_MAP_DATA_TYPE_FLOAT32,
                      3, h->ws + L.u, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                     CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                     CU_TENSOR_MAP_SWIZZLE_NONE, kTmaPromotion,
                      CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) {
       *why = "cuTensorMapEncodeTiled failed for the displacement";

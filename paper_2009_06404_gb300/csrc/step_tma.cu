@@ -129,8 +129,12 @@ __device__ __forceinline__ bool tile_has_receiver(const StepParams &p, int x0, i
   return __ballot_sync(0xffffffffu, any) != 0u;
 }
 
+#ifndef LBM_TMA_MIN_BLOCKS
+#define LBM_TMA_MIN_BLOCKS 3
+#endif
+
 template <class T, class U, bool LAM, int TH, int STAGES>
-__global__ void __launch_bounds__(kTmaThreads, 2)
+__global__ void __launch_bounds__(kTmaThreads, LBM_TMA_MIN_BLOCKS)
     step_tma_kernel(const StepParams p, const __grid_constant__ CUtensorMap fmap,
                     const __grid_constant__ CUtensorMap umap, int ntx, int nty) {
   constexpr int H = LAM ? 2 : 1;

@@ -9,10 +9,22 @@
 
 namespace lbm {
 
+#ifndef LBM_TMA_TILE_H
+#define LBM_TMA_TILE_H 4
+#endif
+#ifndef LBM_TMA_STAGES
+#define LBM_TMA_STAGES 2
+#endif
+#ifndef LBM_TMA_L2_PROMOTION
+#define LBM_TMA_L2_PROMOTION 2   // 0 none, 1 128 B, 2 256 B
+#endif
 constexpr int kTileW = 128;        // tile width in cells (one warp covers 32 of them)
-constexpr int kTileH = 4;          // tile height
-constexpr int kTmaThreads = 256;   // 8 warps: two per tile row
-constexpr int kTmaStages = 2;      // tiles in flight per CTA (several CTAs share an SM)
+constexpr int kTileH = LBM_TMA_TILE_H;  // tile height
+#ifndef LBM_TMA_THREADS
+#define LBM_TMA_THREADS 256
+#endif
+constexpr int kTmaThreads = LBM_TMA_THREADS;  // warps per CTA / kTileH per tile row
+constexpr int kTmaStages = LBM_TMA_STAGES;  // tiles in flight per CTA (several CTAs share an SM)
 constexpr long long kWaitCycles = 2000000000LL;  // ~1 s at 2 GHz: bound of every wait
 
 // Tensor maps of one handle: the two population buffers, each with a halo of
