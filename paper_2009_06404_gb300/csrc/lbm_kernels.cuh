@@ -125,18 +125,29 @@ template <> __device__ __forceinline__ void st<__nv_bfloat16, float>(__nv_bfloat
   *p = __float2bfloat16_rn(v);
 }
 
-// Population loads and stores through the storage scale: 16-bit storage keeps
-// f * 2^k (an exact power of two, so scaling adds no rounding); wider types
-// are stored as they are.
+// Population loads and stores.  16-bit storage keeps f * 2^k; the step works
+// on those scaled values throughout (the step is linear and 2^k is exact, so
+// every rounding is the unscaled one times 2^k): only the body force enters
+// times 2^k, and 1/rho0 (for u += j / rho0) and the fields read out carry
+// 2^-k (see force_scale, irho_at).
 template <class T, class C>
-__device__ __forceinline__ C ldp(const T *ptr, const StepParams &p) {
-  if (sizeof(T) == 2) return ld<T, C>(ptr) * C(p.iscale_f);
+__device__ __forceinline__ C ldp(const T *ptr, const StepParams &) {
   return ld<T, C>(ptr);
 }
 template <class T, class C>
-__device__ __forceinline__ void stp(T *ptr, C v, const StepParams &p) {
-  if (sizeof(T) == 2) st<T, C>(ptr, v * C(p.scale_f));
-  else st<T, C>(ptr, v);
+__device__ __forceinline__ void stp(T *ptr, C v, const StepParams &) {
+  st<T, C>(ptr, v);
+}
+
+// 2^k for 16-bit storage (the body force in the populations' units), else 1.
+template <class T, class C>
+__device__ __forceinline__ C force_scale(const StepParams &p) {
+  return sizeof(T) == 2 ? C(p.scale_f) : C(1);
+}
+// 2^-k for 16-bit storage (back to physical units), else 1.
+template <class T, class C>
+__device__ __forceinline__ C unit_scale(const StepParams &p) {
+  return sizeof(T) == 2 ? C(p.iscale_f) : C(1);
 }
 
 // Loads and stores of two horizontally adjacent populations at once (the
@@ -172,22 +183,14 @@ __device__ __forceinline__ __nv_bfloat162 pack2(float a, float b, __nv_bfloat162
 }
 
 template <class T, class C>
-__device__ __forceinline__ void ldp2(const T *ptr, const StepParams &p, C &a, C &b) {
+__device__ __forceinline__ void ldp2(const T *ptr, const StepParams &, C &a, C &b) {
   using P2 = typename Pair2<T>::type;
   unpack2(*reinterpret_cast<const P2 *>(ptr), a, b);
-  if (sizeof(T) == 2) {
-    a *= C(p.iscale_f);
-    b *= C(p.iscale_f);
-  }
 }
 
 template <class T, class C>
-__device__ __forceinline__ void stp2(T *ptr, C a, C b, const StepParams &p) {
+__device__ __forceinline__ void stp2(T *ptr, C a, C b, const StepParams &) {
   using P2 = typename Pair2<T>::type;
-  if (sizeof(T) == 2) {
-    a *= C(p.scale_f);
-    b *= C(p.scale_f);
-  }
   *reinterpret_cast<P2 *>(ptr) = pack2(a, b, (P2 *)nullptr);
 }
 
@@ -425,6 +428,13 @@ __device__ __forceinline__ C mat_at(const void *tab, int per_cell, int x, int y,
   return per_cell ? t[y * pitch + x] : t[y];
 }
 
+// 1/rho0 at (x, y) times the populations' unit scale (u and v come out in
+// physical units from j in the populations' units).
+template <class T, class C>
+__device__ __forceinline__ C irho_at(const StepParams &p, int x, int y) {
+  return mat_at<C>(p.irho, p.mat_per_cell, x, y, p.pitch) * unit_scale<T, C>(p);
+}
+
 // ------------------------------------------------------------ the step
 
 // Density of the streamed populations at an interior cell whose nine
@@ -547,7 +557,7 @@ __device__ __forceinline__ void finish_cell(const StepParams &p, const C *f, C g
   const C A = sponge_A<C>(p, xc, yc);
   C jx, jy, Sx, Sy;
   flux_and_source<C>(M.mx, M.my, Gx, Gy, Fx, Fy, A, jx, jy, Sx, Sy);
-  const C irho = mat_at<C>(p.irho, p.mat_per_cell, xc, yc, p.pitch);
+  const C irho = irho_at<T, C>(p, xc, yc);
 
   if (MODE == 1) {
     if (!active) return;
@@ -558,10 +568,11 @@ __device__ __forceinline__ void finish_cell(const StepParams &p, const C *f, C g
     if (p.out[1]) p.out[1][o] = (double)u[p.plane + c];
     if (p.out[2]) p.out[2][o] = (double)mul_rn(jx, irho);
     if (p.out[3]) p.out[3][o] = (double)mul_rn(jy, irho);
-    if (p.out[4]) p.out[4][o] = (double)M.rho;
-    if (p.out[5]) p.out[5][o] = (double)M.pxx;
-    if (p.out[6]) p.out[6][o] = (double)M.pxy;
-    if (p.out[7]) p.out[7][o] = (double)M.pyy;
+    const C us = unit_scale<T, C>(p);
+    if (p.out[4]) p.out[4][o] = (double)(M.rho * us);
+    if (p.out[5]) p.out[5][o] = (double)(M.pxx * us);
+    if (p.out[6]) p.out[6][o] = (double)(M.pxy * us);
+    if (p.out[7]) p.out[7][o] = (double)(M.pyy * us);
     return;
   }
 
@@ -652,6 +663,8 @@ __device__ __noinline__ void general_cell(const StepParams &p, int x, int y, int
   const int yc = y < yend ? y : yend - 1;
   C Fx, Fy;
   body_force<C>(p, xc, yc, Fx, Fy);  // all lanes of the warp take part
+  Fx *= force_scale<T, C>(p);
+  Fy *= force_scale<T, C>(p);
   if (!(xc >= 1 && xc < p.nx - 1 && yc >= 1 && yc < p.ny - 1)) {
     boundary_cell<T, C, U, false, MODE>(p, Fx, Fy, x, y, xc, yc, active);
     return;
@@ -719,6 +732,8 @@ __device__ __noinline__ void general_block_lam(const StepParams &p, int x0, int 
   const int yc = y < yend ? y : yend - 1;
   C Fx, Fy;
   body_force<C>(p, xc, yc, Fx, Fy);  // all lanes of the warp take part
+  Fx *= force_scale<T, C>(p);
+  Fy *= force_scale<T, C>(p);
   const T *fin = (const T *)p.fin;
   C f[9];
   gather<T, C>(p, fin, xc, yc, f);
@@ -768,7 +783,7 @@ __device__ __noinline__ void general_block_lam(const StepParams &p, int x0, int 
 #define LBM_STEP_MIN_BLOCKS 6
 #endif
 #ifndef LBM_STEP_MIN_BLOCKS_LAM
-#define LBM_STEP_MIN_BLOCKS_LAM 6
+#define LBM_STEP_MIN_BLOCKS_LAM 8
 #endif
 
 template <class T, class C, class U, bool LAM, int MODE, int R>
@@ -897,7 +912,7 @@ __device__ __forceinline__ void step_block(const StepParams &p, int bx, int by) 
   const int c = y * p.pitch + x;
   U *u = (U *)p.u;
   const U ux0 = u[c], uy0 = u[p.plane + c];
-  const C irho = mat_at<C>(p.irho, p.mat_per_cell, x, y, p.pitch);
+  const C irho = irho_at<T, C>(p, x, y);
   const Moments<C> M = cell_moments<C>(f);
   C Gx = C(0), Gy = C(0);
   if (LAM) {
@@ -1024,13 +1039,7 @@ __device__ __forceinline__ void step_block_pair(const StepParams &p, int bx, int
   using UP = typename UPair<U>::type;
   const UP ux0 = *reinterpret_cast<const UP *>(u + c);
   const UP uy0 = *reinterpret_cast<const UP *>(u + p.plane + c);
-  C irha, irhb;
-  if (p.mat_per_cell) {
-    irha = ((const C *)p.irho)[c];
-    irhb = ((const C *)p.irho)[c + 1];
-  } else {
-    irha = irhb = ((const C *)p.irho)[y];
-  }
+  const C irha = irho_at<T, C>(p, xa, y), irhb = irho_at<T, C>(p, xa + 1, y);
   const Moments<C> Ma = cell_moments<C>(fa), Mb = cell_moments<C>(fb);
   C Gxa = C(0), Gya = C(0), Gxb = C(0), Gyb = C(0);
   if (LAM) {
