@@ -375,9 +375,13 @@ __global__ void __launch_bounds__(256) adj_pull_kernel(const AdjParams a) {
 // shared memory, then the density adjoint of the inner 34 x 10 cells, then
 // the push of its own cells.  Each population adjoint is read once from
 // HBM by its own block (the ring comes from L2) and written once.
-constexpr int kAdjTW = 32, kAdjTH = 8;
+#ifndef LBM_ADJ_TH
+#define LBM_ADJ_TH 8
+#endif
+constexpr int kAdjTW = 32, kAdjTH = LBM_ADJ_TH;
+constexpr int kAdjThreads = 32 * kAdjTH;
 #ifndef LBM_ADJ_MIN_BLOCKS
-#define LBM_ADJ_MIN_BLOCKS 4
+#define LBM_ADJ_MIN_BLOCKS (2048 / (2 * kAdjThreads))
 #endif
 constexpr int kAdjW2 = kAdjTW + 4, kAdjH2 = kAdjTH + 4;
 constexpr int kAdjW1 = kAdjTW + 2, kAdjH1 = kAdjTH + 2;
@@ -425,7 +429,7 @@ __device__ __forceinline__ C gtot_s(const AdjSmem<C> &S, bool lam_any, int hx, i
 }
 
 template <class C>
-__global__ void __launch_bounds__(256, LBM_ADJ_MIN_BLOCKS) adj_fused_kernel(const AdjParams a) {
+__global__ void __launch_bounds__(kAdjThreads, LBM_ADJ_MIN_BLOCKS) adj_fused_kernel(const AdjParams a) {
   const StepParams &p = a.p;
   __shared__ AdjSmem<C> S;
   const int t = threadIdx.y * 32 + threadIdx.x;
@@ -435,7 +439,7 @@ __global__ void __launch_bounds__(256, LBM_ADJ_MIN_BLOCKS) adj_fused_kernel(cons
                        x0 + kAdjTW - 1 >= p.src_x0 && y0 <= p.src_y1 &&
                        y0 + kAdjTH - 1 >= p.src_y0;
   // ---- local transposes of the block and its two-cell ring
-  for (int k = t; k < kAdjW2 * kAdjH2; k += 256) {
+  for (int k = t; k < kAdjW2 * kAdjH2; k += kAdjThreads) {
     const int hx = k % kAdjW2 - 2, hy = k / kAdjW2 - 2;
     int gx = x0 + hx, gy = y0 + hy;
     bool ex = true;
@@ -494,7 +498,7 @@ __global__ void __launch_bounds__(256, LBM_ADJ_MIN_BLOCKS) adj_fused_kernel(cons
   __syncthreads();
   // ---- density adjoint of the block and its one-cell ring
   if (a.lam_any) {
-    for (int k = t; k < kAdjW1 * kAdjH1; k += 256) {
+    for (int k = t; k < kAdjW1 * kAdjH1; k += kAdjThreads) {
       const int hx = k % kAdjW1 - 1, hy = k / kAdjW1 - 1;
       int gx = x0 + hx, gy = y0 + hy;
       bool ex = true;
@@ -608,7 +612,7 @@ template <class C>
 cudaError_t adj_step_t(const AdjParams &a, bool fused, cudaStream_t s) {
   const dim3 block(32, 8), grid((a.p.nx + 31) / 32, (a.p.ny + 7) / 8);
   if (fused) {
-    adj_fused_kernel<C><<<grid, block, 0, s>>>(a);
+    adj_fused_kernel<C><<<dim3(grid.x, (a.p.ny + kAdjTH - 1) / kAdjTH), dim3(32, kAdjTH), 0, s>>>(a);
   } else {
     adj_local_kernel<C><<<grid, block, 0, s>>>(a);
     if (a.lam_any) adj_div_kernel<C><<<grid, block, 0, s>>>(a);
