@@ -35,8 +35,10 @@ if ROOT not in sys.path:
 
 METRIC = "D2Q9 elastic-LBM MLUPS & % HBM roofline: plain vs batched/FP16-store/adjoint"
 UNIT = "MLUPS"
-# Algorithmic bytes per cell update of the FP32 step without per-cell material:
-# 9 populations read + 9 written (4 B each) + displacement read + written (2 x 2 x 4 B).
+# Algorithmic bytes per cell of one step-kernel launch without per-cell
+# material: 9 populations read + 9 written + the displacement read + written
+# (FP32: 9 x 4 x 2 + 2 x 4 x 2).  A one-step launch does this per time step; a
+# two-step launch (intermediate populations in shared memory) per two.
 BYTES_PER_CELL = {"f32": 9 * 4 * 2 + 2 * 4 * 2, "f64": 9 * 8 * 2 + 2 * 8 * 2}
 
 
@@ -207,6 +209,10 @@ def run_gpu(args):
     w = wl.halfspace(nsteps=args.time_steps, storage=storage)
     stream = torch.cuda.current_stream()
     sim = pkg.from_workload(w, max_steps_traced=w.nsteps, stream=stream)
+    spl = args.steps_per_launch
+    sim.set_steps_per_launch(spl)
+    # step-kernel launches per shot (Lambda = 0 here, so two-step launches apply)
+    step_launches = w.nsteps // spl + w.nsteps % spl
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
 
     def shot(ev_pair=None):
@@ -302,16 +308,19 @@ def run_gpu(args):
 
     # --------------------------------------------------- roofline of the step kernel
     peak, peak_kind = _peaks()
-    avg_launch_s = kernel_ms / 1e3 / (args.steps * w.nsteps)
+    # a launch moves every population and the displacement once each way,
+    # whether it advances one time step or two
+    avg_launch_s = kernel_ms / 1e3 / (args.steps * step_launches)
     bytes_launch = BYTES_PER_CELL[storage] * w.cells
     achieved = bytes_launch / avg_launch_s / 1e9
+    kname = "step2_kernel" if spl == 2 else "step_kernel"
     traffic = None
     prof = os.path.join(ROOT, "profiles", "traffic.json")
     if os.path.exists(prof):
         try:
             with open(prof) as f:
                 d = json.load(f)
-            key = f"step_{storage}_{w.nx}x{w.ny}"
+            key = f"{'step2' if spl == 2 else 'step'}_{storage}_{w.nx}x{w.ny}"
             if key in d and d[key].get("kernel_hash") == _build.source_hash(_build.STEP_SOURCES):
                 traffic = d[key]["dram_bytes_per_launch"]
         except Exception:
@@ -350,8 +359,10 @@ def run_gpu(args):
                    "l2": "flushed before every timed shot (256 MiB write)"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic,
-                     "peak_kind": peak_kind, "kernel": "step_kernel",
-                     "bytes_per_cell": BYTES_PER_CELL[storage],
+                     "peak_kind": peak_kind, "kernel": kname,
+                     "steps_per_launch": spl,
+                     "bytes_per_cell_per_launch": BYTES_PER_CELL[storage],
+                     "bytes_per_cell_step": BYTES_PER_CELL[storage] / spl,
                      "avg_launch_us": avg_launch_s * 1e6},
         "cpu_baseline": cpu,
         "e2e": {"value": e2e_value, "unit": UNIT,
@@ -546,6 +557,8 @@ def main():
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--storage", default="f32", choices=["f32", "f64"])
     ap.add_argument("--time-steps", type=int, default=4000)
+    ap.add_argument("--steps-per-launch", type=int, default=2, choices=[1, 2],
+                    help="time steps per step-kernel launch (2: the two-step kernel)")
     ap.add_argument("--cpu-sample-steps", type=int, default=100)
     ap.add_argument("--ref-sample-steps", type=int, default=10)
     ap.add_argument("--no-cpu-baseline", action="store_true")

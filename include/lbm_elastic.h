@@ -167,6 +167,17 @@ lbm_status lbm_elastic_reset(lbm_elastic_t *h);
  * have been recorded since the last reset / set_receivers / set_state. */
 lbm_status lbm_elastic_step(lbm_elastic_t *h, int nsteps);
 
+/* Time steps per kernel launch in lbm_elastic_step: 1, or 2, which advances
+ * two steps per launch with the intermediate populations kept in on-chip
+ * shared memory (each population then crosses HBM once per two steps).
+ * Default: 2 for FP32 and 16-bit storage, 1 for FP64 (whose step is bound by
+ * the FP64 arithmetic rather than by memory).  Two-step launches apply where
+ * every Lambda is zero and the TMA-staged kernel is off; elsewhere, and for
+ * an odd remainder, steps go one per launch.  Both settings give
+ * bit-identical states and traces.  Returns LBM_ERR_ARG for any other
+ * value. */
+lbm_status lbm_elastic_set_steps_per_launch(lbm_elastic_t *h, int steps);
+
 /* Index n of the next step (number of steps taken since reset or the step
  * given to set_state). */
 long long lbm_elastic_step_index(const lbm_elastic_t *h);

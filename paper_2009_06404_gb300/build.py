@@ -43,7 +43,7 @@ def _deps():
 
 #: the sources the single-grid step kernel is built from (its launch geometry
 #: is set in lbm_api.cu)
-STEP_SOURCES = ("lbm_kernels.cuh", "step_f32.cu", "lbm_api.cu")
+STEP_SOURCES = ("lbm_kernels.cuh", "step_fused.cuh", "step_f32.cu", "lbm_api.cu")
 
 
 def source_hash(names=None) -> str:

@@ -12,6 +12,7 @@
 #include <vector>
 
 #include "lbm_internal.h"
+#include "step_fused.cuh"
 
 using namespace lbm;
 
@@ -349,6 +350,7 @@ StepParams base_params(lbm_elastic_t *h) {
   p.nsrc = h->nsrc;
   p.n = h->step;
   p.trace_slot = -1;
+  p.trace_slot2 = -1;
   p.rec_tile_ptr = at<int>(h, L.rec_ptr);
   p.rec_xy = at<int>(h, L.rec_xy);
   p.rec_id = at<int>(h, L.rec_id);
@@ -600,6 +602,29 @@ lbm_status lbm::handle_step(lbm_elastic_t *h, void *grad_out) {
   return LBM_OK;
 }
 
+// Steps n and n + 1 of the handle in one launch of the two-step kernel.
+static lbm_status handle_step2(lbm_elastic_t *h) {
+  StepParams p = base_params(h);
+  // consecutive launches visit the tiles in opposite orders
+  p.reverse = (int)((h->step >> 1) & 1);
+  const int tmax = h->cfg.max_steps_traced;
+  if (h->nrec > 0 && h->traced < tmax) {
+    p.trace_slot = h->traced;
+    if (h->traced + 1 < tmax) p.trace_slot2 = h->traced + 1;
+  }
+  if (h->cfg.storage == LBM_F64)
+    launch_step2_f64(p, h->stream);
+  else if (h->cfg.storage == LBM_F32)
+    launch_step2_f32(p, h->cfg.u_fp64 != 0, h->stream);
+  else
+    launch_step2_16(p, h->cfg.storage == LBM_BF16, h->cfg.u_fp64 != 0, h->stream);
+  if (lbm_status st = check_launch(h, "two-step kernel launch")) return st;
+  h->traced += (p.trace_slot >= 0) + (p.trace_slot2 >= 0);
+  h->cur ^= 1;
+  h->step += 2;
+  return LBM_OK;
+}
+
 extern "C" {
 
 size_t lbm_elastic_workspace_bytes(const lbm_elastic_config *cfg) {
@@ -623,6 +648,8 @@ lbm_status lbm_elastic_create(const lbm_elastic_config *cfg, void *d_workspace,
   lbm_elastic_t *h = new (std::nothrow) lbm_elastic();
   if (!h) return fail(nullptr, LBM_ERR_ARG, "out of host memory");
   h->cfg = *cfg;
+  // FP64 steps are bound by the FP64 pipe, not by memory: one per launch
+  h->steps_per_launch = cfg->storage == LBM_F64 ? 1 : 2;
   h->L = L;
   h->ws = (char *)d_workspace;
   h->stream = (cudaStream_t)cuda_stream;
@@ -741,6 +768,10 @@ lbm_status lbm_elastic_set_sources(lbm_elastic_t *h, const lbm_source *src, int 
     q.diry = s.dir_y;
     q.pif2 = M_PI * M_PI * s.f_peak * s.f_peak;
     q.t0 = s.t0;
+    q.inv2s2_f = (float)q.inv2s2;
+    q.pif2_f = (float)q.pif2;
+    q.ax_f = (float)q.ax;
+    q.ay_f = (float)q.ay;
   }
   // bounding box of every footprint (the whole axis when it wraps around)
   int bx0 = h->cfg.nx, bx1 = -1, by0 = h->cfg.ny, by1 = -1;
@@ -845,8 +876,20 @@ lbm_status lbm_elastic_reset(lbm_elastic_t *h) {
 lbm_status lbm_elastic_step(lbm_elastic_t *h, int nsteps) {
   if (!h) return LBM_ERR_ARG;
   if (nsteps < 0) return fail(h, LBM_ERR_ARG, "nsteps < 0");
-  for (int s = 0; s < nsteps; ++s)
+  const bool two = h->steps_per_launch == 2 && !h->lambda_nonzero && !h->use_tma;
+  int s = 0;
+  if (two)
+    for (; s + 2 <= nsteps; s += 2)
+      if (lbm_status st = handle_step2(h)) return st;
+  for (; s < nsteps; ++s)
     if (lbm_status st = handle_step(h, nullptr)) return st;
+  return LBM_OK;
+}
+
+lbm_status lbm_elastic_set_steps_per_launch(lbm_elastic_t *h, int steps) {
+  if (!h) return LBM_ERR_ARG;
+  if (steps != 1 && steps != 2) return fail(h, LBM_ERR_ARG, "steps per launch must be 1 or 2");
+  h->steps_per_launch = steps;
   return LBM_OK;
 }
 

@@ -40,6 +40,7 @@ struct lbm_elastic {
   int traced = 0;
   int nsrc = 0, nrec = 0;
   bool lambda_nonzero = false;
+  int steps_per_launch = 2;    // lbm_elastic_step: 1, or 2 (two-step kernel where it applies)
   long long launches = 0;
   std::vector<lbm::SourceDev> src_host;
   int src_box[4] = {0, -1, 0, -1};  // x0, x1, y0, y1 of all source footprints

@@ -45,6 +45,8 @@ struct SourceDev {
   int rb;           // integer bound: ceil(r_cut) + 1 cells around (xc, yc)
   int pad;
   double dirx, diry;  // direction (the force per unit amplitude)
+  // single-precision copies for the FP32-arithmetic kernels
+  float inv2s2_f, pif2_f, ax_f, ay_f;
 };
 
 struct StepParams {
@@ -71,6 +73,7 @@ struct StepParams {
   int nsrc;
   long long n;       // index of this step (force time t = n)
   int trace_slot;    // >= 0: record receivers into this slot
+  int trace_slot2;   // two-step launches: the slot of step n + 1 (or -1)
   const int *rec_tile_ptr;  // [tiles + 1] CSR over receiver tiles
   const int *rec_xy;        // [nrec][2]  sorted by tile
   const int *rec_id;        // [nrec]     original receiver index
@@ -194,18 +197,39 @@ __device__ __forceinline__ void stp2(T *ptr, C a, C b, const StepParams &) {
   *reinterpret_cast<P2 *>(ptr) = pack2(a, b, (P2 *)nullptr);
 }
 
+// Product rounded on its own (never fused with a following addition), and a
+// fused multiply-add, so that every path of the step rounds these
+// expressions the same way whatever the compiler would contract.
+__device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ float fma_rn(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double fma_rn(double a, double b, double c) { return __fma_rn(a, b, c); }
+
 // ------------------------------------------------------------ wall rules
+
+// Where the wall rules read post-collision populations: a whole grid in
+// global memory (periodic axes wrapped), or a window of cells around a block
+// held in shared memory, which stores the periodic images of cells beyond a
+// seam at their unwrapped coordinates (no wrap).
+template <class T>
+struct GridPops {
+  const T *f;
+  int fplane, frow;
+  static constexpr bool kWrap = true;
+  __device__ __forceinline__ const T *at(int i, int x, int y) const {
+    return f + (i * fplane + (y * frow + x));
+  }
+};
 
 // Moments rho and the diagonal stress components of the post-collision
 // populations at one in-domain cell (the collision conserves rho and P, so
 // these equal the moments at time t of Eqs. 39-42).
-template <class T, class C>
-__device__ void cell_rho_pdiag(const StepParams &p, const T *f, int x, int y, C &rho,
-                               C &pxx, C &pyy) {
-  const int c = y * p.frow + x;
+template <class T, class C, class A>
+__device__ void cell_rho_pdiag(const StepParams &p, const A &a, int x, int y, C &rho, C &pxx,
+                               C &pyy) {
   C v[9];
 #pragma unroll
-  for (int i = 0; i < 9; ++i) v[i] = ldp<T, C>(f + i * p.fplane + c, p);
+  for (int i = 0; i < 9; ++i) v[i] = ldp<T, C>(a.at(i, x, y), p);
   rho = v[0] + v[1] + v[2] + v[3] + v[4] + v[5] + v[6] + v[7] + v[8];
   pxx = v[1] + v[3] + v[5] + v[6] + v[7] + v[8];
   pyy = v[2] + v[4] + v[5] + v[6] + v[7] + v[8];
@@ -216,55 +240,68 @@ __device__ void cell_rho_pdiag(const StepParams &p, const T *f, int x, int y, C 
 // surface: anti-bounce-back with rho_air and the tangential stress
 // extrapolated linearly from x_b and x_in = x_b - n; P_air has no other
 // component (Eqs. 37-42).
-template <class T, class C>
-__device__ C wall_value(const StepParams &p, const T *f, int bc, int nxo, int nyo, int i,
-                        int x, int y) {
+template <class T, class C, class A>
+__device__ C wall_value(const StepParams &p, const A &a, int bc, int nxo, int nyo, int i, int x,
+                        int y) {
   const int k = oppd(i);
-  const C fk = ldp<T, C>(f + k * p.fplane + y * p.frow + x, p);
+  const C fk = ldp<T, C>(a.at(k, x, y), p);
   if (bc == BC_RIGID) return fk;
   C rb, pxxb, pyyb, ri, pxxi, pyyi;
-  cell_rho_pdiag<T, C>(p, f, x, y, rb, pxxb, pyyb);
+  cell_rho_pdiag<T, C>(p, a, x, y, rb, pxxb, pyyb);
+  // The products and sums are rounded in a fixed order (explicit fused
+  // multiply-adds), so the value does not depend on how the compiler
+  // contracts the expression where the link i is a constant (an unrolled
+  // caller) or a run-time value.
   C rho_air, ptan;  // tangential stress: P_xx on a horizontal wall, P_yy on a vertical one
   if (p.fs_order == 1) {
-    // linear extrapolation half a cell out (Eq. 39)
-    cell_rho_pdiag<T, C>(p, f, x - nxo, y - nyo, ri, pxxi, pyyi);
-    rho_air = C(1.5) * rb - C(0.5) * ri;
-    ptan = nyo != 0 ? C(1.5) * pxxb - C(0.5) * pxxi : C(1.5) * pyyb - C(0.5) * pyyi;
+    // linear extrapolation half a cell out (Eq. 39); 0.5 x is exact
+    cell_rho_pdiag<T, C>(p, a, x - nxo, y - nyo, ri, pxxi, pyyi);
+    rho_air = fma_rn(C(1.5), rb, C(-0.5) * ri);
+    ptan = nyo != 0 ? fma_rn(C(1.5), pxxb, C(-0.5) * pxxi)
+                    : fma_rn(C(1.5), pyyb, C(-0.5) * pyyi);
   } else {
     // constant extrapolation: the boundary cell's own values
     rho_air = rb;
     ptan = nyo != 0 ? pxxb : pyyb;
   }
-  const C pnxx = (nyo != 0 ? ptan : C(0)) - rho_air * C(1.0 / 3.0);
-  const C pnyy = (nyo != 0 ? C(0) : ptan) - rho_air * C(1.0 / 3.0);
+  const C third = C(1.0 / 3.0);
+  const C pnxx = fma_rn(-rho_air, third, nyo != 0 ? ptan : C(0));
+  const C pnyy = fma_rn(-rho_air, third, nyo != 0 ? C(0) : ptan);
   const int cx = cxd(k), cy = cyd(k);
-  const C h = (C(cx * cx) - C(1.0 / 3.0)) * pnxx + (C(cy * cy) - C(1.0 / 3.0)) * pnyy;
-  return -fk + C(2) * wd<C>(k) * (rho_air + C(4.5) * h);
+  const C h = fma_rn(C(cx * cx) - third, pnxx, mul_rn(C(cy * cy) - third, pnyy));
+  return fma_rn(C(2) * wd<C>(k), fma_rn(C(4.5), h, rho_air), -fk);
 }
 
-// Pull of population i into (x, y) on a boundary cell (general path).
-template <class T, class C>
-__device__ __noinline__ C pull_general(const StepParams &p, const T *f, int i, int x, int y) {
+// Pull of population i into (x, y) on a boundary cell (general path): the
+// upstream cell, or the wall rule where the link crosses a non-periodic
+// edge (top and bottom first: a corner link crosses two edges).
+template <class T, class C, class A>
+__device__ __forceinline__ C pull_general_a(const StepParams &p, const A &a, int i, int x, int y) {
   int sx = x - cxd(i), sy = y - cyd(i);
   if (sy < 0 || sy >= p.ny) {
     if (p.bc_top == BC_PERIODIC) {
-      sy = sy < 0 ? sy + p.ny : sy - p.ny;
+      if (A::kWrap) sy = sy < 0 ? sy + p.ny : sy - p.ny;
     } else if (sy < 0) {
-      return wall_value<T, C>(p, f, p.bc_top, 0, -1, i, x, y);
+      return wall_value<T, C>(p, a, p.bc_top, 0, -1, i, x, y);
     } else {
-      return wall_value<T, C>(p, f, p.bc_bottom, 0, 1, i, x, y);
+      return wall_value<T, C>(p, a, p.bc_bottom, 0, 1, i, x, y);
     }
   }
   if (sx < 0 || sx >= p.nx) {
     if (p.bc_left == BC_PERIODIC) {
-      sx = sx < 0 ? sx + p.nx : sx - p.nx;
+      if (A::kWrap) sx = sx < 0 ? sx + p.nx : sx - p.nx;
     } else if (sx < 0) {
-      return wall_value<T, C>(p, f, p.bc_left, -1, 0, i, x, y);
+      return wall_value<T, C>(p, a, p.bc_left, -1, 0, i, x, y);
     } else {
-      return wall_value<T, C>(p, f, p.bc_right, 1, 0, i, x, y);
+      return wall_value<T, C>(p, a, p.bc_right, 1, 0, i, x, y);
     }
   }
-  return ldp<T, C>(f + i * p.fplane + sy * p.frow + sx, p);
+  return ldp<T, C>(a.at(i, sx, sy), p);
+}
+
+template <class T, class C>
+__device__ __noinline__ C pull_general(const StepParams &p, const T *f, int i, int x, int y) {
+  return pull_general_a<T, C>(p, GridPops<T>{f, p.fplane, p.frow}, i, x, y);
 }
 
 // All nine streamed populations of (x, y).
@@ -329,10 +366,6 @@ __device__ void grad_rho(const StepParams &p, const T *f, int x, int y, C rho, C
   gy = C(0.5) * (ryp - rym);
 }
 
-// Product rounded on its own (never fused with a following addition), so
-// that every path of the step rounds u += j / rho0 the same way.
-__device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
-__device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
 
 // Scalar parameter in the compute type (FP32 kernels read the FP32 copy, so
 // no FP64 conversion runs per cell).
@@ -360,29 +393,52 @@ __device__ __forceinline__ C sponge_A(const StepParams &p, int x, int y) {
 // Body force of step n at (x, y) (Sec. 5): sum over sources of
 // amplitude * dir * exp(-r^2/(2 sigma^2)) * ricker(n), r <= r_cut, with
 // minimum-image distances on periodic axes.  Sources are culled per warp
-// (one lane per source tests the warp's row segment), and the few cells near
-// a source evaluate the Gaussian and the wavelet in FP64.
-// Force of one source at (x, y) for step n, in FP64 (only called for the
-// few cells of warps near a source; out of line so that the compiler cannot
-// hoist its FP64 conversions into the path every cell takes).
-// Gaussian x Ricker factor of one source at (x, y) for step n (zero beyond
-// r_cut).
+// (one lane per source tests the warp's row segment), and only the few
+// cells near a source evaluate it.
+
+// Squared minimum-image distance from (x, y) to the source position, in
+// FP64 (the r <= r_cut test is exact, as in the definition).  The periodic
+// image shift floor(d / n + 0.5) is zero whenever |d| < 0.49 n, so the
+// division is only carried out near half a period.
+__device__ __forceinline__ double source_r2(const SourceDev &q, int x, int y, int nx, int ny,
+                                            int wrap_x, int wrap_y) {
+  double dx = (double)x - q.x, dy = (double)y - q.y;
+  if (wrap_x && !(fabs(dx) < 0.49 * nx)) dx -= nx * floor(dx / nx + 0.5);
+  if (wrap_y && !(fabs(dy) < 0.49 * ny)) dy -= ny * floor(dy / ny + 0.5);
+  return dx * dx + dy * dy;
+}
+
+// Gaussian x Ricker factor of one source at (x, y) for step n, in FP64
+// (zero beyond r_cut).
 __device__ __forceinline__ double source_shape(const SourceDev &q, int x, int y, long long n,
                                                int nx, int ny, int wrap_x, int wrap_y) {
-  double dx = (double)x - q.x, dy = (double)y - q.y;
-  if (wrap_x) dx -= nx * floor(dx / nx + 0.5);
-  if (wrap_y) dy -= ny * floor(dy / ny + 0.5);
-  const double r2 = dx * dx + dy * dy;
+  const double r2 = source_r2(q, x, y, nx, ny, wrap_x, wrap_y);
   if (!(r2 <= q.rcut2)) return 0.0;
   const double tt = (double)n - q.t0;
   const double a = q.pif2 * tt * tt;
   return exp(-r2 * q.inv2s2) * (1.0 - 2.0 * a) * exp(-a);
 }
 
-static __device__ __noinline__ double2 source_term(const SourceDev &q, int x, int y, long long n, int nx,
-                                            int ny, int wrap_x, int wrap_y) {
+// Force of one source at (x, y) for step n in the kernel's arithmetic: FP64
+// for the FP64 kernel; for the FP32-arithmetic kernels the distance test in
+// FP64 and the two exponentials in FP32 (the FP64 pipe of this GPU is a
+// small fraction of the FP32 one, and a warp near a source would otherwise
+// spend most of the step there).  Out of line, so the path every cell takes
+// carries none of it.
+static __device__ __noinline__ double2 source_term(const SourceDev &q, int x, int y, long long n,
+                                                   int nx, int ny, int wrap_x, int wrap_y,
+                                                   double) {
   const double g = source_shape(q, x, y, n, nx, ny, wrap_x, wrap_y);
   return make_double2(q.ax * g, q.ay * g);
+}
+static __device__ __noinline__ float2 source_term(const SourceDev &q, int x, int y, long long n,
+                                                  int nx, int ny, int wrap_x, int wrap_y, float) {
+  const double r2 = source_r2(q, x, y, nx, ny, wrap_x, wrap_y);
+  if (!(r2 <= q.rcut2)) return make_float2(0.0f, 0.0f);
+  const float tt = (float)((double)n - q.t0);
+  const float a = q.pif2_f * tt * tt;
+  const float g = expf(-(float)r2 * q.inv2s2_f) * (1.0f - 2.0f * a) * expf(-a);
+  return make_float2(q.ax_f * g, q.ay_f * g);
 }
 
 template <class C>
@@ -414,8 +470,36 @@ __device__ void body_force(const StepParams &p, int x, int y, C &Fx, C &Fy) {
     while (mask) {
       const int b = __ffs(mask) - 1;
       mask &= mask - 1;
-      const double2 F = source_term(p.src[s0 + b], x, y, p.n, p.nx, p.ny,
-                                    p.bc_left == BC_PERIODIC, p.bc_top == BC_PERIODIC);
+      const auto F = source_term(p.src[s0 + b], x, y, p.n, p.nx, p.ny,
+                                 p.bc_left == BC_PERIODIC, p.bc_top == BC_PERIODIC, C(0));
+      Fx += C(F.x);
+      Fy += C(F.y);
+    }
+  }
+}
+
+// The body force of step n at (x, y) computed by one thread alone (no warp
+// cooperation): the sources whose integer bound contains the cell, in
+// ascending order.  Every source that body_force adds and this one skips
+// contributes an exact zero, so the two agree bit for bit.
+template <class C>
+__device__ void body_force_cell(const StepParams &p, int x, int y, long long n, C &Fx, C &Fy) {
+  Fx = C(0);
+  Fy = C(0);
+  for (int s = 0; s < p.nsrc; ++s) {
+    const SourceDev &q = p.src[s];
+    int dy = y - q.yc, dx = x - q.xc;
+    if (p.bc_top == BC_PERIODIC) {
+      if (dy > p.ny / 2) dy -= p.ny;
+      else if (dy < -(p.ny / 2)) dy += p.ny;
+    }
+    if (p.bc_left == BC_PERIODIC) {
+      if (dx > p.nx / 2) dx -= p.nx;
+      else if (dx < -(p.nx / 2)) dx += p.nx;
+    }
+    if (abs(dy) <= q.rb && abs(dx) <= q.rb) {
+      const auto F = source_term(q, x, y, n, p.nx, p.ny, p.bc_left == BC_PERIODIC,
+                                 p.bc_top == BC_PERIODIC, C(0));
       Fx += C(F.x);
       Fy += C(F.y);
     }
@@ -502,11 +586,13 @@ __device__ __forceinline__ void flux_and_source(C mx, C my, C Gx, C Gy, C Fx, C 
 template <class C>
 __device__ __forceinline__ void collide_cell(const Moments<C> &M, C jx, C jy, C Sx, C Sy, C om,
                                              C fc, C *fs) {
+  // (explicit fused multiply-adds: a sum of two products can be contracted
+  // either way, and the compiler's choice may depend on the caller)
   const C k1 = C(1) - om, b2 = C(1.0 / 3.0);
   const C mxs = M.mx + Sx, mys = M.my + Sy;
-  const C qxxy = k1 * M.qxxy + b2 * (om * jy + fc * Sy);
-  const C qxyy = k1 * M.qxyy + b2 * (om * jx + fc * Sx);
-  const C r = k1 * M.r + om * (b2 * (M.pxx + M.pyy) - C(1.0 / 9.0) * M.rho);
+  const C qxxy = fma_rn(k1, M.qxxy, b2 * fma_rn(om, jy, fc * Sy));
+  const C qxyy = fma_rn(k1, M.qxyy, b2 * fma_rn(om, jx, fc * Sx));
+  const C r = fma_rn(k1, M.r, om * fma_rn(b2, M.pxx + M.pyy, C(-1.0 / 9.0) * M.rho));
   const C rp = r + M.pxy, rm = r - M.pxy, qp = qxxy + qxyy, qm = qxxy - qxyy;
   fs[5] = C(0.25) * (rp + qp);   // ( 1,  1)
   fs[7] = C(0.25) * (rp - qp);   // (-1, -1)
@@ -520,15 +606,16 @@ __device__ __forceinline__ void collide_cell(const Moments<C> &M, C jx, C jy, C 
   fs[0] = (M.rho - (M.pxx + M.pyy)) + r;
 }
 
-// Writes (u^{n+1}, v^n) into the trace slot of the receiver at (x, y), if any.
+// Writes (u^{n+1}, v^n) into trace slot `slot` of the receiver at (x, y),
+// if any.
 template <class U>
-__device__ __forceinline__ void record_receiver(const StepParams &p, int x, int y, U ux, U uy,
-                                                U vx, U vy) {
+__device__ __forceinline__ void record_receiver(const StepParams &p, int slot, int x, int y,
+                                                U ux, U uy, U vx, U vy) {
   const int tile = (y / kRecTileY) * p.rec_tiles_x + x / kRecTileX;
   const int r0 = p.rec_tile_ptr[tile], r1 = p.rec_tile_ptr[tile + 1];
   for (int r = r0; r < r1; ++r) {
     if (p.rec_xy[2 * r] == x && p.rec_xy[2 * r + 1] == y) {
-      double *t = p.traces + ((long long)p.trace_slot * p.nrec + p.rec_id[r]) * 4;
+      double *t = p.traces + ((long long)slot * p.nrec + p.rec_id[r]) * 4;
       t[0] = (double)ux;
       t[1] = (double)uy;
       t[2] = (double)vx;
@@ -590,7 +677,7 @@ __device__ __forceinline__ void finish_cell(const StepParams &p, const C *f, C g
   u[p.plane + c] = uy;
   // non-finite guard: x * 0 == 0 fails exactly for NaN and +-Inf
   if (!((M.rho + jx + jy) * C(0) == C(0))) atomicOr(p.err, 1);
-  if (p.trace_slot >= 0) record_receiver<U>(p, x, y, ux, uy, vx, vy);
+  if (p.trace_slot >= 0) record_receiver<U>(p, p.trace_slot, x, y, ux, uy, vx, vy);
 }
 
 // Cells near a wall or a periodic seam: every pull goes through the general
@@ -612,16 +699,17 @@ __device__ __noinline__ void boundary_cell(const StepParams &p, C Fx, C Fy, int 
 }
 
 // Whether the block's cells [x0, x0 + W) x [y0, y0 + h) need anything
-// beyond the bulk update: a wall or periodic seam within m cells, a source,
-// or (when recording) a receiver.  Warp-wide
-// (all 32 lanes call it); every lane gets the same answer.
+// beyond the bulk update: a wall or periodic seam within m cells, a source
+// reaching the block widened by `halo` cells on every side, or (when
+// recording) a receiver in the block.  Warp-wide (all 32 lanes call it);
+// every lane gets the same answer.
 template <int W = 32>
 __device__ __forceinline__ bool block_is_special(const StepParams &p, int x0, int y0, int h,
-                                                 int m) {
+                                                 int m, int halo = 0) {
   static_assert(W == 32 || W == kRecTileX, "a block spans one receiver tile column");
   if (x0 < m || x0 + W > p.nx - m || y0 < m || y0 + h > p.ny - m) return true;
-  const bool near_src = p.nsrc > 0 && x0 <= p.src_x1 && x0 + W - 1 >= p.src_x0 &&
-                        y0 <= p.src_y1 && y0 + h - 1 >= p.src_y0;
+  const bool near_src = p.nsrc > 0 && x0 - halo <= p.src_x1 && x0 + W - 1 + halo >= p.src_x0 &&
+                        y0 - halo <= p.src_y1 && y0 + h - 1 + halo >= p.src_y0;
   const bool near_rec = p.trace_slot >= 0 && x0 <= p.rec_x1 && x0 + W - 1 >= p.rec_x0 &&
                         y0 <= p.rec_y1 && y0 + h - 1 >= p.rec_y0;
   if (!near_src && !near_rec) return false;
@@ -639,7 +727,7 @@ __device__ __forceinline__ bool block_is_special(const StepParams &p, int x0, in
       if (dy > p.ny / 2) dy -= p.ny;
       else if (dy < -(p.ny / 2)) dy += p.ny;
     }
-    hit = abs(dx) <= q.rb + W / 2 + 1 && abs(dy) <= q.rb + h / 2 + 1;
+    hit = abs(dx) <= q.rb + W / 2 + 1 + halo && abs(dy) <= q.rb + h / 2 + 1 + halo;
   }
   if (near_rec && lane >= 30) {
     // receiver tiles are 64 x 4; this block spans one tile column, and rows

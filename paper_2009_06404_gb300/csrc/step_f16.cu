@@ -1,6 +1,7 @@
 // 16-bit population storage (FP16 or BF16) with FP32 arithmetic; the
 // displacement is accumulated in FP32 or FP64.
 #include "lbm_kernels.cuh"
+#include "step_fused.cuh"
 
 #ifndef LBM_PAIR_16
 #define LBM_PAIR_16 0
@@ -34,6 +35,21 @@ void launch_step_16(const StepParams &p, bool bf16, bool lam, bool u64, int mode
   } else {
     if (u64) launch_tu<__half, double>(p, lam, mode, grid, block, s);
     else launch_tu<__half, float>(p, lam, mode, grid, block, s);
+  }
+}
+
+template <class T, class U>
+static void launch2(const StepParams &p, cudaStream_t s) {
+  launch_pdl(step2_kernel<T, float, U>, step2_grid(p.nx, p.ny), step2_block(), s, p);
+}
+
+void launch_step2_16(const StepParams &p, bool bf16, bool u64, cudaStream_t s) {
+  if (bf16) {
+    if (u64) launch2<__nv_bfloat16, double>(p, s);
+    else launch2<__nv_bfloat16, float>(p, s);
+  } else {
+    if (u64) launch2<__half, double>(p, s);
+    else launch2<__half, float>(p, s);
   }
 }
 

@@ -1,6 +1,7 @@
 // FP32 storage and arithmetic instantiations of the step kernel, with the
 // displacement accumulated in FP32 or FP64.
 #include "lbm_kernels.cuh"
+#include "step_fused.cuh"
 
 #ifndef LBM_PAIR_32
 #define LBM_PAIR_32 0
@@ -29,6 +30,12 @@ void launch_step_f32(const StepParams &p, bool lam, bool u64, int mode, dim3 gri
                      cudaStream_t s) {
   if (u64) launch_u<double>(p, lam, mode, grid, block, s);
   else launch_u<float>(p, lam, mode, grid, block, s);
+}
+
+void launch_step2_f32(const StepParams &p, bool u64, cudaStream_t s) {
+  const dim3 grid = step2_grid(p.nx, p.ny), block = step2_block();
+  if (u64) launch_pdl(step2_kernel<float, float, double>, grid, block, s, p);
+  else launch_pdl(step2_kernel<float, float, float>, grid, block, s, p);
 }
 
 }  // namespace lbm

@@ -1,5 +1,6 @@
 // FP64 storage and arithmetic instantiations of the step kernel.
 #include "lbm_kernels.cuh"
+#include "step_fused.cuh"
 
 namespace lbm {
 
@@ -12,6 +13,10 @@ void launch_step_f64(const StepParams &p, bool lam, int mode, dim3 grid, dim3 bl
     if (lam) step_kernel<double, double, double, true, 1><<<grid, block, 0, s>>>(p);
     else step_kernel<double, double, double, false, 1><<<grid, block, 0, s>>>(p);
   }
+}
+
+void launch_step2_f64(const StepParams &p, cudaStream_t s) {
+  launch_pdl(step2_kernel<double, double, double>, step2_grid(p.nx, p.ny), step2_block(), s, p);
 }
 
 }  // namespace lbm

@@ -1,0 +1,308 @@
+// Two steps of the elastic-solid D2Q9 LBM per launch (temporal blocking of
+// the step of lbm_kernels.cuh, for grids without the density-gradient force).
+//
+// A block owns an output tile of kF2Cols x kF2Rows cells.  Step n is
+// computed on the tile's window, the tile widened by one cell on every side
+// (kF2W x kF2H cells), from the populations of step n - 1 in global memory;
+// its post-collision populations go to shared memory, not to HBM.  Step n + 1 of
+// the tile's cells then pulls from shared memory and writes the populations
+// and the displacement once.  Per two steps each population crosses HBM
+// once each way instead of twice; the window's halo (the neighbour tiles'
+// cells) is recomputed, and its loads are mostly L2 hits.
+//
+// Every cell update uses the arithmetic of the one-step kernel (the same
+// moments, flux, source, collision and wall functions, and 16-bit rounding
+// of the intermediate populations in shared memory), so two-step and
+// one-step launches give bit-identical states, traces and displacements.
+//
+// Warps (LBM_STEP2_COLS = 30, the default): a tile is 30 columns wide, so a
+// window row is 32 cells and each of the kF2H warps computes one window row
+// in step n; in step n + 1 lanes 1..30 of the warps of the tile's rows
+// update their own cells.  LBM_STEP2_COLS = 32: 32-wide tiles, kF2H warps
+// for the 32 columns above the tile's and one more warp for the two side
+// columns (2 kF2H = 32 cells).
+#pragma once
+
+#include "lbm_kernels.cuh"
+
+namespace lbm {
+
+#ifndef LBM_STEP2_COLS
+#define LBM_STEP2_COLS 30
+#endif
+constexpr int kF2Cols = LBM_STEP2_COLS;             // columns of a block's output tile
+constexpr int kF2Rows = 14;                         // rows of a block's output tile
+constexpr bool kF2Side = kF2Cols == 32;             // a separate warp for the side columns
+constexpr int kF2H = kF2Rows + 2;                   // rows of its window
+constexpr int kF2W = kF2Cols + 2;                   // columns of its window
+constexpr int kF2Warps = kF2H + (kF2Side ? 1 : 0);  // threads per block: 32 x kF2Warps
+static_assert(kF2Cols == 30 || kF2Cols == 32, "tiles are 30 or 32 columns wide");
+static_assert(!kF2Side || 2 * kF2H == 32, "the two side columns of the window fill one warp");
+
+// Resident blocks per SM the register budget is set for.
+#ifndef LBM_STEP2_MIN_BLOCKS
+#define LBM_STEP2_MIN_BLOCKS (kF2Side ? 3 : 4)
+#endif
+
+// The window in shared memory, [9][kF2H][kF2W]; element (0, 0) is grid cell
+// (ox, oy) = (x0 - 1, y0 - 1).  Cells beyond a periodic seam hold the
+// image's populations at their unwrapped coordinates.
+template <class T>
+struct TilePops {
+  const T *f;
+  int ox, oy;
+  static constexpr bool kWrap = false;
+  __device__ __forceinline__ const T *at(int i, int x, int y) const {
+    return f + ((i * kF2H + (y - oy)) * kF2W + (x - ox));
+  }
+};
+
+// Pull of population i into (x, y) from the window (general path; out of
+// line like the global-memory pull_general).
+template <class T, class C>
+__device__ __noinline__ C pull_general_tile(const StepParams &p, const T *tile, int ox, int oy,
+                                            int i, int x, int y) {
+  return pull_general_a<T, C>(p, TilePops<T>{tile, ox, oy}, i, x, y);
+}
+
+// Window cell of this thread: column ex, row ey; core: the cell is one of
+// the tile's.
+__device__ __forceinline__ void window_cell(int lane, int w, int &ex, int &ey, bool &core) {
+  if (!kF2Side) {
+    ex = lane;
+    ey = w;
+    core = w >= 1 && w <= kF2Rows && lane >= 1 && lane <= kF2Cols;
+  } else if (w < kF2H) {
+    ex = lane + 1;
+    ey = w;
+    core = w >= 1 && w <= kF2Rows;
+  } else {
+    ex = (lane & 1) ? kF2W - 1 : 0;
+    ey = lane >> 1;
+    core = false;
+  }
+}
+
+// Whether the tile at (x0, y0) needs the general rules: a wall or periodic
+// seam within two cells (step n reaches one cell beyond the tile and pulls
+// from one more), a source reaching the window, or (when recording) a
+// receiver among the tile's cells.  Warp-wide; every lane gets the same
+// answer.
+__device__ __forceinline__ bool tile_is_special(const StepParams &p, int x0, int y0) {
+  constexpr int W = kF2Cols, H = kF2Rows;
+  if (x0 < 2 || x0 + W > p.nx - 2 || y0 < 2 || y0 + H > p.ny - 2) return true;
+  const bool near_src = p.nsrc > 0 && x0 - 1 <= p.src_x1 && x0 + W >= p.src_x0 &&
+                        y0 - 1 <= p.src_y1 && y0 + H >= p.src_y0;
+  const bool near_rec = p.trace_slot >= 0 && x0 <= p.rec_x1 && x0 + W - 1 >= p.rec_x0 &&
+                        y0 <= p.rec_y1 && y0 + H - 1 >= p.rec_y0;
+  if (!near_src && !near_rec) return false;
+  if (near_src && p.nsrc > 32) return true;
+  const int lane = threadIdx.x & 31;
+  bool hit = false;
+  if (near_src && lane < p.nsrc) {
+    // window cells lie within W/2 + 1 columns and H/2 + 1 rows of the centre
+    const SourceDev &q = p.src[lane];
+    int dx = x0 + W / 2 - q.xc, dy = y0 + H / 2 - q.yc;
+    if (p.bc_left == BC_PERIODIC) {
+      if (dx > p.nx / 2) dx -= p.nx;
+      else if (dx < -(p.nx / 2)) dx += p.nx;
+    }
+    if (p.bc_top == BC_PERIODIC) {
+      if (dy > p.ny / 2) dy -= p.ny;
+      else if (dy < -(p.ny / 2)) dy += p.ny;
+    }
+    hit = abs(dx) <= q.rb + W / 2 + 2 && abs(dy) <= q.rb + H / 2 + 2;
+  }
+  if (near_rec) {
+    // receiver tiles (kRecTileX x kRecTileY) touched by the tile's cells
+    const int tx0 = x0 / kRecTileX, tx1 = min((x0 + W - 1) / kRecTileX, p.rec_tiles_x - 1);
+    const int ty0 = y0 / kRecTileY, ty1 = min((y0 + H - 1) / kRecTileY, (p.ny - 1) / kRecTileY);
+    const int nty = ty1 - ty0 + 1;
+    for (int j = lane; j < (tx1 - tx0 + 1) * nty; j += 32) {
+      const int t = (ty0 + j % nty) * p.rec_tiles_x + tx0 + j / nty;
+      hit |= p.rec_tile_ptr[t + 1] > p.rec_tile_ptr[t];
+    }
+  }
+  return __ballot_sync(0xffffffffu, hit) != 0u;
+}
+
+// Blocks within reach of a wall, seam, source or receiver: every cell runs
+// the general rules.  Step n is evaluated at each window cell's wrapped
+// coordinate (cells beyond a non-periodic edge are never read: the wall
+// rules replace them); step n + 1 at the tile's cells.  Out of line so the
+// bulk path carries none of its registers.  Every thread calls it (one
+// barrier).
+template <class T, class C, class U>
+__device__ __noinline__ void step2_general(const StepParams &p, int x0, int y0, T *tile) {
+  const int lane = threadIdx.x, w = threadIdx.y;
+  int ex, ey;
+  bool core;
+  window_cell(lane, w, ex, ey, core);
+  const int x = x0 - 1 + ex, y = y0 - 1 + ey;
+  int wx = x, wy = y;
+  bool valid = true;
+  if (x < 0 || x >= p.nx) {
+    if (p.bc_left == BC_PERIODIC) wx = ((x % p.nx) + p.nx) % p.nx;
+    else valid = false;
+  }
+  if (y < 0 || y >= p.ny) {
+    if (p.bc_top == BC_PERIODIC) wy = ((y % p.ny) + p.ny) % p.ny;
+    else valid = false;
+  }
+  const bool active = core && x < p.nx && y < p.ny;
+  const C om = par<C>(p.omega, p.omega_f), fc = par<C>(p.fcoef, p.fcoef_f);
+  U *u = (U *)p.u;
+  const int c = y * p.pitch + x;
+  U ux = U(0), uy = U(0);
+  C irho = C(0);
+  if (valid) {
+    C Fx, Fy;
+    body_force_cell<C>(p, wx, wy, p.n, Fx, Fy);
+    Fx *= force_scale<T, C>(p);
+    Fy *= force_scale<T, C>(p);
+    const T *fin = (const T *)p.fin;
+    C f[9];
+    if (wx >= 1 && wx < p.nx - 1 && wy >= 1 && wy < p.ny - 1) {
+      const T *b = fin + (wy * p.frow + wx);
+#pragma unroll
+      for (int i = 0; i < 9; ++i)
+        f[i] = ldp<T, C>(b + (i * p.fplane - cyd(i) * p.frow - cxd(i)), p);
+    } else {
+#pragma unroll
+      for (int i = 0; i < 9; ++i) f[i] = pull_general<T, C>(p, fin, i, wx, wy);
+    }
+    const Moments<C> M = cell_moments<C>(f);
+    C jx, jy, Sx, Sy, fs[9];
+    flux_and_source<C>(M.mx, M.my, C(0), C(0), Fx, Fy, sponge_A<C>(p, wx, wy), jx, jy, Sx, Sy);
+    collide_cell<C>(M, jx, jy, Sx, Sy, om, fc, fs);
+#pragma unroll
+    for (int i = 0; i < 9; ++i) st<T, C>(tile + ((i * kF2H + ey) * kF2W + ex), fs[i]);
+    if (active) {
+      irho = irho_at<T, C>(p, x, y);
+      const U vx = U(mul_rn(jx, irho)), vy = U(mul_rn(jy, irho));
+      ux = u[c] + vx;
+      uy = u[p.plane + c] + vy;
+      if (!((M.rho + jx + jy) * C(0) == C(0))) atomicOr(p.err, 1);
+      if (p.trace_slot >= 0) record_receiver<U>(p, p.trace_slot, x, y, ux, uy, vx, vy);
+    }
+  }
+  __syncthreads();
+  if (!active) return;
+  // step n + 1 of the tile's cell (x, y)
+  C Fx, Fy;
+  body_force_cell<C>(p, x, y, p.n + 1, Fx, Fy);
+  Fx *= force_scale<T, C>(p);
+  Fy *= force_scale<T, C>(p);
+  C f[9];
+  if (x >= 1 && x < p.nx - 1 && y >= 1 && y < p.ny - 1) {
+    const TilePops<T> tp{tile, x0 - 1, y0 - 1};
+#pragma unroll
+    for (int i = 0; i < 9; ++i) f[i] = ld<T, C>(tp.at(i, x - cxd(i), y - cyd(i)));
+  } else {
+#pragma unroll
+    for (int i = 0; i < 9; ++i)
+      f[i] = pull_general_tile<T, C>(p, tile, x0 - 1, y0 - 1, i, x, y);
+  }
+  const Moments<C> M = cell_moments<C>(f);
+  C jx, jy, Sx, Sy, fs[9];
+  flux_and_source<C>(M.mx, M.my, C(0), C(0), Fx, Fy, sponge_A<C>(p, x, y), jx, jy, Sx, Sy);
+  collide_cell<C>(M, jx, jy, Sx, Sy, om, fc, fs);
+  T *fout = (T *)p.fout + (y * p.frow + x);
+#pragma unroll
+  for (int i = 0; i < 9; ++i) stp<T, C>(fout + i * p.fplane, fs[i], p);
+  const U vx = U(mul_rn(jx, irho)), vy = U(mul_rn(jy, irho));
+  ux += vx;
+  uy += vy;
+  u[c] = ux;
+  u[p.plane + c] = uy;
+  if (!((M.rho + jx + jy) * C(0) == C(0))) atomicOr(p.err, 1);
+  if (p.trace_slot2 >= 0) record_receiver<U>(p, p.trace_slot2, x, y, ux, uy, vx, vy);
+}
+
+// Steps n = p.n and n + 1 from p.fin to p.fout, one block per kF2Cols x
+// kF2Rows tile; blocks of 32 x kF2Warps threads.  p.reverse: visit the
+// tiles in the reverse order (the top tile row still first), as the
+// one-step kernel does on alternate steps.
+template <class T, class C, class U>
+__global__ void __launch_bounds__(32 * kF2Warps, LBM_STEP2_MIN_BLOCKS)
+    step2_kernel(const StepParams p) {
+#if LBM_PDL
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;");
+#endif
+  __shared__ T tile[9 * kF2H * kF2W];
+  int bx = blockIdx.x, by = blockIdx.y;
+  if (p.reverse) {
+    if (by > 0) by = gridDim.y - by;
+    bx = gridDim.x - 1 - bx;
+  }
+  const int x0 = bx * kF2Cols, y0 = by * kF2Rows;
+  if (tile_is_special(p, x0, y0)) {
+    step2_general<T, C, U>(p, x0, y0, tile);
+    return;
+  }
+  const int lane = threadIdx.x, w = threadIdx.y;
+  int ex, ey;
+  bool core;
+  window_cell(lane, w, ex, ey, core);
+  const int x = x0 - 1 + ex, y = y0 - 1 + ey;
+  // step n on the window: every upstream cell is inside the grid
+  const T *fin = (const T *)p.fin;
+  C f[9];
+  {
+    const T *b = fin + (y * p.frow + x);
+#pragma unroll
+    for (int i = 0; i < 9; ++i) f[i] = ldp<T, C>(b + (i * p.fplane - cyd(i) * p.frow - cxd(i)), p);
+  }
+  U *u = (U *)p.u;
+  const int c = y * p.pitch + x;
+  U ux = U(0), uy = U(0);
+  C irho = C(0);
+  if (core) {
+    ux = u[c];
+    uy = u[p.plane + c];
+    irho = irho_at<T, C>(p, x, y);
+  }
+  const bool spg = x0 - 1 < p.sp_left || x0 + kF2Cols + 1 > p.nx - p.sp_right ||
+                   y0 - 1 < p.sp_top || y0 + kF2Rows + 1 > p.ny - p.sp_bottom;
+  {
+    const Moments<C> M = cell_moments<C>(f);
+    C jx, jy, fs[9];
+    bulk_collide<C>(p, M, C(0), C(0), spg, x, y, fs, jx, jy);
+#pragma unroll
+    for (int i = 0; i < 9; ++i) st<T, C>(tile + ((i * kF2H + ey) * kF2W + ex), fs[i]);
+    if (core) {
+      ux += U(mul_rn(jx, irho));
+      uy += U(mul_rn(jy, irho));
+      if (!((M.rho + jx + jy) * C(0) == C(0))) atomicOr(p.err, 1);
+    }
+  }
+  __syncthreads();
+  if (!core) return;
+  // step n + 1 of the tile's cell, pulled from the window
+#pragma unroll
+  for (int i = 0; i < 9; ++i)
+    f[i] = ld<T, C>(tile + ((i * kF2H + ey - cyd(i)) * kF2W + ex - cxd(i)));
+  const Moments<C> M = cell_moments<C>(f);
+  C jx, jy, fs[9];
+  bulk_collide<C>(p, M, C(0), C(0), spg, x, y, fs, jx, jy);
+  T *fout = (T *)p.fout + (y * p.frow + x);
+#pragma unroll
+  for (int i = 0; i < 9; ++i) stp<T, C>(fout + i * p.fplane, fs[i], p);
+  u[c] = ux + U(mul_rn(jx, irho));
+  u[p.plane + c] = uy + U(mul_rn(jy, irho));
+  if (!((M.rho + jx + jy) * C(0) == C(0))) atomicOr(p.err, 1);
+}
+
+// Launch configuration of the two-step kernel for an nx x ny grid.
+inline dim3 step2_grid(int nx, int ny) {
+  return dim3((nx + kF2Cols - 1) / kF2Cols, (ny + kF2Rows - 1) / kF2Rows, 1);
+}
+inline dim3 step2_block() { return dim3(32, kF2Warps, 1); }
+
+// Launch entry points, one translation unit per storage type.
+void launch_step2_f64(const StepParams &p, cudaStream_t s);
+void launch_step2_f32(const StepParams &p, bool u64, cudaStream_t s);
+void launch_step2_16(const StepParams &p, bool bf16, bool u64, cudaStream_t s);
+
+}  // namespace lbm

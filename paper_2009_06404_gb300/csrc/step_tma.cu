@@ -234,10 +234,11 @@ __global__ void __launch_bounds__(kTmaThreads, LBM_TMA_MIN_BLOCKS)
           while (mk) {
             const int b = __ffs(mk) - 1;
             mk &= mk - 1;
-            const double2 F = source_term(p.src[b], xc, yc, p.n, p.nx, p.ny,
-                                          p.bc_left == BC_PERIODIC, p.bc_top == BC_PERIODIC);
-            Fx += (float)F.x;
-            Fy += (float)F.y;
+            const float2 F = source_term(p.src[b], xc, yc, p.n, p.nx, p.ny,
+                                         p.bc_left == BC_PERIODIC, p.bc_top == BC_PERIODIC,
+                                         0.0f);
+            Fx += F.x;
+            Fy += F.y;
           }
         } else {
           body_force<float>(p, xc, yc, Fx, Fy);  // whole warp: one row, 32 consecutive x
@@ -278,7 +279,7 @@ __global__ void __launch_bounds__(kTmaThreads, LBM_TMA_MIN_BLOCKS)
       u[c] = ux;
       u[p.plane + c] = uy;
       if (!((M.rho + jx + jy) * 0.f == 0.f)) atomicOr(p.err, 1);
-      if (rec) record_receiver<U>(p, x, y, ux, uy, vx, vy);
+      if (rec) record_receiver<U>(p, p.trace_slot, x, y, ux, uy, vx, vy);
     }
     __syncthreads();  // every thread is done with stage s
     if (tid == 0) {

@@ -439,11 +439,14 @@ def test_16bit_storage_random_state(storage, k, bcname):
     assert max_rel(u, st.u) <= TOL_16[storage]
 
 
-@pytest.mark.parametrize("storage,k,tol", [("f16", 10, 2e-3), ("bf16", 0, 5e-2)])
+@pytest.mark.parametrize("storage,k,tol", [("f16", 10, 5e-3), ("bf16", 0, 5e-2)])
 def test_16bit_halfspace_traces_first_1000_steps(storage, k, tol):
     """The full half-space with 16-bit storage: surface traces of the first
-    1000 steps against the stored oracle samples (measured: FP16 5.5e-4,
-    BF16 1.8e-2 rel-L2)."""
+    1000 steps against the stored oracle samples.  A 16-bit run's error is
+    one realization of a walk of storage roundings: changing the source
+    amplitude by 1e-6 moves it between 5.5e-4 and 2.2e-3 rel-L2 (FP16) and
+    between 1.8e-2 and 3.2e-2 (BF16).  The FP16 tolerance is below the
+    random-walk scale of 1000 half-ulp roundings, sqrt(1000) 2^-12 = 7.7e-3."""
     g = np.load(os.path.join(ROOT, "tests", "golden", "halfspace_2048x1024_4000.npz"))
     w = _wl().halfspace(nsteps=1000, storage=storage)
     sim = _pkg().from_workload(w, store_scale_log2=k, max_steps_traced=1000)
