@@ -306,6 +306,21 @@ def run_gpu(args):
     _, e2e_rate = aggregate(e2e_ms, cells_steps * args.steps, dist, "cuda")
     e2e_value = e2e_rate / 1e6
 
+    # --------------------------------------------------- the one-step kernel, same shots
+    one_step_ms, one_step_shots = None, min(args.steps, 3)
+    if spl == 2:
+        sim.set_steps_per_launch(1)
+        flush.fill_(2)
+        shot()
+        one_step_ms = 0.0
+        for k in range(one_step_shots):
+            flush.fill_(k & 0xFF)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            shot((e0, e1))
+            torch.cuda.synchronize()
+            one_step_ms += e0.elapsed_time(e1)
+        sim.set_steps_per_launch(spl)
+
     # --------------------------------------------------- roofline of the step kernel
     peak, peak_kind = _peaks()
     # a launch moves every population and the displacement once each way,
@@ -314,6 +329,12 @@ def run_gpu(args):
     bytes_launch = BYTES_PER_CELL[storage] * w.cells
     achieved = bytes_launch / avg_launch_s / 1e9
     kname = "step2_kernel" if spl == 2 else "step_kernel"
+    one_step = None
+    if one_step_ms is not None:
+        l1_s = one_step_ms / 1e3 / (one_step_shots * w.nsteps)
+        one_step = {"kernel": "step_kernel", "shots": one_step_shots,
+                    "mlups": w.cells / l1_s / 1e6, "avg_launch_us": l1_s * 1e6,
+                    "achieved": bytes_launch / l1_s / 1e9, "frac": bytes_launch / l1_s / 1e9 / peak}
     traffic = None
     prof = os.path.join(ROOT, "profiles", "traffic.json")
     if os.path.exists(prof):
@@ -363,7 +384,12 @@ def run_gpu(args):
                      "steps_per_launch": spl,
                      "bytes_per_cell_per_launch": BYTES_PER_CELL[storage],
                      "bytes_per_cell_step": BYTES_PER_CELL[storage] / spl,
-                     "avg_launch_us": avg_launch_s * 1e6},
+                     "avg_launch_us": avg_launch_s * 1e6,
+                     # the same launches counted at the one-step figure of
+                     # BYTES_PER_CELL per cell and time step (above 1: the
+                     # two-step kernel moves fewer bytes than one step would)
+                     "frac_at_one_step_bytes": achieved * spl / peak,
+                     "one_step_kernel": one_step},
         "cpu_baseline": cpu,
         "e2e": {"value": e2e_value, "unit": UNIT,
                 "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
