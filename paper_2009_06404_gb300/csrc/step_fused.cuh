@@ -15,6 +15,12 @@
 // of the intermediate populations in shared memory), so two-step and
 // one-step launches give bit-identical states, traces and displacements.
 //
+// Non-finite values are tested in step n + 1 only: a non-finite population
+// of step n reaches the step n + 1 moments of some tile cell in the same
+// launch (its own cell's rest population if the density is non-finite, the
+// neighbours' otherwise; a window's halo cell is also a tile cell of the
+// block that owns it, which recomputes it the same way).
+//
 // Warps (LBM_STEP2_COLS = 30, the default): a tile is 30 columns wide, so a
 // window row is 32 cells and each of the kF2H warps computes one window row
 // in step n; in step n + 1 lanes 1..30 of the warps of the tile's rows
@@ -30,18 +36,22 @@ namespace lbm {
 #ifndef LBM_STEP2_COLS
 #define LBM_STEP2_COLS 30
 #endif
+#ifndef LBM_STEP2_ROWS
+#define LBM_STEP2_ROWS 14
+#endif
 constexpr int kF2Cols = LBM_STEP2_COLS;             // columns of a block's output tile
-constexpr int kF2Rows = 14;                         // rows of a block's output tile
+constexpr int kF2Rows = LBM_STEP2_ROWS;             // rows of a block's output tile
 constexpr bool kF2Side = kF2Cols == 32;             // a separate warp for the side columns
 constexpr int kF2H = kF2Rows + 2;                   // rows of its window
 constexpr int kF2W = kF2Cols + 2;                   // columns of its window
 constexpr int kF2Warps = kF2H + (kF2Side ? 1 : 0);  // threads per block: 32 x kF2Warps
 static_assert(kF2Cols == 30 || kF2Cols == 32, "tiles are 30 or 32 columns wide");
 static_assert(!kF2Side || 2 * kF2H == 32, "the two side columns of the window fill one warp");
+static_assert(kF2Warps <= 32, "at most 1024 threads per block");
 
 // Resident blocks per SM the register budget is set for.
 #ifndef LBM_STEP2_MIN_BLOCKS
-#define LBM_STEP2_MIN_BLOCKS (kF2Side ? 3 : 4)
+#define LBM_STEP2_MIN_BLOCKS (2048 / (32 * kF2Warps))
 #endif
 
 // The window in shared memory, [9][kF2H][kF2W]; element (0, 0) is grid cell
@@ -83,23 +93,38 @@ __device__ __forceinline__ void window_cell(int lane, int w, int &ex, int &ey, b
   }
 }
 
-// Whether the tile at (x0, y0) needs the general rules: a wall or periodic
-// seam within two cells (step n reaches one cell beyond the tile and pulls
-// from one more), a source reaching the window, or (when recording) a
-// receiver among the tile's cells.  Warp-wide; every lane gets the same
-// answer.
-__device__ __forceinline__ bool tile_is_special(const StepParams &p, int x0, int y0) {
+// Kinds of tile, from its position only (every lane of every warp gets the
+// same answer).  kTileGeneral: the general rules -- a non-periodic edge
+// within two cells (step n reaches one cell beyond the tile and pulls from
+// one more), a partial tile, or a periodic axis shorter than two tiles.
+// Otherwise any of: kTileWrap, the window or its pulls cross a periodic
+// seam; kTileSrc, a source reaches the window; kTileRec, a receiver is
+// among the tile's cells (when recording).  0: the plain bulk update.
+enum { kTileGeneral = 1, kTileWrap = 2, kTileSrc = 4, kTileRec = 8 };
+
+__device__ __forceinline__ int tile_kind(const StepParams &p, int x0, int y0) {
   constexpr int W = kF2Cols, H = kF2Rows;
-  if (x0 < 2 || x0 + W > p.nx - 2 || y0 < 2 || y0 + H > p.ny - 2) return true;
+  int kind = 0;
+  if (p.bc_left == BC_PERIODIC) {
+    if (x0 + W > p.nx || p.nx < 2 * W) return kTileGeneral;
+    if (x0 < 2 || x0 + W > p.nx - 2) kind |= kTileWrap;
+  } else if (x0 < 2 || x0 + W > p.nx - 2) {
+    return kTileGeneral;
+  }
+  if (p.bc_top == BC_PERIODIC) {
+    if (y0 + H > p.ny || p.ny < 2 * H) return kTileGeneral;
+    if (y0 < 2 || y0 + H > p.ny - 2) kind |= kTileWrap;
+  } else if (y0 < 2 || y0 + H > p.ny - 2) {
+    return kTileGeneral;
+  }
   const bool near_src = p.nsrc > 0 && x0 - 1 <= p.src_x1 && x0 + W >= p.src_x0 &&
                         y0 - 1 <= p.src_y1 && y0 + H >= p.src_y0;
   const bool near_rec = p.trace_slot >= 0 && x0 <= p.rec_x1 && x0 + W - 1 >= p.rec_x0 &&
                         y0 <= p.rec_y1 && y0 + H - 1 >= p.rec_y0;
-  if (!near_src && !near_rec) return false;
-  if (near_src && p.nsrc > 32) return true;
+  if (!near_src && !near_rec) return kind;
   const int lane = threadIdx.x & 31;
-  bool hit = false;
-  if (near_src && lane < p.nsrc) {
+  bool hit_src = near_src && p.nsrc > 32;
+  if (near_src && p.nsrc <= 32 && lane < p.nsrc) {
     // window cells lie within W/2 + 1 columns and H/2 + 1 rows of the centre
     const SourceDev &q = p.src[lane];
     int dx = x0 + W / 2 - q.xc, dy = y0 + H / 2 - q.yc;
@@ -111,8 +136,9 @@ __device__ __forceinline__ bool tile_is_special(const StepParams &p, int x0, int
       if (dy > p.ny / 2) dy -= p.ny;
       else if (dy < -(p.ny / 2)) dy += p.ny;
     }
-    hit = abs(dx) <= q.rb + W / 2 + 2 && abs(dy) <= q.rb + H / 2 + 2;
+    hit_src = abs(dx) <= q.rb + W / 2 + 2 && abs(dy) <= q.rb + H / 2 + 2;
   }
+  bool hit_rec = false;
   if (near_rec) {
     // receiver tiles (kRecTileX x kRecTileY) touched by the tile's cells
     const int tx0 = x0 / kRecTileX, tx1 = min((x0 + W - 1) / kRecTileX, p.rec_tiles_x - 1);
@@ -120,10 +146,12 @@ __device__ __forceinline__ bool tile_is_special(const StepParams &p, int x0, int
     const int nty = ty1 - ty0 + 1;
     for (int j = lane; j < (tx1 - tx0 + 1) * nty; j += 32) {
       const int t = (ty0 + j % nty) * p.rec_tiles_x + tx0 + j / nty;
-      hit |= p.rec_tile_ptr[t + 1] > p.rec_tile_ptr[t];
+      hit_rec |= p.rec_tile_ptr[t + 1] > p.rec_tile_ptr[t];
     }
   }
-  return __ballot_sync(0xffffffffu, hit) != 0u;
+  if (__ballot_sync(0xffffffffu, hit_src)) kind |= kTileSrc;
+  if (__ballot_sync(0xffffffffu, hit_rec)) kind |= kTileRec;
+  return kind;
 }
 
 // Blocks within reach of a wall, seam, source or receiver: every cell runs
@@ -182,7 +210,6 @@ __device__ __noinline__ void step2_general(const StepParams &p, int x0, int y0, 
       const U vx = U(mul_rn(jx, irho)), vy = U(mul_rn(jy, irho));
       ux = u[c] + vx;
       uy = u[p.plane + c] + vy;
-      if (!((M.rho + jx + jy) * C(0) == C(0))) atomicOr(p.err, 1);
       if (p.trace_slot >= 0) record_receiver<U>(p, p.trace_slot, x, y, ux, uy, vx, vy);
     }
   }
@@ -219,6 +246,100 @@ __device__ __noinline__ void step2_general(const StepParams &p, int x0, int y0, 
   if (p.trace_slot2 >= 0) record_receiver<U>(p, p.trace_slot2, x, y, ux, uy, vx, vy);
 }
 
+// A coordinate one period back into the grid (at most one period out).
+__device__ __forceinline__ int wrap1(int v, int n) { return v < 0 ? v + n : (v >= n ? v - n : v); }
+
+// Tiles without a non-periodic edge nearby whose window crosses a periodic
+// seam, or that a source reaches, or that hold receivers: the bulk update
+// with the window's cells and pulls wrapped, the body force where a source
+// reaches, and the receivers recorded.  Out of line, so the plain bulk path
+// carries none of its registers.  Every thread calls it (one barrier).
+template <class T, class C, class U, bool SRC>
+__device__ __noinline__ void step2_featured(const StepParams &p, int x0, int y0, int kind,
+                                            T *tile) {
+  const int lane = threadIdx.x, w = threadIdx.y;
+  int ex, ey;
+  bool core;
+  window_cell(lane, w, ex, ey, core);
+  const int x = x0 - 1 + ex, y = y0 - 1 + ey;  // tile cells: inside the grid
+  const int wx = wrap1(x, p.nx), wy = wrap1(y, p.ny);
+  constexpr bool src = SRC;  // kind & kTileSrc
+  const bool spg = (kind & kTileWrap) || x0 - 1 < p.sp_left || x0 + kF2Cols + 1 > p.nx - p.sp_right ||
+                   y0 - 1 < p.sp_top || y0 + kF2Rows + 1 > p.ny - p.sp_bottom;
+  const C om = par<C>(p.omega, p.omega_f), fc = par<C>(p.fcoef, p.fcoef_f);
+  // step n on the window
+  const T *fin = (const T *)p.fin;
+  C f[9];
+  {
+    const int xs[3] = {wrap1(wx - 1, p.nx), wx, wrap1(wx + 1, p.nx)};
+    const int ys[3] = {wrap1(wy - 1, p.ny), wy, wrap1(wy + 1, p.ny)};
+#pragma unroll
+    for (int i = 0; i < 9; ++i)
+      f[i] = ldp<T, C>(fin + (i * p.fplane + (ys[1 - cyd(i)] * p.frow + xs[1 - cxd(i)])), p);
+  }
+  U *u = (U *)p.u;
+  const int c = y * p.pitch + x;
+  U ux = U(0), uy = U(0);
+  C irho = C(0);
+  if (core) {
+    ux = u[c];
+    uy = u[p.plane + c];
+    irho = irho_at<T, C>(p, x, y);
+  }
+  {
+    const Moments<C> M = cell_moments<C>(f);
+    C jx, jy, fs[9];
+    if (src) {  // (a compile-time branch)
+      C Fx, Fy, Sx, Sy;
+      body_force_cell<C>(p, wx, wy, p.n, Fx, Fy);
+      Fx *= force_scale<T, C>(p);
+      Fy *= force_scale<T, C>(p);
+      flux_and_source<C>(M.mx, M.my, C(0), C(0), Fx, Fy, sponge_A<C>(p, wx, wy), jx, jy, Sx, Sy);
+      collide_cell<C>(M, jx, jy, Sx, Sy, om, fc, fs);
+    } else {
+      bulk_collide<C>(p, M, C(0), C(0), spg, wx, wy, fs, jx, jy);
+    }
+#pragma unroll
+    for (int i = 0; i < 9; ++i) st<T, C>(tile + ((i * kF2H + ey) * kF2W + ex), fs[i]);
+    if (core) {
+      const U vx = U(mul_rn(jx, irho)), vy = U(mul_rn(jy, irho));
+      ux += vx;
+      uy += vy;
+      if ((kind & kTileRec) && p.trace_slot >= 0)
+        record_receiver<U>(p, p.trace_slot, x, y, ux, uy, vx, vy);
+    }
+  }
+  __syncthreads();
+  if (!core) return;
+  // step n + 1 of the tile's cell, pulled from the window
+#pragma unroll
+  for (int i = 0; i < 9; ++i)
+    f[i] = ld<T, C>(tile + ((i * kF2H + ey - cyd(i)) * kF2W + ex - cxd(i)));
+  const Moments<C> M = cell_moments<C>(f);
+  C jx, jy, fs[9];
+  if (src) {
+    C Fx, Fy, Sx, Sy;
+    body_force_cell<C>(p, x, y, p.n + 1, Fx, Fy);
+    Fx *= force_scale<T, C>(p);
+    Fy *= force_scale<T, C>(p);
+    flux_and_source<C>(M.mx, M.my, C(0), C(0), Fx, Fy, sponge_A<C>(p, x, y), jx, jy, Sx, Sy);
+    collide_cell<C>(M, jx, jy, Sx, Sy, om, fc, fs);
+  } else {
+    bulk_collide<C>(p, M, C(0), C(0), spg, x, y, fs, jx, jy);
+  }
+  T *fout = (T *)p.fout + (y * p.frow + x);
+#pragma unroll
+  for (int i = 0; i < 9; ++i) stp<T, C>(fout + i * p.fplane, fs[i], p);
+  const U vx = U(mul_rn(jx, irho)), vy = U(mul_rn(jy, irho));
+  ux += vx;
+  uy += vy;
+  u[c] = ux;
+  u[p.plane + c] = uy;
+  if (!((M.rho + jx + jy) * C(0) == C(0))) atomicOr(p.err, 1);
+  if ((kind & kTileRec) && p.trace_slot2 >= 0)
+    record_receiver<U>(p, p.trace_slot2, x, y, ux, uy, vx, vy);
+}
+
 // Steps n = p.n and n + 1 from p.fin to p.fout, one block per kF2Cols x
 // kF2Rows tile; blocks of 32 x kF2Warps threads.  p.reverse: visit the
 // tiles in the reverse order (the top tile row still first), as the
@@ -237,8 +358,17 @@ __global__ void __launch_bounds__(32 * kF2Warps, LBM_STEP2_MIN_BLOCKS)
     bx = gridDim.x - 1 - bx;
   }
   const int x0 = bx * kF2Cols, y0 = by * kF2Rows;
-  if (tile_is_special(p, x0, y0)) {
+  const int kind = tile_kind(p, x0, y0);
+  if (kind & kTileGeneral) {
     step2_general<T, C, U>(p, x0, y0, tile);
+    return;
+  }
+  if (kind & kTileSrc) {
+    step2_featured<T, C, U, true>(p, x0, y0, kind, tile);
+    return;
+  }
+  if (kind) {
+    step2_featured<T, C, U, false>(p, x0, y0, kind, tile);
     return;
   }
   const int lane = threadIdx.x, w = threadIdx.y;
@@ -274,7 +404,6 @@ __global__ void __launch_bounds__(32 * kF2Warps, LBM_STEP2_MIN_BLOCKS)
     if (core) {
       ux += U(mul_rn(jx, irho));
       uy += U(mul_rn(jy, irho));
-      if (!((M.rho + jx + jy) * C(0) == C(0))) atomicOr(p.err, 1);
     }
   }
   __syncthreads();
