@@ -21,6 +21,8 @@ struct Layout {
   size_t f[2] = {0, 0}, u = 0, lam = 0, irho = 0, src = 0, rec_ptr = 0, rec_xy = 0,
          rec_id = 0, traces = 0, partials = 0, flags = 0, stage = 0, total = 0;
   int rec_tiles_x = 0, rec_tiles = 0, stage_rows = 0;
+  size_t done = 0;                // persistent two-step form: per-tile phase counters
+  int tiles2x = 0, tiles2y = 0;   // its tiles per row and per column
   long long mat_count = 0;
 };
 
@@ -40,7 +42,10 @@ struct lbm_elastic {
   int traced = 0;
   int nsrc = 0, nrec = 0;
   bool lambda_nonzero = false;
-  int steps_per_launch = 2;    // lbm_elastic_step: 1, or 2 (two-step kernel where it applies)
+  int steps_per_launch = 2;    // lbm_elastic_step: 1, 2, or 0 (persistent two-step form)
+  long long persist_wait = 0;  // persistent form: wait limit in SM cycles (0: default)
+  int persist_hold = -1;       // persistent form, tests: tile that never publishes
+  int persist_blocks = -1;     // resident blocks per SM of the persistent kernel (-1: unknown)
   long long launches = 0;
   std::vector<lbm::SourceDev> src_host;
   int src_box[4] = {0, -1, 0, -1};  // x0, x1, y0, y1 of all source footprints

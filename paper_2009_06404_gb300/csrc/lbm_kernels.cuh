@@ -73,7 +73,7 @@ struct StepParams {
   int nsrc;
   long long n;       // index of this step (force time t = n)
   int trace_slot;    // >= 0: record receivers into this slot
-  int trace_slot2;   // two-step launches: the slot of step n + 1 (or -1)
+  int trace_end;     // two-step launches: trace slots below this exist
   const int *rec_tile_ptr;  // [tiles + 1] CSR over receiver tiles
   const int *rec_xy;        // [nrec][2]  sorted by tile
   const int *rec_id;        // [nrec]     original receiver index
@@ -133,9 +133,21 @@ template <> __device__ __forceinline__ void st<__nv_bfloat16, float>(__nv_bfloat
 // every rounding is the unscaled one times 2^k): only the body force enters
 // times 2^k, and 1/rho0 (for u += j / rho0) and the fields read out carry
 // 2^-k (see force_scale, irho_at).
+//
+// Global loads of populations and displacements go to L2 directly (ld.cg):
+// within a step no cell's value is loaded twice by one block, and a kernel
+// that advances several steps with blocks waiting on one another (the
+// persistent two-step kernel) must not read a stale line from the SM's L1.
+template <class T, class C> __device__ __forceinline__ C ldg(const T *p) { return C(__ldcg(p)); }
+template <> __device__ __forceinline__ float ldg<__half, float>(const __half *p) {
+  return __half2float(__ldcg(p));
+}
+template <> __device__ __forceinline__ float ldg<__nv_bfloat16, float>(const __nv_bfloat16 *p) {
+  return __bfloat162float(__ldcg(p));
+}
 template <class T, class C>
 __device__ __forceinline__ C ldp(const T *ptr, const StepParams &) {
-  return ld<T, C>(ptr);
+  return ldg<T, C>(ptr);
 }
 template <class T, class C>
 __device__ __forceinline__ void stp(T *ptr, C v, const StepParams &) {
@@ -216,8 +228,9 @@ struct GridPops {
   const T *f;
   int fplane, frow;
   static constexpr bool kWrap = true;
-  __device__ __forceinline__ const T *at(int i, int x, int y) const {
-    return f + (i * fplane + (y * frow + x));
+  template <class C>
+  __device__ __forceinline__ C load(int i, int x, int y) const {
+    return ldg<T, C>(f + (i * fplane + (y * frow + x)));
   }
 };
 
@@ -229,7 +242,7 @@ __device__ void cell_rho_pdiag(const StepParams &p, const A &a, int x, int y, C 
                                C &pyy) {
   C v[9];
 #pragma unroll
-  for (int i = 0; i < 9; ++i) v[i] = ldp<T, C>(a.at(i, x, y), p);
+  for (int i = 0; i < 9; ++i) v[i] = a.template load<C>(i, x, y);
   rho = v[0] + v[1] + v[2] + v[3] + v[4] + v[5] + v[6] + v[7] + v[8];
   pxx = v[1] + v[3] + v[5] + v[6] + v[7] + v[8];
   pyy = v[2] + v[4] + v[5] + v[6] + v[7] + v[8];
@@ -244,7 +257,7 @@ template <class T, class C, class A>
 __device__ C wall_value(const StepParams &p, const A &a, int bc, int nxo, int nyo, int i, int x,
                         int y) {
   const int k = oppd(i);
-  const C fk = ldp<T, C>(a.at(k, x, y), p);
+  const C fk = a.template load<C>(k, x, y);
   if (bc == BC_RIGID) return fk;
   C rb, pxxb, pyyb, ri, pxxi, pyyi;
   cell_rho_pdiag<T, C>(p, a, x, y, rb, pxxb, pyyb);
@@ -296,7 +309,7 @@ __device__ __forceinline__ C pull_general_a(const StepParams &p, const A &a, int
       return wall_value<T, C>(p, a, p.bc_right, 1, 0, i, x, y);
     }
   }
-  return ldp<T, C>(a.at(i, sx, sy), p);
+  return a.template load<C>(i, sx, sy);
 }
 
 template <class T, class C>

@@ -38,4 +38,13 @@ void launch_step2_f32(const StepParams &p, bool u64, cudaStream_t s) {
   else launch_pdl(step2_kernel<float, float, float>, grid, block, s, p);
 }
 
+cudaError_t launch_step2_run_f32(const Step2Run &r, bool u64, int grid, cudaStream_t s) {
+  return u64 ? launch_step2_run_t<float, float, double>(r, grid, s)
+             : launch_step2_run_t<float, float, float>(r, grid, s);
+}
+int step2_run_blocks_f32(bool u64) {
+  return u64 ? step2_persistent_blocks_t<float, float, double>()
+             : step2_persistent_blocks_t<float, float, float>();
+}
+
 }  // namespace lbm

@@ -65,6 +65,10 @@ struct TilePops {
   __device__ __forceinline__ const T *at(int i, int x, int y) const {
     return f + ((i * kF2H + (y - oy)) * kF2W + (x - ox));
   }
+  template <class C>
+  __device__ __forceinline__ C load(int i, int x, int y) const {
+    return ld<T, C>(at(i, x, y));
+  }
 };
 
 // Pull of population i into (x, y) from the window (general path; out of
@@ -73,6 +77,29 @@ template <class T, class C>
 __device__ __noinline__ C pull_general_tile(const StepParams &p, const T *tile, int ox, int oy,
                                             int i, int x, int y) {
   return pull_general_a<T, C>(p, TilePops<T>{tile, ox, oy}, i, x, y);
+}
+
+// What changes from one two-step phase to the next: phase k of a run reads
+// what phase k - 1 wrote (the two buffers alternate), advances steps
+// n + 2k and n + 2k + 1, and records into trace slots trace_slot + 2k and
+// trace_slot + 2k + 1 while they exist.  The rest of the step's parameters
+// stay in the kernel's parameter space.
+struct Phase2 {
+  const void *fin;
+  void *fout;
+  long long n;
+  int slot_a, slot_b;
+};
+__device__ __forceinline__ Phase2 phase2(const StepParams &p, int k) {
+  Phase2 q;
+  const bool odd = k & 1;
+  q.fin = odd ? (const void *)p.fout : p.fin;
+  q.fout = odd ? (void *)p.fin : p.fout;
+  q.n = p.n + 2LL * k;
+  const int s = p.trace_slot + 2 * k;
+  q.slot_a = (p.trace_slot >= 0 && s < p.trace_end) ? s : -1;
+  q.slot_b = (p.trace_slot >= 0 && s + 1 < p.trace_end) ? s + 1 : -1;
+  return q;
 }
 
 // Window cell of this thread: column ex, row ey; core: the cell is one of
@@ -102,7 +129,7 @@ __device__ __forceinline__ void window_cell(int lane, int w, int &ex, int &ey, b
 // among the tile's cells (when recording).  0: the plain bulk update.
 enum { kTileGeneral = 1, kTileWrap = 2, kTileSrc = 4, kTileRec = 8 };
 
-__device__ __forceinline__ int tile_kind(const StepParams &p, int x0, int y0) {
+__device__ __forceinline__ int tile_kind(const StepParams &p, int x0, int y0, int slot_a) {
   constexpr int W = kF2Cols, H = kF2Rows;
   int kind = 0;
   if (p.bc_left == BC_PERIODIC) {
@@ -119,7 +146,7 @@ __device__ __forceinline__ int tile_kind(const StepParams &p, int x0, int y0) {
   }
   const bool near_src = p.nsrc > 0 && x0 - 1 <= p.src_x1 && x0 + W >= p.src_x0 &&
                         y0 - 1 <= p.src_y1 && y0 + H >= p.src_y0;
-  const bool near_rec = p.trace_slot >= 0 && x0 <= p.rec_x1 && x0 + W - 1 >= p.rec_x0 &&
+  const bool near_rec = slot_a >= 0 && x0 <= p.rec_x1 && x0 + W - 1 >= p.rec_x0 &&
                         y0 <= p.rec_y1 && y0 + H - 1 >= p.rec_y0;
   if (!near_src && !near_rec) return kind;
   const int lane = threadIdx.x & 31;
@@ -161,7 +188,8 @@ __device__ __forceinline__ int tile_kind(const StepParams &p, int x0, int y0) {
 // bulk path carries none of its registers.  Every thread calls it (one
 // barrier).
 template <class T, class C, class U>
-__device__ __noinline__ void step2_general(const StepParams &p, int x0, int y0, T *tile) {
+__device__ __noinline__ void step2_general(const StepParams &p, int x0, int y0, T *tile, int k) {
+  const Phase2 ph = phase2(p, k);
   const int lane = threadIdx.x, w = threadIdx.y;
   int ex, ey;
   bool core;
@@ -185,10 +213,10 @@ __device__ __noinline__ void step2_general(const StepParams &p, int x0, int y0, 
   C irho = C(0);
   if (valid) {
     C Fx, Fy;
-    body_force_cell<C>(p, wx, wy, p.n, Fx, Fy);
+    body_force_cell<C>(p, wx, wy, ph.n, Fx, Fy);
     Fx *= force_scale<T, C>(p);
     Fy *= force_scale<T, C>(p);
-    const T *fin = (const T *)p.fin;
+    const T *fin = (const T *)ph.fin;
     C f[9];
     if (wx >= 1 && wx < p.nx - 1 && wy >= 1 && wy < p.ny - 1) {
       const T *b = fin + (wy * p.frow + wx);
@@ -208,16 +236,16 @@ __device__ __noinline__ void step2_general(const StepParams &p, int x0, int y0, 
     if (active) {
       irho = irho_at<T, C>(p, x, y);
       const U vx = U(mul_rn(jx, irho)), vy = U(mul_rn(jy, irho));
-      ux = u[c] + vx;
-      uy = u[p.plane + c] + vy;
-      if (p.trace_slot >= 0) record_receiver<U>(p, p.trace_slot, x, y, ux, uy, vx, vy);
+      ux = __ldcg(u + c) + vx;
+      uy = __ldcg(u + p.plane + c) + vy;
+      if (ph.slot_a >= 0) record_receiver<U>(p, ph.slot_a, x, y, ux, uy, vx, vy);
     }
   }
   __syncthreads();
   if (!active) return;
   // step n + 1 of the tile's cell (x, y)
   C Fx, Fy;
-  body_force_cell<C>(p, x, y, p.n + 1, Fx, Fy);
+  body_force_cell<C>(p, x, y, ph.n + 1, Fx, Fy);
   Fx *= force_scale<T, C>(p);
   Fy *= force_scale<T, C>(p);
   C f[9];
@@ -234,7 +262,7 @@ __device__ __noinline__ void step2_general(const StepParams &p, int x0, int y0, 
   C jx, jy, Sx, Sy, fs[9];
   flux_and_source<C>(M.mx, M.my, C(0), C(0), Fx, Fy, sponge_A<C>(p, x, y), jx, jy, Sx, Sy);
   collide_cell<C>(M, jx, jy, Sx, Sy, om, fc, fs);
-  T *fout = (T *)p.fout + (y * p.frow + x);
+  T *fout = (T *)ph.fout + (y * p.frow + x);
 #pragma unroll
   for (int i = 0; i < 9; ++i) stp<T, C>(fout + i * p.fplane, fs[i], p);
   const U vx = U(mul_rn(jx, irho)), vy = U(mul_rn(jy, irho));
@@ -243,7 +271,7 @@ __device__ __noinline__ void step2_general(const StepParams &p, int x0, int y0, 
   u[c] = ux;
   u[p.plane + c] = uy;
   if (!((M.rho + jx + jy) * C(0) == C(0))) atomicOr(p.err, 1);
-  if (p.trace_slot2 >= 0) record_receiver<U>(p, p.trace_slot2, x, y, ux, uy, vx, vy);
+  if (ph.slot_b >= 0) record_receiver<U>(p, ph.slot_b, x, y, ux, uy, vx, vy);
 }
 
 // A coordinate one period back into the grid (at most one period out).
@@ -256,7 +284,8 @@ __device__ __forceinline__ int wrap1(int v, int n) { return v < 0 ? v + n : (v >
 // carries none of its registers.  Every thread calls it (one barrier).
 template <class T, class C, class U, bool SRC>
 __device__ __noinline__ void step2_featured(const StepParams &p, int x0, int y0, int kind,
-                                            T *tile) {
+                                            T *tile, int k) {
+  const Phase2 ph = phase2(p, k);
   const int lane = threadIdx.x, w = threadIdx.y;
   int ex, ey;
   bool core;
@@ -268,7 +297,7 @@ __device__ __noinline__ void step2_featured(const StepParams &p, int x0, int y0,
                    y0 - 1 < p.sp_top || y0 + kF2Rows + 1 > p.ny - p.sp_bottom;
   const C om = par<C>(p.omega, p.omega_f), fc = par<C>(p.fcoef, p.fcoef_f);
   // step n on the window
-  const T *fin = (const T *)p.fin;
+  const T *fin = (const T *)ph.fin;
   C f[9];
   {
     const int xs[3] = {wrap1(wx - 1, p.nx), wx, wrap1(wx + 1, p.nx)};
@@ -282,8 +311,8 @@ __device__ __noinline__ void step2_featured(const StepParams &p, int x0, int y0,
   U ux = U(0), uy = U(0);
   C irho = C(0);
   if (core) {
-    ux = u[c];
-    uy = u[p.plane + c];
+    ux = __ldcg(u + c);
+    uy = __ldcg(u + p.plane + c);
     irho = irho_at<T, C>(p, x, y);
   }
   {
@@ -291,7 +320,7 @@ __device__ __noinline__ void step2_featured(const StepParams &p, int x0, int y0,
     C jx, jy, fs[9];
     if (src) {  // (a compile-time branch)
       C Fx, Fy, Sx, Sy;
-      body_force_cell<C>(p, wx, wy, p.n, Fx, Fy);
+      body_force_cell<C>(p, wx, wy, ph.n, Fx, Fy);
       Fx *= force_scale<T, C>(p);
       Fy *= force_scale<T, C>(p);
       flux_and_source<C>(M.mx, M.my, C(0), C(0), Fx, Fy, sponge_A<C>(p, wx, wy), jx, jy, Sx, Sy);
@@ -305,8 +334,8 @@ __device__ __noinline__ void step2_featured(const StepParams &p, int x0, int y0,
       const U vx = U(mul_rn(jx, irho)), vy = U(mul_rn(jy, irho));
       ux += vx;
       uy += vy;
-      if ((kind & kTileRec) && p.trace_slot >= 0)
-        record_receiver<U>(p, p.trace_slot, x, y, ux, uy, vx, vy);
+      if ((kind & kTileRec) && ph.slot_a >= 0)
+        record_receiver<U>(p, ph.slot_a, x, y, ux, uy, vx, vy);
     }
   }
   __syncthreads();
@@ -319,7 +348,7 @@ __device__ __noinline__ void step2_featured(const StepParams &p, int x0, int y0,
   C jx, jy, fs[9];
   if (src) {
     C Fx, Fy, Sx, Sy;
-    body_force_cell<C>(p, x, y, p.n + 1, Fx, Fy);
+    body_force_cell<C>(p, x, y, ph.n + 1, Fx, Fy);
     Fx *= force_scale<T, C>(p);
     Fy *= force_scale<T, C>(p);
     flux_and_source<C>(M.mx, M.my, C(0), C(0), Fx, Fy, sponge_A<C>(p, x, y), jx, jy, Sx, Sy);
@@ -327,7 +356,7 @@ __device__ __noinline__ void step2_featured(const StepParams &p, int x0, int y0,
   } else {
     bulk_collide<C>(p, M, C(0), C(0), spg, x, y, fs, jx, jy);
   }
-  T *fout = (T *)p.fout + (y * p.frow + x);
+  T *fout = (T *)ph.fout + (y * p.frow + x);
 #pragma unroll
   for (int i = 0; i < 9; ++i) stp<T, C>(fout + i * p.fplane, fs[i], p);
   const U vx = U(mul_rn(jx, irho)), vy = U(mul_rn(jy, irho));
@@ -336,39 +365,28 @@ __device__ __noinline__ void step2_featured(const StepParams &p, int x0, int y0,
   u[c] = ux;
   u[p.plane + c] = uy;
   if (!((M.rho + jx + jy) * C(0) == C(0))) atomicOr(p.err, 1);
-  if ((kind & kTileRec) && p.trace_slot2 >= 0)
-    record_receiver<U>(p, p.trace_slot2, x, y, ux, uy, vx, vy);
+  if ((kind & kTileRec) && ph.slot_b >= 0)
+    record_receiver<U>(p, ph.slot_b, x, y, ux, uy, vx, vy);
 }
 
-// Steps n = p.n and n + 1 from p.fin to p.fout, one block per kF2Cols x
-// kF2Rows tile; blocks of 32 x kF2Warps threads.  p.reverse: visit the
-// tiles in the reverse order (the top tile row still first), as the
-// one-step kernel does on alternate steps.
+// Phase k (steps p.n + 2k and p.n + 2k + 1) of the tile (bx, by), by the
+// 32 x kF2Warps threads of the block (tile: the block's shared-memory
+// window).  Every thread calls it; it holds one block barrier.
 template <class T, class C, class U>
-__global__ void __launch_bounds__(32 * kF2Warps, LBM_STEP2_MIN_BLOCKS)
-    step2_kernel(const StepParams p) {
-#if LBM_PDL
-  asm volatile("griddepcontrol.wait;" ::: "memory");
-  asm volatile("griddepcontrol.launch_dependents;");
-#endif
-  __shared__ T tile[9 * kF2H * kF2W];
-  int bx = blockIdx.x, by = blockIdx.y;
-  if (p.reverse) {
-    if (by > 0) by = gridDim.y - by;
-    bx = gridDim.x - 1 - bx;
-  }
+__device__ __forceinline__ void step2_tile(const StepParams &p, int bx, int by, T *tile, int k) {
+  const Phase2 ph = phase2(p, k);
   const int x0 = bx * kF2Cols, y0 = by * kF2Rows;
-  const int kind = tile_kind(p, x0, y0);
+  const int kind = tile_kind(p, x0, y0, ph.slot_a);
   if (kind & kTileGeneral) {
-    step2_general<T, C, U>(p, x0, y0, tile);
+    step2_general<T, C, U>(p, x0, y0, tile, k);
     return;
   }
   if (kind & kTileSrc) {
-    step2_featured<T, C, U, true>(p, x0, y0, kind, tile);
+    step2_featured<T, C, U, true>(p, x0, y0, kind, tile, k);
     return;
   }
   if (kind) {
-    step2_featured<T, C, U, false>(p, x0, y0, kind, tile);
+    step2_featured<T, C, U, false>(p, x0, y0, kind, tile, k);
     return;
   }
   const int lane = threadIdx.x, w = threadIdx.y;
@@ -377,7 +395,7 @@ __global__ void __launch_bounds__(32 * kF2Warps, LBM_STEP2_MIN_BLOCKS)
   window_cell(lane, w, ex, ey, core);
   const int x = x0 - 1 + ex, y = y0 - 1 + ey;
   // step n on the window: every upstream cell is inside the grid
-  const T *fin = (const T *)p.fin;
+  const T *fin = (const T *)ph.fin;
   C f[9];
   {
     const T *b = fin + (y * p.frow + x);
@@ -389,8 +407,8 @@ __global__ void __launch_bounds__(32 * kF2Warps, LBM_STEP2_MIN_BLOCKS)
   U ux = U(0), uy = U(0);
   C irho = C(0);
   if (core) {
-    ux = u[c];
-    uy = u[p.plane + c];
+    ux = __ldcg(u + c);
+    uy = __ldcg(u + p.plane + c);
     irho = irho_at<T, C>(p, x, y);
   }
   const bool spg = x0 - 1 < p.sp_left || x0 + kF2Cols + 1 > p.nx - p.sp_right ||
@@ -415,12 +433,125 @@ __global__ void __launch_bounds__(32 * kF2Warps, LBM_STEP2_MIN_BLOCKS)
   const Moments<C> M = cell_moments<C>(f);
   C jx, jy, fs[9];
   bulk_collide<C>(p, M, C(0), C(0), spg, x, y, fs, jx, jy);
-  T *fout = (T *)p.fout + (y * p.frow + x);
+  T *fout = (T *)ph.fout + (y * p.frow + x);
 #pragma unroll
   for (int i = 0; i < 9; ++i) stp<T, C>(fout + i * p.fplane, fs[i], p);
   u[c] = ux + U(mul_rn(jx, irho));
   u[p.plane + c] = uy + U(mul_rn(jy, irho));
   if (!((M.rho + jx + jy) * C(0) == C(0))) atomicOr(p.err, 1);
+}
+
+// Steps n = p.n and n + 1 from p.fin to p.fout, one block per kF2Cols x
+// kF2Rows tile; blocks of 32 x kF2Warps threads.  p.reverse: visit the
+// tiles in the reverse order (the top tile row still first), as the
+// one-step kernel does on alternate steps.
+template <class T, class C, class U>
+__global__ void __launch_bounds__(32 * kF2Warps, LBM_STEP2_MIN_BLOCKS)
+    step2_kernel(const StepParams p) {
+#if LBM_PDL
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;");
+#endif
+  __shared__ T tile[9 * kF2H * kF2W];
+  int bx = blockIdx.x, by = blockIdx.y;
+  if (p.reverse) {
+    if (by > 0) by = gridDim.y - by;
+    bx = gridDim.x - 1 - bx;
+  }
+  step2_tile<T, C, U>(p, bx, by, tile, 0);
+}
+
+// ------------------------------------------------------------ persistent form
+//
+// Many two-step phases in one launch, without a grid-wide barrier between
+// them.  The (phase, tile) pairs are numbered phase by phase, tiles row by
+// row, and block b takes pairs b, b + grid, b + 2 grid, ...  Tile t of phase
+// k reads what the tiles around it (itself and its eight neighbours, which
+// hold every cell within two of its cells) wrote in phase k - 1, and
+// overwrites cells those tiles read in phase k - 1; so it waits until each
+// of them has published the completion of phase k - 1 (done[] counts
+// completed phases; release store after the tile's writes, acquire load
+// before its reads).  Every pair it waits for has a smaller number, and the
+// smallest unfinished pair waits for nothing, so with all blocks resident
+// (cooperative launch) the run cannot deadlock.  Each wait is bounded: past
+// wait_cycles, or once another wait has given up, bit 1 of *p.err is set
+// and the block stops.  The tail of one phase overlaps the start of the
+// next, which a launch per phase cannot do.
+
+struct Step2Run {
+  StepParams p;         // phase 0 (p.fin, p.fout, p.n, p.trace_slot, p.trace_end)
+  int nphase;           // phases (two steps each) of this launch
+  int ntx, nty;         // tiles per row and per column
+  unsigned *done;       // per tile: phases completed (zero at launch)
+  long long wait_cycles;
+  int hold_tile;        // for tests: this tile never publishes (-1: none)
+};
+
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned *p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_release_u32(unsigned *p, unsigned v) {
+  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ int ld_volatile_int(const int *p) {
+  return *(const volatile int *)p;
+}
+
+template <class T, class C, class U>
+__global__ void __launch_bounds__(32 * kF2Warps, LBM_STEP2_MIN_BLOCKS)
+    step2_persistent_kernel(const Step2Run r) {
+  __shared__ T tile[9 * kF2H * kF2W];
+  __shared__ int stop;
+  const int t = threadIdx.y * 32 + threadIdx.x;
+  const int ntiles = r.ntx * r.nty;
+  const long long total = (long long)r.nphase * ntiles;
+  for (long long j = blockIdx.x; j < total; j += gridDim.x) {
+    const int k = (int)(j / ntiles), ti = (int)(j - (long long)k * ntiles);
+    const int by = ti / r.ntx, bx = ti - by * r.ntx;
+    if (threadIdx.y == 0) {
+      // lanes 0..8: the tile and its neighbours (wrapped on periodic axes,
+      // absent beyond a wall) must have completed phase k - 1
+      bool gave_up = false;
+      if (threadIdx.x < 9) {
+        int nbx = bx + (int)threadIdx.x % 3 - 1, nby = by + (int)threadIdx.x / 3 - 1;
+        bool need = true;
+        if (nbx < 0 || nbx >= r.ntx) {
+          if (r.p.bc_left == BC_PERIODIC) nbx = (nbx + r.ntx) % r.ntx;
+          else need = false;
+        }
+        if (nby < 0 || nby >= r.nty) {
+          if (r.p.bc_top == BC_PERIODIC) nby = (nby + r.nty) % r.nty;
+          else need = false;
+        }
+        if (need) {
+          const unsigned *d = r.done + (nby * r.ntx + nbx);
+          const long long t0 = clock64();
+          while (ld_acquire_u32(d) < (unsigned)k) {
+            if (clock64() - t0 > r.wait_cycles || (ld_volatile_int(r.p.err) & 2)) {
+              gave_up = true;
+              break;
+            }
+            __nanosleep(64);
+          }
+        }
+      }
+      const bool any = __ballot_sync(0xffffffffu, gave_up) != 0u;
+      if (threadIdx.x == 0) {
+        if (any) atomicOr(r.p.err, 2);
+        stop = any;
+      }
+    }
+    __syncthreads();
+    if (stop) break;
+    step2_tile<T, C, U>(r.p, bx, by, tile, k);
+    __syncthreads();  // every write of the tile is done, and the window is free
+    if (t == 0 && ti != r.hold_tile) {
+      __threadfence();
+      st_release_u32(r.done + ti, (unsigned)k + 1u);
+    }
+  }
 }
 
 // Launch configuration of the two-step kernel for an nx x ny grid.
@@ -433,5 +564,30 @@ inline dim3 step2_block() { return dim3(32, kF2Warps, 1); }
 void launch_step2_f64(const StepParams &p, cudaStream_t s);
 void launch_step2_f32(const StepParams &p, bool u64, cudaStream_t s);
 void launch_step2_16(const StepParams &p, bool bf16, bool u64, cudaStream_t s);
+
+// The persistent form: a cooperative launch of `grid` blocks (at most the
+// resident blocks: the blocks-per-SM value below times the SM count).
+cudaError_t launch_step2_run_f64(const Step2Run &r, int grid, cudaStream_t s);
+cudaError_t launch_step2_run_f32(const Step2Run &r, bool u64, int grid, cudaStream_t s);
+cudaError_t launch_step2_run_16(const Step2Run &r, bool bf16, bool u64, int grid,
+                                cudaStream_t s);
+int step2_run_blocks_f64();
+int step2_run_blocks_f32(bool u64);
+int step2_run_blocks_16(bool bf16, bool u64);
+
+template <class T, class C, class U>
+cudaError_t launch_step2_run_t(const Step2Run &r, int grid, cudaStream_t s) {
+  void *args[] = {(void *)&r};
+  return cudaLaunchCooperativeKernel((const void *)step2_persistent_kernel<T, C, U>, dim3(grid),
+                                     step2_block(), args, 0, s);
+}
+template <class T, class C, class U>
+int step2_persistent_blocks_t() {
+  int n = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, step2_persistent_kernel<T, C, U>,
+                                                    32 * kF2Warps, 0) != cudaSuccess)
+    return 0;
+  return n;
+}
 
 }  // namespace lbm
