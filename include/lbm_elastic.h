@@ -173,14 +173,16 @@ lbm_status lbm_elastic_step(lbm_elastic_t *h, int nsteps);
  * 0, the persistent form of the two-step update: all steps of one
  * lbm_elastic_step call in one cooperative launch, tiles of the next pair of
  * steps starting as soon as their neighbours finish the previous pair (no
- * grid-wide barrier between pairs).  Default: 2 for FP32 and 16-bit
- * storage, 1 for FP64 (whose step is bound by the FP64 arithmetic rather
- * than by memory).  The two-step forms apply where every Lambda is zero
- * and the TMA-staged kernel is off (the persistent one also needs grid
- * sizes that leave no tile one cell wide or high: nx mod 30 != 1,
- * ny mod 14 != 1); elsewhere, and for an odd remainder, steps go one per
- * launch.  All settings give bit-identical states and traces.  Returns
- * LBM_ERR_ARG for any other value. */
+ * grid-wide barrier between pairs).  Until set, the handle chooses: 2 for
+ * FP32, and for 16-bit storage when every Lambda is zero; 1 for FP64
+ * (bound by the FP64 arithmetic rather than by memory) and for 16-bit
+ * storage with the density-gradient force (issue-bound, where the larger
+ * two-step window costs more than the bytes it saves).  Two-step launches
+ * need the TMA-staged kernel off; the persistent form also needs every
+ * Lambda zero and grid sizes that leave no tile one cell wide or high
+ * (nx mod 30 != 1, ny mod 14 != 1), else it takes two-step launches; an
+ * odd remainder takes a one-step launch.  All settings give bit-identical
+ * states and traces.  Returns LBM_ERR_ARG for any other value. */
 lbm_status lbm_elastic_set_steps_per_launch(lbm_elastic_t *h, int steps);
 
 /* Persistent form (steps_per_launch = 0): a tile waits at most wait_cycles

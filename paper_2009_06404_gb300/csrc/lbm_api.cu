@@ -13,6 +13,7 @@
 
 #include "lbm_internal.h"
 #include "step_fused.cuh"
+#include "step2_lam.cuh"
 
 using namespace lbm;
 
@@ -612,12 +613,16 @@ static lbm_status handle_step2(lbm_elastic_t *h) {
   p.reverse = (int)((h->step >> 1) & 1);
   const int tmax = h->cfg.max_steps_traced;
   if (h->nrec > 0 && h->traced < tmax) p.trace_slot = h->traced;
-  if (h->cfg.storage == LBM_F64)
-    launch_step2_f64(p, h->stream);
-  else if (h->cfg.storage == LBM_F32)
-    launch_step2_f32(p, h->cfg.u_fp64 != 0, h->stream);
-  else
-    launch_step2_16(p, h->cfg.storage == LBM_BF16, h->cfg.u_fp64 != 0, h->stream);
+  const bool u64 = h->cfg.u_fp64 != 0, bf16 = h->cfg.storage == LBM_BF16;
+  if (h->lambda_nonzero) {
+    if (h->cfg.storage == LBM_F64) launch_step2_lam_f64(p, h->stream);
+    else if (h->cfg.storage == LBM_F32) launch_step2_lam_f32(p, u64, h->stream);
+    else launch_step2_lam_16(p, bf16, u64, h->stream);
+  } else {
+    if (h->cfg.storage == LBM_F64) launch_step2_f64(p, h->stream);
+    else if (h->cfg.storage == LBM_F32) launch_step2_f32(p, u64, h->stream);
+    else launch_step2_16(p, bf16, u64, h->stream);
+  }
   if (lbm_status st = check_launch(h, "two-step kernel launch")) return st;
   if (p.trace_slot >= 0) h->traced += p.trace_slot + 1 < tmax ? 2 : 1;
   h->cur ^= 1;
@@ -708,8 +713,6 @@ lbm_status lbm_elastic_create(const lbm_elastic_config *cfg, void *d_workspace,
   lbm_elastic_t *h = new (std::nothrow) lbm_elastic();
   if (!h) return fail(nullptr, LBM_ERR_ARG, "out of host memory");
   h->cfg = *cfg;
-  // FP64 steps are bound by the FP64 pipe, not by memory: one per launch
-  h->steps_per_launch = cfg->storage == LBM_F64 ? 1 : 2;
   h->L = L;
   h->ws = (char *)d_workspace;
   h->stream = (cudaStream_t)cuda_stream;
@@ -936,11 +939,19 @@ lbm_status lbm_elastic_reset(lbm_elastic_t *h) {
 lbm_status lbm_elastic_step(lbm_elastic_t *h, int nsteps) {
   if (!h) return LBM_ERR_ARG;
   if (nsteps < 0) return fail(h, LBM_ERR_ARG, "nsteps < 0");
+  int spl = h->steps_per_launch;
+  if (spl < 0) {
+    // FP64 steps are bound by the FP64 pipe, not by memory; with the
+    // density-gradient force the 16-bit step is issue-bound and the larger
+    // two-step window costs more than the bytes it saves
+    const bool b16 = h->cfg.storage == LBM_F16 || h->cfg.storage == LBM_BF16;
+    spl = (h->cfg.storage == LBM_F64 || (b16 && h->lambda_nonzero)) ? 1 : 2;
+  }
   int s = 0;
-  if (h->steps_per_launch == 0 && persistent_ok(h) && nsteps >= 2) {
+  if (spl == 0 && persistent_ok(h) && nsteps >= 2) {
     if (lbm_status st = handle_step2_run(h, nsteps / 2)) return st;
     s = nsteps / 2 * 2;
-  } else if (h->steps_per_launch != 1 && !h->lambda_nonzero && !h->use_tma) {
+  } else if (spl != 1 && !h->use_tma) {
     for (; s + 2 <= nsteps; s += 2)
       if (lbm_status st = handle_step2(h)) return st;
   }

@@ -42,7 +42,7 @@ struct lbm_elastic {
   int traced = 0;
   int nsrc = 0, nrec = 0;
   bool lambda_nonzero = false;
-  int steps_per_launch = 2;    // lbm_elastic_step: 1, 2, or 0 (persistent two-step form)
+  int steps_per_launch = -1;   // lbm_elastic_step: 1, 2, 0 (persistent two-step form), -1 auto
   long long persist_wait = 0;  // persistent form: wait limit in SM cycles (0: default)
   int persist_hold = -1;       // persistent form, tests: tile that never publishes
   int persist_blocks = -1;     // resident blocks per SM of the persistent kernel (-1: unknown)

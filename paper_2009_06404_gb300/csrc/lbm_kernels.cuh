@@ -650,9 +650,11 @@ __device__ __forceinline__ void finish_cell(const StepParams &p, const C *f, C g
   C Gx = C(0), Gy = C(0);
   if (LAM) {
     // elastic force (mu - lambda)/rho0 grad rho = Lambda b^2 grad rho (Eq. 9)
+    // (products rounded on their own: Gx + Fx is never contracted, so cells
+    // near a source round alike on every path)
     const C lb2 = mat_at<C>(p.lam, p.mat_per_cell, xc, yc, p.pitch) * C(1.0 / 3.0);
-    Gx = lb2 * gx;
-    Gy = lb2 * gy;
+    Gx = mul_rn(lb2, gx);
+    Gy = mul_rn(lb2, gy);
   }
   const C A = sponge_A<C>(p, xc, yc);
   C jx, jy, Sx, Sy;
@@ -1040,8 +1042,8 @@ __device__ __forceinline__ void step_block(const StepParams &p, int bx, int by) 
       ((C *)p.grad_out)[p.plane + c] = gy;
     }
     const C lb2 = mat_at<C>(p.lam, p.mat_per_cell, x, y, p.pitch) * C(1.0 / 3.0);
-    Gx = lb2 * gx;
-    Gy = lb2 * gy;
+    Gx = mul_rn(lb2, gx);
+    Gy = mul_rn(lb2, gy);
   }
   C jx, jy, fs[9];
   const bool spg = x0 < p.sp_left || x0 + 32 > p.nx - p.sp_right || y0 < p.sp_top ||
@@ -1179,10 +1181,10 @@ __device__ __forceinline__ void step_block_pair(const StepParams &p, int bx, int
     }
     la *= C(1.0 / 3.0);
     lb *= C(1.0 / 3.0);
-    Gxa = la * gxa;
-    Gya = la * gya;
-    Gxb = lb * gxb;
-    Gyb = lb * gyb;
+    Gxa = mul_rn(la, gxa);
+    Gya = mul_rn(la, gya);
+    Gxb = mul_rn(lb, gxb);
+    Gyb = mul_rn(lb, gyb);
   }
   const bool spg = x0 < p.sp_left || x0 + 64 > p.nx - p.sp_right || y0 < p.sp_top ||
                    y0 + R > p.ny - p.sp_bottom;

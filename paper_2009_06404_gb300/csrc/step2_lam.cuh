@@ -1,0 +1,351 @@
+// Two steps per launch with the density-gradient force (some Lambda != 0).
+//
+// The force of a cell needs the streamed densities of its four neighbours
+// (Eq. 10), so each step reaches one cell further than without it.  A block
+// owns a 28 x kL2Rows tile and computes:
+//   step n on W2 = the tile widened by two cells (32 x (kL2Rows + 4), one
+//     cell per thread), from the streamed densities of W3 = the tile widened
+//     by three cells (W2's own plus a one-cell ring pulled from HBM);
+//   its post-collision populations on W2 into shared memory;
+//   the streamed densities of step n + 1 on W1 = the tile widened by one cell
+//     (pulled from the shared W2 window), then step n + 1 of the tile cells.
+// Per two steps the populations cross HBM once each way; every cell update
+// uses the one-step arithmetic (the plain sums f_0 + ... + f_8 for every
+// density that enters a gradient, the same wall ghosts), so results are
+// bit-identical to one step per launch.
+#pragma once
+
+#include "step_fused.cuh"
+
+namespace lbm {
+
+constexpr int kL2Cols = 28;             // columns of a tile
+constexpr int kL2Rows = 12;             // rows of a tile
+constexpr int kL2W = kL2Cols + 4;       // W2: 32 columns, one warp per row
+constexpr int kL2H = kL2Rows + 4;       // W2 rows = warps per block
+constexpr int kL2RW = kL2W + 2;         // W3 columns (density buffer)
+constexpr int kL2RH = kL2H + 2;         // W3 rows
+constexpr int kL2Ring = 2 * kL2RW + 2 * kL2H;  // W3 cells outside W2
+static_assert(kL2W == 32, "a W2 row is one warp");
+static_assert(kL2Ring <= 32 * kL2H, "one ring cell per thread at most");
+
+#ifndef LBM_STEP2L_MIN_BLOCKS
+#define LBM_STEP2L_MIN_BLOCKS (2048 / (32 * kL2H))
+#endif
+
+// Ring cell t (0 <= t < kL2Ring) of W3 in W3 coordinates: the top and bottom
+// rows, then the left and right columns beside W2's rows.
+__device__ __forceinline__ void lam_ring_cell(int t, int &hx, int &hy) {
+  if (t < 2 * kL2RW) {
+    hx = t % kL2RW;
+    hy = t < kL2RW ? 0 : kL2RH - 1;
+  } else {
+    const int q = t - 2 * kL2RW;
+    hx = (q & 1) ? kL2RW - 1 : 0;
+    hy = 1 + (q >> 1);
+  }
+}
+
+// Whether a tile at (x0, y0) takes the general rules: an edge or seam of the
+// grid within four cells (W3's pulls), a source reaching W2, or a receiver
+// among the tile's cells when recording.  Warp-wide.
+__device__ __forceinline__ bool lam_tile_special(const StepParams &p, int x0, int y0,
+                                                 int slot_a) {
+  constexpr int W = kL2Cols, H = kL2Rows;
+  if (x0 < 4 || x0 + W > p.nx - 4 || y0 < 4 || y0 + H > p.ny - 4) return true;
+  const bool near_src = p.nsrc > 0 && x0 - 2 <= p.src_x1 && x0 + W + 1 >= p.src_x0 &&
+                        y0 - 2 <= p.src_y1 && y0 + H + 1 >= p.src_y0;
+  const bool near_rec = slot_a >= 0 && x0 <= p.rec_x1 && x0 + W - 1 >= p.rec_x0 &&
+                        y0 <= p.rec_y1 && y0 + H - 1 >= p.rec_y0;
+  if (!near_src && !near_rec) return false;
+  if (near_src && p.nsrc > 32) return true;
+  const int lane = threadIdx.x & 31;
+  bool hit = false;
+  if (near_src && lane < p.nsrc) {
+    // W2 cells lie within W/2 + 2 columns and H/2 + 2 rows of the centre
+    const SourceDev &q = p.src[lane];
+    int dx = x0 + W / 2 - q.xc, dy = y0 + H / 2 - q.yc;
+    if (p.bc_left == BC_PERIODIC) {
+      if (dx > p.nx / 2) dx -= p.nx;
+      else if (dx < -(p.nx / 2)) dx += p.nx;
+    }
+    if (p.bc_top == BC_PERIODIC) {
+      if (dy > p.ny / 2) dy -= p.ny;
+      else if (dy < -(p.ny / 2)) dy += p.ny;
+    }
+    hit = abs(dx) <= q.rb + W / 2 + 3 && abs(dy) <= q.rb + H / 2 + 3;
+  }
+  if (near_rec) {
+    const int tx0 = x0 / kRecTileX, tx1 = min((x0 + W - 1) / kRecTileX, p.rec_tiles_x - 1);
+    const int ty0 = y0 / kRecTileY, ty1 = min((y0 + H - 1) / kRecTileY, (p.ny - 1) / kRecTileY);
+    const int nty = ty1 - ty0 + 1;
+    for (int j = lane; j < (tx1 - tx0 + 1) * nty; j += 32) {
+      const int t = (ty0 + j % nty) * p.rec_tiles_x + tx0 + j / nty;
+      hit |= p.rec_tile_ptr[t + 1] > p.rec_tile_ptr[t];
+    }
+  }
+  return __ballot_sync(0xffffffffu, hit) != 0u;
+}
+
+// The W2 window in shared memory, [9][kL2H][kL2W]; element (0, 0) is grid
+// cell (ox, oy) = (x0 - 2, y0 - 2); periodic images at unwrapped
+// coordinates.
+template <class T>
+struct LamTilePops {
+  const T *f;
+  int ox, oy;
+  static constexpr bool kWrap = false;
+  __device__ __forceinline__ const T *at(int i, int x, int y) const {
+    return f + ((i * kL2H + (y - oy)) * kL2W + (x - ox));
+  }
+  template <class C>
+  __device__ __forceinline__ C load(int i, int x, int y) const {
+    return ld<T, C>(at(i, x, y));
+  }
+};
+
+template <class T, class C>
+__device__ __noinline__ C pull_general_lam_tile(const StepParams &p, const T *tile, int ox, int oy,
+                                                int i, int x, int y) {
+  return pull_general_a<T, C>(p, LamTilePops<T>{tile, ox, oy}, i, x, y);
+}
+
+// The plain bulk tile: no edge or seam within four cells, no source, no
+// receiver.  Every thread calls it (three block barriers).
+template <class T, class C, class U>
+__device__ __forceinline__ void lam_bulk(const StepParams &p, const Phase2 &ph, int x0, int y0,
+                                         T *tile, C (*rho_s)[kL2RW]) {
+  const int lane = threadIdx.x, w = threadIdx.y, t = w * 32 + lane;
+  const int x = x0 - 2 + lane, y = y0 - 2 + w;  // this thread's W2 cell
+  const bool w1 = lane >= 1 && lane <= kL2W - 2 && w >= 1 && w <= kL2H - 2;
+  const bool core = lane >= 2 && lane <= kL2W - 3 && w >= 2 && w <= kL2H - 3;
+  const T *fin = (const T *)ph.fin;
+  C f[9];
+  {
+    const T *b = fin + (y * p.frow + x);
+#pragma unroll
+    for (int i = 0; i < 9; ++i) f[i] = ldp<T, C>(b + (i * p.fplane - cyd(i) * p.frow - cxd(i)), p);
+  }
+  // the ring of W3 around W2, pulled together with the cells' own
+  int hx = 0, hy = 0;
+  C hf[9];
+  if (t < kL2Ring) {
+    lam_ring_cell(t, hx, hy);
+    const T *b = fin + ((y0 - 3 + hy) * p.frow + (x0 - 3 + hx));
+#pragma unroll
+    for (int i = 0; i < 9; ++i)
+      hf[i] = ldp<T, C>(b + (i * p.fplane - cyd(i) * p.frow - cxd(i)), p);
+  }
+  U *u = (U *)p.u;
+  const int c = y * p.pitch + x;
+  U ux = U(0), uy = U(0);
+  C irho = C(0);
+  if (core) {
+    ux = __ldcg(u + c);
+    uy = __ldcg(u + p.plane + c);
+    irho = irho_at<T, C>(p, x, y);
+  }
+  // streamed densities of step n on W3 (the plain sums, as on every path)
+  rho_s[w + 1][lane + 1] = f[0] + f[1] + f[2] + f[3] + f[4] + f[5] + f[6] + f[7] + f[8];
+  if (t < kL2Ring) {
+    C r = C(0);
+#pragma unroll
+    for (int i = 0; i < 9; ++i) r += hf[i];
+    rho_s[hy][hx] = r;
+  }
+  __syncthreads();
+  const bool spg = x0 - 2 < p.sp_left || x0 + kL2Cols + 2 > p.nx - p.sp_right ||
+                   y0 - 2 < p.sp_top || y0 + kL2Rows + 2 > p.ny - p.sp_bottom;
+  const C lb2 = mat_at<C>(p.lam, p.mat_per_cell, x, y, p.pitch) * C(1.0 / 3.0);
+  {
+    // step n on W2: elastic force Lambda b^2 grad rho (Eqs. 9-10)
+    const C gx = C(0.5) * (rho_s[w + 1][lane + 2] - rho_s[w + 1][lane]);
+    const C gy = C(0.5) * (rho_s[w + 2][lane + 1] - rho_s[w][lane + 1]);
+    const Moments<C> M = cell_moments<C>(f);
+    C jx, jy, fs[9];
+    bulk_collide<C>(p, M, mul_rn(lb2, gx), mul_rn(lb2, gy), spg, x, y, fs, jx, jy);
+#pragma unroll
+    for (int i = 0; i < 9; ++i) st<T, C>(tile + ((i * kL2H + w) * kL2W + lane), fs[i]);
+    if (core) {
+      ux += U(mul_rn(jx, irho));
+      uy += U(mul_rn(jy, irho));
+    }
+  }
+  __syncthreads();
+  // streamed densities of step n + 1 on W1, pulled from the window
+  if (w1) {
+#pragma unroll
+    for (int i = 0; i < 9; ++i)
+      f[i] = ld<T, C>(tile + ((i * kL2H + w - cyd(i)) * kL2W + lane - cxd(i)));
+    rho_s[w + 1][lane + 1] = f[0] + f[1] + f[2] + f[3] + f[4] + f[5] + f[6] + f[7] + f[8];
+  }
+  __syncthreads();
+  if (!core) return;
+  // step n + 1 of the tile cell
+  const C gx = C(0.5) * (rho_s[w + 1][lane + 2] - rho_s[w + 1][lane]);
+  const C gy = C(0.5) * (rho_s[w + 2][lane + 1] - rho_s[w][lane + 1]);
+  const Moments<C> M = cell_moments<C>(f);
+  C jx, jy, fs[9];
+  bulk_collide<C>(p, M, mul_rn(lb2, gx), mul_rn(lb2, gy), spg, x, y, fs, jx, jy);
+  T *fout = (T *)ph.fout + (y * p.frow + x);
+#pragma unroll
+  for (int i = 0; i < 9; ++i) stp<T, C>(fout + i * p.fplane, fs[i], p);
+  u[c] = ux + U(mul_rn(jx, irho));
+  u[p.plane + c] = uy + U(mul_rn(jy, irho));
+  if (!((M.rho + jx + jy) * C(0) == C(0))) atomicOr(p.err, 1);
+}
+
+// Tiles near an edge or seam, a source or receivers: every cell at its
+// wrapped coordinate, cells beyond a non-periodic edge skipped (density 0,
+// as rho_wrapped gives; the wall ghosts replace it), the wall rules for the
+// pulls (from HBM in step n, from the window in step n + 1), the body force
+// per cell and the receivers.  Out of line; every thread calls it.
+template <class T, class C, class U>
+__device__ __noinline__ void lam_general(const StepParams &p, const Phase2 &ph, int x0, int y0,
+                                         T *tile, C (*rho_s)[kL2RW]) {
+  const int lane = threadIdx.x, w = threadIdx.y, t = w * 32 + lane;
+  const int x = x0 - 2 + lane, y = y0 - 2 + w;  // W2 cell, unwrapped
+  int wx = x, wy = y;
+  bool valid = true;
+  if (x < 0 || x >= p.nx) {
+    if (p.bc_left == BC_PERIODIC) wx = ((x % p.nx) + p.nx) % p.nx;
+    else valid = false;
+  }
+  if (y < 0 || y >= p.ny) {
+    if (p.bc_top == BC_PERIODIC) wy = ((y % p.ny) + p.ny) % p.ny;
+    else valid = false;
+  }
+  const bool w1 = lane >= 1 && lane <= kL2W - 2 && w >= 1 && w <= kL2H - 2;
+  const bool core = lane >= 2 && lane <= kL2W - 3 && w >= 2 && w <= kL2H - 3;
+  const bool active = core && x < p.nx && y < p.ny;
+  const C om = par<C>(p.omega, p.omega_f), fc = par<C>(p.fcoef, p.fcoef_f);
+  const T *fin = (const T *)ph.fin;
+  C f[9];
+  C rho = C(0);
+  if (valid) {
+    gather<T, C>(p, fin, wx, wy, f);
+    rho = f[0] + f[1] + f[2] + f[3] + f[4] + f[5] + f[6] + f[7] + f[8];
+  }
+  rho_s[w + 1][lane + 1] = rho;
+  if (t < kL2Ring) {
+    int hx, hy;
+    lam_ring_cell(t, hx, hy);
+    rho_s[hy][hx] = rho_wrapped<T, C>(p, fin, x0 - 3 + hx, y0 - 3 + hy);
+  }
+  __syncthreads();
+  U *u = (U *)p.u;
+  const int c = y * p.pitch + x;
+  U ux = U(0), uy = U(0);
+  C irho = C(0);
+  if (valid) {
+    // step n on W2
+    C rxm = rho_s[w + 1][lane], rxp = rho_s[w + 1][lane + 2];
+    C rym = rho_s[w][lane + 1], ryp = rho_s[w + 2][lane + 1];
+    wall_ghosts<C>(p, wx == 0, wx == p.nx - 1, p.bc_left, p.bc_right, rho, rxm, rxp);
+    wall_ghosts<C>(p, wy == 0, wy == p.ny - 1, p.bc_top, p.bc_bottom, rho, rym, ryp);
+    const C gx = C(0.5) * (rxp - rxm), gy = C(0.5) * (ryp - rym);
+    const C lb2 = mat_at<C>(p.lam, p.mat_per_cell, wx, wy, p.pitch) * C(1.0 / 3.0);
+    C Fx, Fy;
+    body_force_cell<C>(p, wx, wy, ph.n, Fx, Fy);
+    Fx *= force_scale<T, C>(p);
+    Fy *= force_scale<T, C>(p);
+    const Moments<C> M = cell_moments<C>(f);
+    C jx, jy, Sx, Sy, fs[9];
+    flux_and_source<C>(M.mx, M.my, mul_rn(lb2, gx), mul_rn(lb2, gy), Fx, Fy,
+                       sponge_A<C>(p, wx, wy), jx, jy, Sx, Sy);
+    collide_cell<C>(M, jx, jy, Sx, Sy, om, fc, fs);
+#pragma unroll
+    for (int i = 0; i < 9; ++i) st<T, C>(tile + ((i * kL2H + w) * kL2W + lane), fs[i]);
+    if (active) {
+      irho = irho_at<T, C>(p, x, y);
+      const U vx = U(mul_rn(jx, irho)), vy = U(mul_rn(jy, irho));
+      ux = __ldcg(u + c) + vx;
+      uy = __ldcg(u + p.plane + c) + vy;
+      if (ph.slot_a >= 0) record_receiver<U>(p, ph.slot_a, x, y, ux, uy, vx, vy);
+    }
+  }
+  __syncthreads();
+  // streamed densities of step n + 1 on W1 (0 beyond a non-periodic edge)
+  if (w1) {
+    rho = C(0);
+    if (valid) {
+      if (wx >= 1 && wx < p.nx - 1 && wy >= 1 && wy < p.ny - 1) {
+#pragma unroll
+        for (int i = 0; i < 9; ++i)
+          f[i] = ld<T, C>(tile + ((i * kL2H + w - cyd(i)) * kL2W + lane - cxd(i)));
+      } else {
+#pragma unroll
+        for (int i = 0; i < 9; ++i)
+          f[i] = pull_general_lam_tile<T, C>(p, tile, x0 - 2, y0 - 2, i, x, y);
+      }
+      rho = f[0] + f[1] + f[2] + f[3] + f[4] + f[5] + f[6] + f[7] + f[8];
+    }
+    rho_s[w + 1][lane + 1] = rho;
+  }
+  __syncthreads();
+  if (!active) return;
+  // step n + 1 of the tile cell (x, y)
+  C rxm = rho_s[w + 1][lane], rxp = rho_s[w + 1][lane + 2];
+  C rym = rho_s[w][lane + 1], ryp = rho_s[w + 2][lane + 1];
+  wall_ghosts<C>(p, x == 0, x == p.nx - 1, p.bc_left, p.bc_right, rho, rxm, rxp);
+  wall_ghosts<C>(p, y == 0, y == p.ny - 1, p.bc_top, p.bc_bottom, rho, rym, ryp);
+  const C gx = C(0.5) * (rxp - rxm), gy = C(0.5) * (ryp - rym);
+  const C lb2 = mat_at<C>(p.lam, p.mat_per_cell, x, y, p.pitch) * C(1.0 / 3.0);
+  C Fx, Fy;
+  body_force_cell<C>(p, x, y, ph.n + 1, Fx, Fy);
+  Fx *= force_scale<T, C>(p);
+  Fy *= force_scale<T, C>(p);
+  const Moments<C> M = cell_moments<C>(f);
+  C jx, jy, Sx, Sy, fs[9];
+  flux_and_source<C>(M.mx, M.my, mul_rn(lb2, gx), mul_rn(lb2, gy), Fx, Fy, sponge_A<C>(p, x, y),
+                     jx, jy, Sx, Sy);
+  collide_cell<C>(M, jx, jy, Sx, Sy, om, fc, fs);
+  T *fout = (T *)ph.fout + (y * p.frow + x);
+#pragma unroll
+  for (int i = 0; i < 9; ++i) stp<T, C>(fout + i * p.fplane, fs[i], p);
+  const U vx = U(mul_rn(jx, irho)), vy = U(mul_rn(jy, irho));
+  ux += vx;
+  uy += vy;
+  u[c] = ux;
+  u[p.plane + c] = uy;
+  if (!((M.rho + jx + jy) * C(0) == C(0))) atomicOr(p.err, 1);
+  if (ph.slot_b >= 0) record_receiver<U>(p, ph.slot_b, x, y, ux, uy, vx, vy);
+}
+
+// Steps n = p.n and n + 1 from p.fin to p.fout with the density-gradient
+// force, one block of 32 x kL2H threads per 28 x kL2Rows tile.  p.reverse:
+// the tiles in reverse order (the top tile row still first).
+template <class T, class C, class U>
+__global__ void __launch_bounds__(32 * kL2H, LBM_STEP2L_MIN_BLOCKS)
+    step2_lam_kernel(const StepParams p) {
+#if LBM_PDL
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;");
+#endif
+  __shared__ T tile[9 * kL2H * kL2W];
+  __shared__ C rho_s[kL2RH][kL2RW];
+  int bx = blockIdx.x, by = blockIdx.y;
+  if (p.reverse) {
+    if (by > 0) by = gridDim.y - by;
+    bx = gridDim.x - 1 - bx;
+  }
+  const Phase2 ph = phase2(p, 0);
+  const int x0 = bx * kL2Cols, y0 = by * kL2Rows;
+  if (lam_tile_special(p, x0, y0, ph.slot_a)) {
+    lam_general<T, C, U>(p, ph, x0, y0, tile, rho_s);
+    return;
+  }
+  lam_bulk<T, C, U>(p, ph, x0, y0, tile, rho_s);
+}
+
+inline dim3 step2_lam_grid(int nx, int ny) {
+  return dim3((nx + kL2Cols - 1) / kL2Cols, (ny + kL2Rows - 1) / kL2Rows, 1);
+}
+inline dim3 step2_lam_block() { return dim3(32, kL2H, 1); }
+
+// Launch entry points, one translation unit per storage type.
+void launch_step2_lam_f64(const StepParams &p, cudaStream_t s);
+void launch_step2_lam_f32(const StepParams &p, bool u64, cudaStream_t s);
+void launch_step2_lam_16(const StepParams &p, bool bf16, bool u64, cudaStream_t s);
+
+}  // namespace lbm

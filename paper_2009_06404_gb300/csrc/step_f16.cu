@@ -2,6 +2,7 @@
 // displacement is accumulated in FP32 or FP64.
 #include "lbm_kernels.cuh"
 #include "step_fused.cuh"
+#include "step2_lam.cuh"
 
 #ifndef LBM_PAIR_16
 #define LBM_PAIR_16 0
@@ -57,6 +58,21 @@ int step2_run_blocks_16(bool bf16, bool u64) {
                : step2_persistent_blocks_t<__nv_bfloat16, float, float>();
   return u64 ? step2_persistent_blocks_t<__half, float, double>()
              : step2_persistent_blocks_t<__half, float, float>();
+}
+
+template <class T, class U>
+static void launch2l(const StepParams &p, cudaStream_t s) {
+  launch_pdl(step2_lam_kernel<T, float, U>, step2_lam_grid(p.nx, p.ny), step2_lam_block(), s, p);
+}
+
+void launch_step2_lam_16(const StepParams &p, bool bf16, bool u64, cudaStream_t s) {
+  if (bf16) {
+    if (u64) launch2l<__nv_bfloat16, double>(p, s);
+    else launch2l<__nv_bfloat16, float>(p, s);
+  } else {
+    if (u64) launch2l<__half, double>(p, s);
+    else launch2l<__half, float>(p, s);
+  }
 }
 
 void launch_step2_16(const StepParams &p, bool bf16, bool u64, cudaStream_t s) {

@@ -2,6 +2,7 @@
 // displacement accumulated in FP32 or FP64.
 #include "lbm_kernels.cuh"
 #include "step_fused.cuh"
+#include "step2_lam.cuh"
 
 #ifndef LBM_PAIR_32
 #define LBM_PAIR_32 0
@@ -42,6 +43,12 @@ cudaError_t launch_step2_run_f32(const Step2Run &r, bool u64, int grid, cudaStre
   return u64 ? launch_step2_run_t<float, float, double>(r, grid, s)
              : launch_step2_run_t<float, float, float>(r, grid, s);
 }
+void launch_step2_lam_f32(const StepParams &p, bool u64, cudaStream_t s) {
+  const dim3 grid = step2_lam_grid(p.nx, p.ny), block = step2_lam_block();
+  if (u64) launch_pdl(step2_lam_kernel<float, float, double>, grid, block, s, p);
+  else launch_pdl(step2_lam_kernel<float, float, float>, grid, block, s, p);
+}
+
 int step2_run_blocks_f32(bool u64) {
   return u64 ? step2_persistent_blocks_t<float, float, double>()
              : step2_persistent_blocks_t<float, float, float>();

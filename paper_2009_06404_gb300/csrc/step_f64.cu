@@ -1,6 +1,7 @@
 // FP64 storage and arithmetic instantiations of the step kernel.
 #include "lbm_kernels.cuh"
 #include "step_fused.cuh"
+#include "step2_lam.cuh"
 
 namespace lbm {
 
@@ -23,5 +24,10 @@ cudaError_t launch_step2_run_f64(const Step2Run &r, int grid, cudaStream_t s) {
   return launch_step2_run_t<double, double, double>(r, grid, s);
 }
 int step2_run_blocks_f64() { return step2_persistent_blocks_t<double, double, double>(); }
+
+void launch_step2_lam_f64(const StepParams &p, cudaStream_t s) {
+  launch_pdl(step2_lam_kernel<double, double, double>, step2_lam_grid(p.nx, p.ny),
+             step2_lam_block(), s, p);
+}
 
 }  // namespace lbm

@@ -261,8 +261,8 @@ __global__ void __launch_bounds__(kTmaThreads, LBM_TMA_MIN_BLOCKS)
         const float lam = p.mat_per_cell ? ((const float *)p.lam)[c] : lam_row;
         // elastic force Lambda b^2 grad rho with the centred difference (Eqs. 9-10)
         const float lb2 = lam * (1.0f / 3.0f);
-        Gx = lb2 * (0.5f * (rr[1] - rr[-1]));
-        Gy = lb2 * (0.5f * (rr[G::kRhoLen] - rr[-G::kRhoLen]));
+        Gx = mul_rn(lb2, 0.5f * (rr[1] - rr[-1]));
+        Gy = mul_rn(lb2, 0.5f * (rr[G::kRhoLen] - rr[-G::kRhoLen]));
       }
       const float A = spg ? sponge_A<float>(p, x, y) : 0.f;
       float jx, jy, Sx, Sy;

@@ -172,23 +172,93 @@ def test_two_step_many_sources_bitwise():
     assert np.abs(outs[0][1]).max() > 0
 
 
-def test_two_step_needs_lambda_zero():
-    """With some Lambda != 0 every step takes its own launch (same results)."""
+def _case_lam(nx, ny, bcname, storage, fs_order=0, per_cell=False, seed=3):
+    """As _case, with a Poisson ratio per row (per cell with per_cell) in
+    [0.15, 0.33]: Lambda != 0, the density-gradient force is on."""
     wl = _wl()
-    w = _case(70, 45, "halfspace_sponges", "f32")
-    lam, mu = wl.lame(np.full(45, 0.3), w.rho0)
-    w = w.with_(lam=lam, mu=mu)
+    w = _case(nx, ny, bcname, storage, fs_order, per_cell, seed)
+    nu = np.random.default_rng(seed + 1).uniform(0.15, 0.33, size=np.shape(w.rho0))
+    lam, mu = wl.lame(nu, w.rho0)
+    return w.with_(lam=lam, mu=mu)
+
+
+@pytest.mark.parametrize("storage,u64,k", STORAGES)
+@pytest.mark.parametrize("bcname", sorted(BCS))
+@pytest.mark.parametrize("nx,ny", [(3, 3), (13, 7), (40, 21), (70, 45), (300, 37)])
+def test_two_step_gradient_force_equals_one_step_bitwise(storage, u64, k, bcname, nx, ny):
+    """With the density-gradient force (step n on the tile widened by two
+    cells, densities on the tile widened by three): seven steps, three
+    two-step launches and one one-step launch, bit for bit."""
+    w = _case_lam(nx, ny, bcname, storage)
+    _, fs1, u1, tr1, l1 = _run(w, 1, u64, k, max_traced=6)
+    _, fs2, u2, tr2, l2 = _run(w, 2, u64, k, max_traced=6)
+    assert (l1, l2) == (7, 4)
+    assert np.array_equal(fs1, fs2)
+    assert np.array_equal(u1, u2)
+    assert np.array_equal(tr1, tr2)
+
+
+@pytest.mark.parametrize("fs_order", [0, 1])
+@pytest.mark.parametrize("bcname", ["halfspace_sponges", "free_box", "free_tb_rigid_lr"])
+def test_two_step_gradient_force_per_cell_bitwise(fs_order, bcname):
+    """Per-cell Lambda, both free-surface extrapolation orders (the wall
+    ghosts of the density gradient), FP64."""
+    w = _case_lam(70, 45, bcname, "f64", fs_order=fs_order, per_cell=True)
+    _, fs1, u1, tr1, _ = _run(w, 1)
+    _, fs2, u2, tr2, _ = _run(w, 2)
+    assert np.array_equal(fs1, fs2) and np.array_equal(u1, u2) and np.array_equal(tr1, tr2)
+
+
+@pytest.mark.parametrize("storage,tol", [("f64", 1e-12), ("f32", 1e-5)])
+@pytest.mark.parametrize("bcname", ["halfspace_sponges", "free_tb_rigid_lr", "periodic"])
+def test_two_step_gradient_force_matches_oracle(storage, tol, bcname):
+    """Six steps with Lambda != 0 (three two-step launches) from a random
+    state equal the oracle's element by element."""
+    w = _case_lam(70, 45, bcname, storage, fs_order=1).with_(nsteps=6)
+    _, fs, u, tr, launches = _run(w, 2)
+    assert launches == 3
+    prob = oracle_problem(w)
+    fs0, u0 = _wl().random_state(w.nx, w.ny, seed=5)
+    st, tro = oracle.run(prob, 6, oracle.State(prob, fs=fs0, u=u0, n=3))
+    assert max_rel(fs, st.fs) <= tol
+    assert max_rel(u, st.u) <= tol
+    assert max_rel(tr, tro) <= tol
+
+
+def test_two_step_gradient_force_layered_run_bitwise():
+    """A layered half-space (Lambda != 0 in every layer) from rest, 300
+    steps with traces, FP32: two-step and one-step launches bit for bit."""
+    w = _wl().layered_halfspace(256, 96, 300, seed=4, sponge=16, nrec=32, storage="f32")
+    res = []
+    for spl in (1, 2):
+        sim = _pkg().from_workload(w, kernel="simple")
+        sim.set_steps_per_launch(spl)
+        sim.step(w.nsteps)
+        res.append((sim.get_state(), sim.read_traces()))
+    (a, ta), (b, tb) = res
+    assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
+    assert np.array_equal(ta, tb)
+    assert rel_l2(ta, np.zeros_like(ta)) > 0
+
+
+def test_persistent_form_needs_lambda_zero():
+    """The persistent form applies to Lambda = 0 only; with the gradient
+    force steps_per_launch = 0 takes two-step launches (same results)."""
+    w = _case_lam(70, 45, "halfspace_sponges", "f32")
     _, fs1, u1, _, l1 = _run(w, 1)
-    _, fs2, u2, _, l2 = _run(w, 2)
-    assert l1 == l2 == 7
-    assert np.array_equal(fs1, fs2) and np.array_equal(u1, u2)
+    _, fs0, u0, _, l0 = _run(w, 0)
+    assert (l1, l0) == (7, 4)
+    assert np.array_equal(fs1, fs0) and np.array_equal(u1, u0)
 
 
 def test_steps_per_launch_argument_and_defaults():
-    """0, 1 and 2 are accepted; FP32 and 16-bit handles default to two steps
-    per launch, FP64 handles to one."""
-    for storage, k, per_launch in (("f32", 0, 2), ("f16", 10, 2), ("f64", 0, 1)):
-        w = _case(13, 7, "periodic", storage)
+    """0, 1 and 2 are accepted; until set, FP32 handles take two steps per
+    launch, 16-bit handles two without and one with the gradient force, FP64
+    handles one."""
+    for storage, k, lam, per_launch in (("f32", 0, False, 2), ("f16", 10, False, 2),
+                                        ("f64", 0, False, 1), ("f32", 0, True, 2),
+                                        ("f16", 10, True, 1), ("bf16", 0, True, 1)):
+        w = (_case_lam if lam else _case)(13, 7, "periodic", storage)
         sim = _pkg().from_workload(w, store_scale_log2=k)
         n0 = sim.kernel_launches
         sim.step(4)
