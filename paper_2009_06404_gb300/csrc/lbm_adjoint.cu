@@ -236,10 +236,19 @@ lbm_status lbm_adjoint_forward(lbm_adjoint_t *a) {
   lbm_elastic_t *h = a->h;
   a->n_start = h->step;
   a->traced_start = h->traced;
-  for (int n = 0; n < a->nsteps; ++n) {
-    if (n % a->K == 0)
-      if (lbm_status st = ckpt_io(a, n / a->K, true)) return st;
-    if (lbm_status st = capture_step(a, n % a->K)) return st;
+  const int last = a->A.nck - 1;  // the segment whose gradients the sweep starts with
+  for (int seg = 0; seg <= last; ++seg) {
+    const int n0 = seg * a->K, n1 = std::min(a->nsteps, n0 + a->K);
+    if (lbm_status st = ckpt_io(a, seg, true)) return st;
+    if (seg < last) {
+      // only checkpoints are kept: the handle's own stepping (two steps per
+      // launch where it applies; the same states bit for bit)
+      if (lbm_status st = lbm_elastic_step(h, n1 - n0))
+        return afail(a, st, std::string("forward steps: ") + h->err);
+    } else {
+      for (int n = n0; n < n1; ++n)
+        if (lbm_status st = capture_step(a, n - n0)) return st;
+    }
   }
   if (lbm_status st = ckpt_io(a, a->A.nck, true)) return st;
   a->forward_done = true;
