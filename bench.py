@@ -473,7 +473,7 @@ def form_batched(torch, pkg, wl, nshots=64, time_steps=50):
     plain()
     plain_ms = _timed(torch, plain)
     b = pkg.Batch(shots)
-    best_us = b.autotune(3)
+    best_us = b.autotune(10)  # 18 candidates x 11 steps
     launch = b.launch
     b.step(time_steps)
     batch_ms = _timed(torch, lambda: b.step(time_steps))
@@ -484,7 +484,7 @@ def form_batched(torch, pkg, wl, nshots=64, time_steps=50):
     out = {"workload": f"{nshots} layered half-space shots, sizes 512^2..2048x1024, "
                        f"{cells} cells, FP32", "time_steps": time_steps,
            "mlups": batch_m, "plain_mlups": plain_m, "speedup_vs_plain": batch_m / plain_m,
-           "launch": {k: launch[k] for k in ("mode", "rows", "order")},
+           "launch": {k: launch[k] for k in ("mode", "rows", "order", "cells_per_thread")},
            "autotune_best_us_per_step": best_us, "kernel_launches": launches,
            "error": "bit-identical to the shots stepped alone (tested)"}
     b.close()

@@ -306,7 +306,8 @@ lbm_status lbm_elastic_moment_sums_noalloc(const void *f9, const void *u2, int s
  * launch for many steps.  The step of every cell is the single-grid step
  * (Sec. 2, Eq. 18, with the boundaries of Sec. 6 and the sources of Sec. 5),
  * so a shot advanced in a batch gives the same result as the shot advanced
- * alone.  Each step is split into tiles of 32 x rows cells of all shots;
+ * alone.  Each step is split into tiles of 32 x rows cells (64 x rows with
+ * two cells per thread) of all shots;
  * how the tiles are launched is the batch's launch configuration, which
  * lbm_batch_autotune chooses by timing the candidates on the batch itself.
  *
@@ -320,7 +321,7 @@ lbm_status lbm_elastic_moment_sums_noalloc(const void *f9, const void *u2, int s
 typedef struct lbm_batch lbm_batch_t;
 
 typedef enum {
-  LBM_BATCH_AUTO = 0,       /* tune on the first lbm_batch_step of >= 64 steps */
+  LBM_BATCH_AUTO = 0,       /* tune on the first lbm_batch_step of >= 96 steps */
   LBM_BATCH_STREAM = 1,     /* one launch per step (programmatic dependent launch) */
   LBM_BATCH_GRAPH = 2,      /* the same launches captured in a CUDA graph   */
   LBM_BATCH_PERSISTENT = 3  /* one cooperative launch for steps_per_launch steps:
@@ -343,6 +344,9 @@ typedef struct {
   int barrier_extra;     /* PERSISTENT, for tests of the time-out: arrivals each
                             barrier waits for beyond the grid size (> 0: every
                             wait runs out).  Normally 0.                        */
+  int cells_per_thread;  /* 1, or 2 with rows = 8: a thread updates two
+                            horizontally adjacent cells with paired loads and
+                            stores (tiles 64 x rows)                          */
 } lbm_batch_launch;
 
 /* Workspace bytes for a batch of these n shots. */
@@ -361,8 +365,8 @@ lbm_status lbm_batch_create(lbm_elastic_t *const *shots, int n, void *d_workspac
 lbm_status lbm_batch_set_launch(lbm_batch_t *b, const lbm_batch_launch *l);
 lbm_status lbm_batch_get_launch(const lbm_batch_t *b, lbm_batch_launch *l);
 
-/* Times each candidate configuration (the three modes x rows 4, 8 x both
- * orders) for 1 + steps_per_trial steps of the batch itself and keeps the
+/* Times each candidate configuration (the three modes x rows 4, 8 x cells
+ * per thread 1, 2 (2 with rows 8) x both orders: 18) for 1 + steps_per_trial steps of the batch itself and keeps the
  * fastest.  This ADVANCES every shot by (1 + steps_per_trial) x the number
  * of candidates steps.  *us_per_step (may be NULL) receives the best time
  * per step in microseconds.  Synchronises the stream. */

@@ -4,23 +4,26 @@
 
 namespace lbm {
 
-cudaError_t batch_launch_16(bool bf16, bool u64, int R, bool persistent, const BatchArgs &a,
-                            int count, int grid, bool pdl, cudaStream_t s) {
+cudaError_t batch_launch_16(bool bf16, bool u64, int R, int cpt, bool persistent,
+                            const BatchArgs &a, int count, int grid, bool pdl, cudaStream_t s) {
   if (bf16) {
     if (u64)
-      return batch_launch_r<__nv_bfloat16, float, double>(R, persistent, a, count, grid, pdl, s);
-    return batch_launch_r<__nv_bfloat16, float, float>(R, persistent, a, count, grid, pdl, s);
+      return batch_launch_r<__nv_bfloat16, float, double>(R, cpt, persistent, a, count, grid,
+                                                          pdl, s);
+    return batch_launch_r<__nv_bfloat16, float, float>(R, cpt, persistent, a, count, grid, pdl,
+                                                       s);
   }
-  if (u64) return batch_launch_r<__half, float, double>(R, persistent, a, count, grid, pdl, s);
-  return batch_launch_r<__half, float, float>(R, persistent, a, count, grid, pdl, s);
+  if (u64)
+    return batch_launch_r<__half, float, double>(R, cpt, persistent, a, count, grid, pdl, s);
+  return batch_launch_r<__half, float, float>(R, cpt, persistent, a, count, grid, pdl, s);
 }
 
-int batch_occupancy_16(bool bf16, bool u64, int R) {
+int batch_occupancy_16(bool bf16, bool u64, int R, int cpt) {
   if (bf16)
-    return u64 ? batch_occupancy_r<__nv_bfloat16, float, double>(R)
-               : batch_occupancy_r<__nv_bfloat16, float, float>(R);
-  return u64 ? batch_occupancy_r<__half, float, double>(R)
-             : batch_occupancy_r<__half, float, float>(R);
+    return u64 ? batch_occupancy_r<__nv_bfloat16, float, double>(R, cpt)
+               : batch_occupancy_r<__nv_bfloat16, float, float>(R, cpt);
+  return u64 ? batch_occupancy_r<__half, float, double>(R, cpt)
+             : batch_occupancy_r<__half, float, float>(R, cpt);
 }
 
 }  // namespace lbm

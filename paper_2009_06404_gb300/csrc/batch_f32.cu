@@ -3,14 +3,15 @@
 
 namespace lbm {
 
-cudaError_t batch_launch_f32(bool u64, int R, bool persistent, const BatchArgs &a, int count,
-                             int grid, bool pdl, cudaStream_t s) {
-  if (u64) return batch_launch_r<float, float, double>(R, persistent, a, count, grid, pdl, s);
-  return batch_launch_r<float, float, float>(R, persistent, a, count, grid, pdl, s);
+cudaError_t batch_launch_f32(bool u64, int R, int cpt, bool persistent, const BatchArgs &a,
+                             int count, int grid, bool pdl, cudaStream_t s) {
+  if (u64) return batch_launch_r<float, float, double>(R, cpt, persistent, a, count, grid, pdl, s);
+  return batch_launch_r<float, float, float>(R, cpt, persistent, a, count, grid, pdl, s);
 }
 
-int batch_occupancy_f32(bool u64, int R) {
-  return u64 ? batch_occupancy_r<float, float, double>(R) : batch_occupancy_r<float, float, float>(R);
+int batch_occupancy_f32(bool u64, int R, int cpt) {
+  return u64 ? batch_occupancy_r<float, float, double>(R, cpt)
+             : batch_occupancy_r<float, float, float>(R, cpt);
 }
 
 __global__ void batch_advance_kernel(BatchHdr *h, int g) { h->kbase += g; }

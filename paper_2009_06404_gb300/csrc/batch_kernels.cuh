@@ -1,7 +1,7 @@
 // Batched step: many independent grids ("shots") advanced together.  The
 // work of one step is a flat list of tiles (shot, block column, block row)
-// of 32 x R cells; each tile runs the same block update as the single-grid
-// kernel, with its shot's parameters staged in shared memory.  Two launch
+// of 32 x R cells (64 x R with two cells per thread); each tile runs the
+// same block update as the single-grid kernel, with its shot's parameters staged in shared memory.  Two launch
 // forms share it: one launch per step over all tiles (stream launches or a
 // CUDA graph), and a persistent cooperative launch that claims tiles from an
 // atomic queue and separates the steps with a grid barrier.
@@ -73,15 +73,26 @@ __device__ __forceinline__ void load_shot(const BatchArgs &a, int s, int k, Step
   __syncthreads();
 }
 
-template <class T, class C, class U, int R>
+// One tile: 32 x R cells, one per thread (CPT 1), or 64 x R cells, two
+// horizontally adjacent cells per thread (CPT 2, paired loads and stores).
+template <class T, class C, class U, int R, int CPT>
 __device__ __forceinline__ void batch_tile(const StepParams &sp, int lam, int bx, int by) {
-  if (lam) step_block<T, C, U, true, 0, R>(sp, bx, by);
-  else step_block<T, C, U, false, 0, R>(sp, bx, by);
+  if constexpr (CPT == 2) {
+    if (lam) step_block_pair<T, C, U, true, R>(sp, bx, by);
+    else step_block_pair<T, C, U, false, R>(sp, bx, by);
+  } else {
+    if (lam) step_block<T, C, U, true, 0, R>(sp, bx, by);
+    else step_block<T, C, U, false, 0, R>(sp, bx, by);
+  }
 }
 
+// Resident blocks per SM the register budget of a tile kind is set for.
+template <int R, int CPT> constexpr int batch_min_blocks() { return CPT == 2 ? 4 : 48 / R; }
+
 // One step (index hdr->kbase + k of this call) over every tile.
-template <class T, class C, class U, int R>
-__global__ void __launch_bounds__(32 * R, 48 / R) batch_step_kernel(const BatchArgs a, int k) {
+template <class T, class C, class U, int R, int CPT>
+__global__ void __launch_bounds__(32 * R, (batch_min_blocks<R, CPT>()))
+    batch_step_kernel(const BatchArgs a, int k) {
 #if LBM_PDL
   asm volatile("griddepcontrol.wait;" ::: "memory");
   asm volatile("griddepcontrol.launch_dependents;");
@@ -90,7 +101,7 @@ __global__ void __launch_bounds__(32 * R, 48 / R) batch_step_kernel(const BatchA
   __shared__ int lam;
   const int4 tl = a.tiles[blockIdx.x];
   load_shot<32 * R>(a, tl.x, k, sp, lam);
-  batch_tile<T, C, U, R>(sp, lam, tl.y, tl.z);
+  batch_tile<T, C, U, R, CPT>(sp, lam, tl.y, tl.z);
 }
 
 __device__ __forceinline__ unsigned long long load_acquire(const unsigned long long *p) {
@@ -105,8 +116,8 @@ __device__ __forceinline__ unsigned long long load_acquire(const unsigned long l
 // step.  The barrier wait is bounded: past barrier_cycles it sets bit 1 of
 // hdr->err and the block returns.  Needs a cooperative launch (all blocks
 // resident).
-template <class T, class C, class U, int R>
-__global__ void __launch_bounds__(32 * R, 48 / R)
+template <class T, class C, class U, int R, int CPT>
+__global__ void __launch_bounds__(32 * R, (batch_min_blocks<R, CPT>()))
     batch_persistent_kernel(const BatchArgs a, int nsteps) {
   __shared__ StepParams sp;
   __shared__ int lam, tile, quit;
@@ -121,7 +132,7 @@ __global__ void __launch_bounds__(32 * R, 48 / R)
       if (ti >= a.ntiles) break;  // the same for the whole block
       const int4 tl = a.tiles[ti];
       load_shot<32 * R>(a, tl.x, k, sp, lam);
-      batch_tile<T, C, U, R>(sp, lam, tl.y, tl.z);
+      batch_tile<T, C, U, R, CPT>(sp, lam, tl.y, tl.z);
       __syncthreads();  // every thread is done with sp before the next claim
     }
     if (t == 0) {
@@ -147,26 +158,26 @@ __global__ void __launch_bounds__(32 * R, 48 / R)
 // Advances hdr->kbase by g (the last node of a captured group of steps).
 __global__ void batch_advance_kernel(BatchHdr *h, int g);
 
-// Launch entry points, one translation unit per storage type.  storage: the
-// lbm_storage value; R: 4 or 8.
-cudaError_t batch_launch_f64(int R, bool persistent, const BatchArgs &a, int count, int grid,
-                             bool pdl, cudaStream_t s);
-cudaError_t batch_launch_f32(bool u64, int R, bool persistent, const BatchArgs &a, int count,
+// Launch entry points, one translation unit per storage type.  R: 4 or 8;
+// cpt: cells per thread, 1 or 2 (2 with R = 8 only).
+cudaError_t batch_launch_f64(int R, int cpt, bool persistent, const BatchArgs &a, int count,
                              int grid, bool pdl, cudaStream_t s);
-cudaError_t batch_launch_16(bool bf16, bool u64, int R, bool persistent, const BatchArgs &a,
-                            int count, int grid, bool pdl, cudaStream_t s);
-int batch_occupancy_f64(int R);
-int batch_occupancy_f32(bool u64, int R);
-int batch_occupancy_16(bool bf16, bool u64, int R);
+cudaError_t batch_launch_f32(bool u64, int R, int cpt, bool persistent, const BatchArgs &a,
+                             int count, int grid, bool pdl, cudaStream_t s);
+cudaError_t batch_launch_16(bool bf16, bool u64, int R, int cpt, bool persistent,
+                            const BatchArgs &a, int count, int grid, bool pdl, cudaStream_t s);
+int batch_occupancy_f64(int R, int cpt);
+int batch_occupancy_f32(bool u64, int R, int cpt);
+int batch_occupancy_16(bool bf16, bool u64, int R, int cpt);
 
 // Launches one form of the batched kernel: persistent (count = steps, grid
 // = resident blocks, cooperative) or one step (count = k, grid = tiles).
-template <class T, class C, class U, int R>
+template <class T, class C, class U, int R, int CPT>
 cudaError_t batch_launch_t(bool persistent, const BatchArgs &a, int count, int grid, bool pdl,
                            cudaStream_t s) {
   if (persistent) {
     void *args[] = {(void *)&a, (void *)&count};
-    return cudaLaunchCooperativeKernel((const void *)batch_persistent_kernel<T, C, U, R>,
+    return cudaLaunchCooperativeKernel((const void *)batch_persistent_kernel<T, C, U, R, CPT>,
                                        dim3(grid), dim3(32, R), args, 0, s);
   }
   cudaLaunchConfig_t cfg = {};
@@ -178,28 +189,30 @@ cudaError_t batch_launch_t(bool persistent, const BatchArgs &a, int count, int g
   attr[0].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = attr;
   cfg.numAttrs = (pdl && LBM_PDL) ? 1 : 0;
-  return cudaLaunchKernelEx(&cfg, batch_step_kernel<T, C, U, R>, a, count);
+  return cudaLaunchKernelEx(&cfg, batch_step_kernel<T, C, U, R, CPT>, a, count);
 }
 
-template <class T, class C, class U, int R>
+template <class T, class C, class U, int R, int CPT>
 int batch_occupancy_t() {
   int n = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, batch_persistent_kernel<T, C, U, R>,
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, batch_persistent_kernel<T, C, U, R, CPT>,
                                                     32 * R, 0) != cudaSuccess)
     return 0;
   return n;
 }
 
 template <class T, class C, class U>
-cudaError_t batch_launch_r(int R, bool persistent, const BatchArgs &a, int count, int grid,
-                           bool pdl, cudaStream_t s) {
-  if (R == 4) return batch_launch_t<T, C, U, 4>(persistent, a, count, grid, pdl, s);
-  return batch_launch_t<T, C, U, 8>(persistent, a, count, grid, pdl, s);
+cudaError_t batch_launch_r(int R, int cpt, bool persistent, const BatchArgs &a, int count,
+                           int grid, bool pdl, cudaStream_t s) {
+  if (cpt == 2) return batch_launch_t<T, C, U, 8, 2>(persistent, a, count, grid, pdl, s);
+  if (R == 4) return batch_launch_t<T, C, U, 4, 1>(persistent, a, count, grid, pdl, s);
+  return batch_launch_t<T, C, U, 8, 1>(persistent, a, count, grid, pdl, s);
 }
 
 template <class T, class C, class U>
-int batch_occupancy_r(int R) {
-  return R == 4 ? batch_occupancy_t<T, C, U, 4>() : batch_occupancy_t<T, C, U, 8>();
+int batch_occupancy_r(int R, int cpt) {
+  if (cpt == 2) return batch_occupancy_t<T, C, U, 8, 2>();
+  return R == 4 ? batch_occupancy_t<T, C, U, 4, 1>() : batch_occupancy_t<T, C, U, 8, 1>();
 }
 
 }  // namespace lbm

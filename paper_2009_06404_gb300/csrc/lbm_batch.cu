@@ -17,7 +17,7 @@ namespace {
 
 constexpr size_t kBatchAlign = 256;
 constexpr long long kDefaultBarrierCycles = 4000000000LL;  // ~2 s at 2 GHz
-constexpr int kAutoMinSteps = 64;
+constexpr int kAutoMinSteps = 96;
 
 size_t up(size_t v) { return (v + kBatchAlign - 1) / kBatchAlign * kBatchAlign; }
 
@@ -63,7 +63,7 @@ struct lbm_batch {
   lbm_batch_launch launch;
   bool tuned = false;
   // tile list on the device
-  int ntiles = 0, tiles_rows = 0, tiles_order = -1;
+  int ntiles = 0, tiles_rows = 0, tiles_order = -1, tiles_cpt = 0;
   // captured graph of graph_steps steps for the current tile list
   cudaGraphExec_t graph = nullptr;
   int graph_steps = 0;
@@ -111,32 +111,34 @@ bool launch_ok(const lbm_batch_launch &l) {
   return l.mode >= LBM_BATCH_AUTO && l.mode <= LBM_BATCH_PERSISTENT &&
          (l.rows == 4 || l.rows == 8) && (l.order == 0 || l.order == 1) && l.graph_steps >= 1 &&
          l.steps_per_launch >= 1 && l.ctas_per_sm >= 0 && l.barrier_cycles >= 0 &&
-         l.barrier_extra >= 0;
+         l.barrier_extra >= 0 &&
+         (l.cells_per_thread == 1 || (l.cells_per_thread == 2 && l.rows == 8));
 }
 
-// Whether tile (x0, y0) of 32 x R cells of shot h is likely to take the
+// Whether tile (x0, y0) of W x R cells of shot h is likely to take the
 // general path (near an edge, a source footprint or a receiver).
-bool tile_is_edge(const lbm_elastic_t *h, int x0, int y0, int R) {
+bool tile_is_edge(const lbm_elastic_t *h, int x0, int y0, int W, int R) {
   const int nx = h->cfg.nx, ny = h->cfg.ny, m = 2;
-  if (x0 < m || x0 + 32 > nx - m || y0 < m || y0 + R > ny - m) return true;
+  if (x0 < m || x0 + W > nx - m || y0 < m || y0 + R > ny - m) return true;
   auto hit = [&](const int *bx) {
-    return bx[1] >= bx[0] && x0 <= bx[1] && x0 + 31 >= bx[0] && y0 <= bx[3] &&
+    return bx[1] >= bx[0] && x0 <= bx[1] && x0 + W - 1 >= bx[0] && y0 <= bx[3] &&
            y0 + R - 1 >= bx[2];
   };
   return (h->nsrc > 0 && hit(h->src_box)) || (h->nrec > 0 && hit(h->rec_box));
 }
 
-lbm_status upload_tiles(lbm_batch_t *b, int R, int order) {
-  if (b->tiles_rows == R && b->tiles_order == order) return LBM_OK;
+lbm_status upload_tiles(lbm_batch_t *b, int R, int order, int cpt) {
+  if (b->tiles_rows == R && b->tiles_order == order && b->tiles_cpt == cpt) return LBM_OK;
+  const int W = 32 * cpt;
   std::vector<int4> &t = b->tile_host;
   t.clear();
   for (int pass = 0; pass < (order == 1 ? 2 : 1); ++pass) {
     for (int s = 0; s < (int)b->shots.size(); ++s) {
       const lbm_elastic_t *h = b->shots[s];
-      const int gx = (h->cfg.nx + 31) / 32, gy = (h->cfg.ny + R - 1) / R;
+      const int gx = (h->cfg.nx + W - 1) / W, gy = (h->cfg.ny + R - 1) / R;
       for (int by = 0; by < gy; ++by)
         for (int bx = 0; bx < gx; ++bx) {
-          if (order == 1 && tile_is_edge(h, bx * 32, by * R, R) != (pass == 0)) continue;
+          if (order == 1 && tile_is_edge(h, bx * W, by * R, W, R) != (pass == 0)) continue;
           t.push_back(make_int4(s, bx, by, 0));
         }
     }
@@ -146,6 +148,7 @@ lbm_status upload_tiles(lbm_batch_t *b, int R, int order) {
                                 cudaMemcpyHostToDevice, b->stream));
   b->tiles_rows = R;
   b->tiles_order = order;
+  b->tiles_cpt = cpt;
   if (b->graph) {
     cudaGraphExecDestroy(b->graph);
     b->graph = nullptr;
@@ -191,17 +194,19 @@ void advance_shots(lbm_batch_t *b, int nsteps) {
 
 cudaError_t launch_form(lbm_batch_t *b, bool persistent, const BatchArgs &a, int count, int grid,
                         bool pdl, cudaStream_t s) {
-  const int R = b->launch.rows;
-  if (b->storage == LBM_F64) return batch_launch_f64(R, persistent, a, count, grid, pdl, s);
-  if (b->storage == LBM_F32) return batch_launch_f32(b->u64, R, persistent, a, count, grid, pdl, s);
-  return batch_launch_16(b->storage == LBM_BF16, b->u64, R, persistent, a, count, grid, pdl, s);
+  const int R = b->launch.rows, cpt = b->launch.cells_per_thread;
+  if (b->storage == LBM_F64) return batch_launch_f64(R, cpt, persistent, a, count, grid, pdl, s);
+  if (b->storage == LBM_F32)
+    return batch_launch_f32(b->u64, R, cpt, persistent, a, count, grid, pdl, s);
+  return batch_launch_16(b->storage == LBM_BF16, b->u64, R, cpt, persistent, a, count, grid, pdl,
+                         s);
 }
 
 int occupancy(lbm_batch_t *b) {
-  const int R = b->launch.rows;
-  if (b->storage == LBM_F64) return batch_occupancy_f64(R);
-  if (b->storage == LBM_F32) return batch_occupancy_f32(b->u64, R);
-  return batch_occupancy_16(b->storage == LBM_BF16, b->u64, R);
+  const int R = b->launch.rows, cpt = b->launch.cells_per_thread;
+  if (b->storage == LBM_F64) return batch_occupancy_f64(R, cpt);
+  if (b->storage == LBM_F32) return batch_occupancy_f32(b->u64, R, cpt);
+  return batch_occupancy_16(b->storage == LBM_BF16, b->u64, R, cpt);
 }
 
 lbm_status counted(lbm_batch_t *b, cudaError_t e, const char *what) {
@@ -302,7 +307,9 @@ lbm_status run_persistent(lbm_batch_t *b, int nsteps) {
 
 lbm_status run(lbm_batch_t *b, int nsteps, int mode) {
   if (nsteps == 0) return LBM_OK;
-  if (lbm_status st = upload_tiles(b, b->launch.rows, b->launch.order)) return st;
+  if (lbm_status st =
+          upload_tiles(b, b->launch.rows, b->launch.order, b->launch.cells_per_thread))
+    return st;
   if (lbm_status st = prepare_call(b)) return st;
   lbm_status st;
   if (mode == LBM_BATCH_STREAM) st = run_stream(b, nsteps);
@@ -316,12 +323,14 @@ lbm_status run(lbm_batch_t *b, int nsteps, int mode) {
 lbm_status tune(lbm_batch_t *b, int trial, double *best_us) {
   const lbm_batch_launch keep = b->launch;
   struct Cand {
-    int mode, rows, order;
+    int mode, rows, order, cpt;
   };
   std::vector<Cand> cands;
   for (int mode : {LBM_BATCH_STREAM, LBM_BATCH_GRAPH, LBM_BATCH_PERSISTENT})
     for (int rows : {8, 4})
-      for (int order : {1, 0}) cands.push_back({mode, rows, order});
+      for (int cpt : {1, 2})
+        if (cpt == 1 || rows == 8)
+          for (int order : {1, 0}) cands.push_back({mode, rows, order, cpt});
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   BATCH_CUDA(b, cudaEventCreate(&e0));
   BATCH_CUDA(b, cudaEventCreate(&e1));
@@ -332,6 +341,7 @@ lbm_status tune(lbm_batch_t *b, int trial, double *best_us) {
     b->launch.mode = c.mode;
     b->launch.rows = c.rows;
     b->launch.order = c.order;
+    b->launch.cells_per_thread = c.cpt;
     b->launch.graph_steps = trial;
     b->launch.steps_per_launch = std::max(keep.steps_per_launch, trial);
     // one untimed step (tile upload, graph capture), then the timed ones
@@ -359,6 +369,7 @@ lbm_status tune(lbm_batch_t *b, int trial, double *best_us) {
   b->launch.mode = win.mode;
   b->launch.rows = win.rows;
   b->launch.order = win.order;
+  b->launch.cells_per_thread = win.cpt;
   b->tuned = true;
   if (best_us) *best_us = best;
   return LBM_OK;
@@ -416,6 +427,7 @@ lbm_status lbm_batch_create(lbm_elastic_t *const *shots, int n, void *d_workspac
   b->launch.ctas_per_sm = 0;
   b->launch.barrier_cycles = 0;
   b->launch.barrier_extra = 0;
+  b->launch.cells_per_thread = 1;
   if (cudaMemsetAsync(d_workspace, 0, sizeof(BatchHdr), b->stream) != cudaSuccess) {
     delete b;
     return bfail(nullptr, LBM_ERR_CUDA, "batch workspace clear failed");
@@ -448,10 +460,10 @@ lbm_status lbm_batch_step(lbm_batch_t *b, int nsteps) {
   if (!b) return LBM_ERR_ARG;
   if (nsteps < 0) return bfail(b, LBM_ERR_ARG, "nsteps < 0");
   if (b->launch.mode == LBM_BATCH_AUTO && !b->tuned) {
-    // 12 candidates x (1 + 3) steps
+    // 18 candidates x (1 + 3) steps
     if (nsteps >= kAutoMinSteps) {
       if (lbm_status st = tune(b, 3, nullptr)) return st;
-      nsteps -= 48;
+      nsteps -= 72;
     } else {
       return run(b, nsteps, LBM_BATCH_GRAPH);
     }

@@ -200,7 +200,7 @@ __device__ __forceinline__ __nv_bfloat162 pack2(float a, float b, __nv_bfloat162
 template <class T, class C>
 __device__ __forceinline__ void ldp2(const T *ptr, const StepParams &, C &a, C &b) {
   using P2 = typename Pair2<T>::type;
-  unpack2(*reinterpret_cast<const P2 *>(ptr), a, b);
+  unpack2(__ldcg(reinterpret_cast<const P2 *>(ptr)), a, b);
 }
 
 template <class T, class C>
@@ -687,7 +687,8 @@ __device__ __forceinline__ void finish_cell(const StepParams &p, const C *f, C g
   for (int i = 0; i < 9; ++i) stp<T, C>(fout + i * p.fplane, fs[i], p);
   U *u = (U *)p.u;
   const U vx = U(mul_rn(jx, irho)), vy = U(mul_rn(jy, irho));
-  const U ux = (UIN ? ux0 : u[c]) + vx, uy = (UIN ? uy0 : u[p.plane + c]) + vy;
+  const U ux = (UIN ? ux0 : __ldcg(u + c)) + vx;
+  const U uy = (UIN ? uy0 : __ldcg(u + p.plane + c)) + vy;
   u[c] = ux;
   u[p.plane + c] = uy;
   // non-finite guard: x * 0 == 0 fails exactly for NaN and +-Inf
@@ -781,7 +782,7 @@ __device__ __noinline__ void general_cell(const StepParams &p, int x, int y, int
   }
   const U *u = (const U *)p.u;
   const int c = yc * p.pitch + xc;
-  const U ux0 = u[c], uy0 = u[p.plane + c];  // before any store
+  const U ux0 = __ldcg(u + c), uy0 = __ldcg(u + p.plane + c);  // before any store
   finish_cell<T, C, U, false, MODE, true>(p, f, C(0), C(0), Fx, Fy, x, y, xc, yc, active, ux0,
                                           uy0);
 }
@@ -1014,7 +1015,7 @@ __device__ __forceinline__ void step_block(const StepParams &p, int bx, int by) 
   }
   const int c = y * p.pitch + x;
   U *u = (U *)p.u;
-  const U ux0 = u[c], uy0 = u[p.plane + c];
+  const U ux0 = __ldcg(u + c), uy0 = __ldcg(u + p.plane + c);
   const C irho = irho_at<T, C>(p, x, y);
   const Moments<C> M = cell_moments<C>(f);
   C Gx = C(0), Gy = C(0);
@@ -1140,8 +1141,8 @@ __device__ __forceinline__ void step_block_pair(const StepParams &p, int bx, int
   const int c = y * p.pitch + xa;
   U *u = (U *)p.u;
   using UP = typename UPair<U>::type;
-  const UP ux0 = *reinterpret_cast<const UP *>(u + c);
-  const UP uy0 = *reinterpret_cast<const UP *>(u + p.plane + c);
+  const UP ux0 = __ldcg(reinterpret_cast<const UP *>(u + c));
+  const UP uy0 = __ldcg(reinterpret_cast<const UP *>(u + p.plane + c));
   const C irha = irho_at<T, C>(p, xa, y), irhb = irho_at<T, C>(p, xa + 1, y);
   const Moments<C> Ma = cell_moments<C>(fa), Mb = cell_moments<C>(fb);
   C Gxa = C(0), Gya = C(0), Gxb = C(0), Gyb = C(0);

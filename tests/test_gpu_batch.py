@@ -84,16 +84,17 @@ def _assert_same(a, b, what):
     assert np.array_equal(ta, tb), f"{what}: traces differ"
 
 
-MODES = [("stream", 8, 0), ("stream", 4, 1), ("graph", 8, 1), ("graph", 4, 0),
-         ("persistent", 8, 1), ("persistent", 4, 0)]
+MODES = [("stream", 8, 0, 1), ("stream", 4, 1, 1), ("graph", 8, 1, 1), ("graph", 4, 0, 1),
+         ("persistent", 8, 1, 1), ("persistent", 4, 0, 1),
+         ("stream", 8, 1, 2), ("graph", 8, 0, 2), ("persistent", 8, 1, 2)]
 
 
 @pytest.mark.parametrize("storage", ["f64", "f32", "f16"])
-@pytest.mark.parametrize("mode,rows,order", MODES)
-def test_batch_equals_shots_alone(storage, mode, rows, order):
-    """Every launch form, tile height and order gives, bit for bit, what each
-    shot gives when stepped alone (the step of a cell does not depend on the
-    tile it is in)."""
+@pytest.mark.parametrize("mode,rows,order,cpt", MODES)
+def test_batch_equals_shots_alone(storage, mode, rows, order, cpt):
+    """Every launch form, tile height, order and cells per thread gives, bit
+    for bit, what each shot gives when stepped alone (the step of a cell does
+    not depend on the tile it is in, nor on the thread that updates it)."""
     ws = _shot_workloads(storage)
     alone = _make(ws, storage)
     for s in alone:
@@ -101,7 +102,9 @@ def test_batch_equals_shots_alone(storage, mode, rows, order):
     ref = [_state(s) for s in alone]
     shots = _make(ws, storage)
     b = _pkg().Batch(shots)
-    b.set_launch(mode=mode, rows=rows, order=order, graph_steps=5, steps_per_launch=7)
+    b.set_launch(mode=mode, rows=rows, order=order, graph_steps=5, steps_per_launch=7,
+                 cells_per_thread=cpt)
+    assert b.launch["cells_per_thread"] == cpt
     b.step(23)
     b.sync()
     for i, s in enumerate(shots):
@@ -151,7 +154,7 @@ def test_batch_matches_oracle():
 
 def test_batch_autotune_advances_and_matches():
     """The autotuner times every candidate on the batch itself: the shots
-    advance by (1 + trial) x 12 steps and still equal shots stepped alone."""
+    advance by (1 + trial) x 18 steps and still equal shots stepped alone."""
     ws = _shot_workloads("f32", nsteps=60)
     shots = _make(ws, "f32")
     b = _pkg().Batch(shots)
@@ -159,8 +162,9 @@ def test_batch_autotune_advances_and_matches():
     b.sync()
     assert us > 0
     assert b.launch["mode"] in ("stream", "graph", "persistent")
+    assert b.launch["cells_per_thread"] in (1, 2)
     n = shots[0].step_index
-    assert n == 36 and all(s.step_index == n for s in shots)
+    assert n == 54 and all(s.step_index == n for s in shots)
     alone = _make(ws, "f32")
     for s in alone:
         s.step(n)
@@ -169,16 +173,16 @@ def test_batch_autotune_advances_and_matches():
 
 
 def test_batch_auto_mode_tunes_on_long_calls():
-    ws = _shot_workloads("f32", nsteps=80)[:2]
+    ws = _shot_workloads("f32", nsteps=110)[:2]
     shots = _make(ws, "f32")
     b = _pkg().Batch(shots)
     assert b.launch["mode"] == "auto"
-    b.step(70)
+    b.step(100)
     b.sync()
-    assert all(s.step_index == 70 for s in shots)
+    assert all(s.step_index == 100 for s in shots)
     alone = _make(ws, "f32")
     for s in alone:
-        s.step(70)
+        s.step(100)
     for i, s in enumerate(shots):
         _assert_same(_state(s), _state(alone[i]), f"shot {i}")
 
@@ -219,6 +223,7 @@ def test_batch_rejects_mixed_storage_and_bad_launch():
         pkg.Batch([a, c])
     assert e.value.status == -1
     b = pkg.Batch([a])
-    for bad in ({"rows": 16}, {"order": 2}, {"graph_steps": 0}, {"steps_per_launch": 0}):
+    for bad in ({"rows": 16}, {"order": 2}, {"graph_steps": 0}, {"steps_per_launch": 0},
+                {"cells_per_thread": 3}, {"cells_per_thread": 2, "rows": 4}):
         with pytest.raises(pkg.LBMError):
             b.set_launch(**bad)

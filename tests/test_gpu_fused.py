@@ -274,6 +274,18 @@ def test_steps_per_launch_argument_and_defaults():
             sim.set_persistent_wait(0, hold_tile=10 ** 6)
 
 
+@pytest.mark.parametrize("nx,ny", [(61, 45), (70, 29)])
+def test_persistent_form_falls_back_on_one_cell_tiles(nx, ny):
+    """Grid sizes that leave a tile one cell wide (nx mod 30 = 1) or high
+    (ny mod 14 = 1) take two-step launches instead of the persistent form,
+    with the same results."""
+    w = _case(nx, ny, "periodic", "f32")
+    _, fs1, u1, tr1, l1 = _run(w, 1)
+    _, fs0, u0, tr0, l0 = _run(w, 0)
+    assert (l1, l0) == (7, 4)
+    assert np.array_equal(fs1, fs0) and np.array_equal(u1, u0) and np.array_equal(tr1, tr0)
+
+
 def test_persistent_wait_times_out_and_recovers():
     """A tile that never publishes its progress makes its neighbours' bounded
     waits run out: the launch stops, the next synchronising call reports the
