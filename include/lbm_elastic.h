@@ -366,8 +366,8 @@ lbm_status lbm_batch_set_launch(lbm_batch_t *b, const lbm_batch_launch *l);
 lbm_status lbm_batch_get_launch(const lbm_batch_t *b, lbm_batch_launch *l);
 
 /* Times each candidate configuration (the three modes x rows 4, 8 x cells
- * per thread 1, 2 (2 with rows 8) x both orders: 18) for 1 + steps_per_trial steps of the batch itself and keeps the
- * fastest.  This ADVANCES every shot by (1 + steps_per_trial) x the number
+ * per thread 1, 2 (2 with rows 8) x both orders: 18) for 1 + steps_per_trial
+ * steps of the batch itself and keeps the fastest.  This ADVANCES every shot by (1 + steps_per_trial) x the number
  * of candidates steps.  *us_per_step (may be NULL) receives the best time
  * per step in microseconds.  Synchronises the stream. */
 lbm_status lbm_batch_autotune(lbm_batch_t *b, int steps_per_trial, double *us_per_step);

@@ -8,6 +8,8 @@ cudaError_t batch_launch_f64(int R, int cpt, bool persistent, const BatchArgs &a
   return batch_launch_r<double, double, double>(R, cpt, persistent, a, count, grid, pdl, s);
 }
 
-int batch_occupancy_f64(int R, int cpt) { return batch_occupancy_r<double, double, double>(R, cpt); }
+int batch_occupancy_f64(int R, int cpt) {
+  return batch_occupancy_r<double, double, double>(R, cpt);
+}
 
 }  // namespace lbm

@@ -1,10 +1,11 @@
 // Batched step: many independent grids ("shots") advanced together.  The
 // work of one step is a flat list of tiles (shot, block column, block row)
 // of 32 x R cells (64 x R with two cells per thread); each tile runs the
-// same block update as the single-grid kernel, with its shot's parameters staged in shared memory.  Two launch
-// forms share it: one launch per step over all tiles (stream launches or a
-// CUDA graph), and a persistent cooperative launch that claims tiles from an
-// atomic queue and separates the steps with a grid barrier.
+// same block update as the single-grid kernel, with its shot's parameters
+// staged in shared memory.  Two launch forms share it: one launch per step
+// over all tiles (stream launches or a CUDA graph), and a persistent
+// cooperative launch that claims tiles from an atomic queue and separates
+// the steps with a grid barrier.
 #pragma once
 
 #include "lbm_kernels.cuh"
