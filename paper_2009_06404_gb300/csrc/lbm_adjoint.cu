@@ -9,6 +9,7 @@
 
 #include "adjoint_kernels.cuh"
 #include "lbm_internal.h"
+#include "step2_lam.cuh"
 
 using namespace lbm;
 
@@ -195,6 +196,45 @@ lbm_status capture_step(lbm_adjoint_t *a, int slot) {
   return LBM_OK;
 }
 
+// FP32 states: steps n and n + 1 in one launch of the two-step
+// gradient-force kernel, storing both steps' density gradients into records
+// slot and slot + 1 (the states and records of two capture_step calls, bit
+// for bit).  FP64 states keep one step per launch (FP64-arithmetic bound).
+bool two_step_capture(const lbm_adjoint_t *a) { return !a->f64; }
+
+lbm_status capture_two(lbm_adjoint_t *a, int slot) {
+  lbm_elastic_t *h = a->h;
+  StepParams p = handle_step_params(h);
+  p.reverse = (int)((h->step >> 1) & 1);
+  p.grad_out = grad_slot(a, slot);
+  const int tmax = h->cfg.max_steps_traced;
+  if (h->nrec > 0 && h->traced < tmax) p.trace_slot = h->traced;
+  launch_step2_lam_f32(p, h->cfg.u_fp64 != 0, h->stream);
+  h->launches++;
+  const cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess)
+    return afail(a, LBM_ERR_CUDA, std::string("forward steps: ") + cudaGetErrorString(e));
+  if (p.trace_slot >= 0) h->traced += p.trace_slot + 1 < tmax ? 2 : 1;
+  h->cur ^= 1;
+  h->step += 2;
+  return LBM_OK;
+}
+
+// Steps n0 .. n1 - 1 of a segment, recording their gradients in slots
+// 0 .. n1 - n0 - 1.
+lbm_status capture_segment(lbm_adjoint_t *a, int n0, int n1) {
+  for (int n = n0; n < n1;) {
+    if (two_step_capture(a) && n + 1 < n1) {
+      if (lbm_status st = capture_two(a, n - n0)) return st;
+      n += 2;
+    } else {
+      if (lbm_status st = capture_step(a, n - n0)) return st;
+      n += 1;
+    }
+  }
+  return LBM_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -246,8 +286,7 @@ lbm_status lbm_adjoint_forward(lbm_adjoint_t *a) {
       if (lbm_status st = lbm_elastic_step(h, n1 - n0))
         return afail(a, st, std::string("forward steps: ") + h->err);
     } else {
-      for (int n = n0; n < n1; ++n)
-        if (lbm_status st = capture_step(a, n - n0)) return st;
+      if (lbm_status st = capture_segment(a, n0, n1)) return st;
     }
   }
   if (lbm_status st = ckpt_io(a, a->A.nck, true)) return st;
@@ -287,7 +326,7 @@ lbm_status lbm_adjoint_backward(lbm_adjoint_t *a, const double *d_dtraces) {
       // recompute the segment from its checkpoint, storing its gradients
       if ((st = ckpt_io(a, seg, false))) break;
       h->step = a->n_start + n0;
-      for (int n = n0; n < n1 && !st; ++n) st = capture_step(a, n - n0);
+      st = capture_segment(a, n0, n1);
       a->grads_seg = seg;
     }
     for (int n = n1 - 1; n >= n0 && !st; --n) {

@@ -110,6 +110,17 @@ __device__ __noinline__ C pull_general_lam_tile(const StepParams &p, const T *ti
   return pull_general_a<T, C>(p, LamTilePops<T>{tile, ox, oy}, i, x, y);
 }
 
+// With p.grad_out set (the adjoint's recording runs): the centred density
+// gradient of step n + k (k = 0, 1) of cell index c, into the k-th of two
+// consecutive records of two planes each ([2][2][ny][pitch], compute type),
+// as the one-step kernel stores it.
+template <class C>
+__device__ __forceinline__ void store_grad(const StepParams &p, int k, int c, C gx, C gy) {
+  C *g = (C *)p.grad_out + 2LL * k * p.plane;
+  g[c] = gx;
+  g[p.plane + c] = gy;
+}
+
 // The plain bulk tile: no edge or seam within four cells, no source, no
 // receiver.  Every thread calls it (three block barriers).
 template <class T, class C, class U>
@@ -161,6 +172,7 @@ __device__ __forceinline__ void lam_bulk(const StepParams &p, const Phase2 &ph, 
     // step n on W2: elastic force Lambda b^2 grad rho (Eqs. 9-10)
     const C gx = C(0.5) * (rho_s[w + 1][lane + 2] - rho_s[w + 1][lane]);
     const C gy = C(0.5) * (rho_s[w + 2][lane + 1] - rho_s[w][lane + 1]);
+    if (core && p.grad_out) store_grad<C>(p, 0, c, gx, gy);
     const Moments<C> M = cell_moments<C>(f);
     C jx, jy, fs[9];
     bulk_collide<C>(p, M, mul_rn(lb2, gx), mul_rn(lb2, gy), spg, x, y, fs, jx, jy);
@@ -184,6 +196,7 @@ __device__ __forceinline__ void lam_bulk(const StepParams &p, const Phase2 &ph, 
   // step n + 1 of the tile cell
   const C gx = C(0.5) * (rho_s[w + 1][lane + 2] - rho_s[w + 1][lane]);
   const C gy = C(0.5) * (rho_s[w + 2][lane + 1] - rho_s[w][lane + 1]);
+  if (p.grad_out) store_grad<C>(p, 1, c, gx, gy);
   const Moments<C> M = cell_moments<C>(f);
   C jx, jy, fs[9];
   bulk_collide<C>(p, M, mul_rn(lb2, gx), mul_rn(lb2, gy), spg, x, y, fs, jx, jy);
@@ -244,6 +257,7 @@ __device__ __noinline__ void lam_general(const StepParams &p, const Phase2 &ph, 
     wall_ghosts<C>(p, wx == 0, wx == p.nx - 1, p.bc_left, p.bc_right, rho, rxm, rxp);
     wall_ghosts<C>(p, wy == 0, wy == p.ny - 1, p.bc_top, p.bc_bottom, rho, rym, ryp);
     const C gx = C(0.5) * (rxp - rxm), gy = C(0.5) * (ryp - rym);
+    if (active && p.grad_out) store_grad<C>(p, 0, c, gx, gy);
     const C lb2 = mat_at<C>(p.lam, p.mat_per_cell, wx, wy, p.pitch) * C(1.0 / 3.0);
     C Fx, Fy;
     body_force_cell<C>(p, wx, wy, ph.n, Fx, Fy);
@@ -290,6 +304,7 @@ __device__ __noinline__ void lam_general(const StepParams &p, const Phase2 &ph, 
   wall_ghosts<C>(p, x == 0, x == p.nx - 1, p.bc_left, p.bc_right, rho, rxm, rxp);
   wall_ghosts<C>(p, y == 0, y == p.ny - 1, p.bc_top, p.bc_bottom, rho, rym, ryp);
   const C gx = C(0.5) * (rxp - rxm), gy = C(0.5) * (ryp - rym);
+  if (p.grad_out) store_grad<C>(p, 1, c, gx, gy);
   const C lb2 = mat_at<C>(p.lam, p.mat_per_cell, x, y, p.pitch) * C(1.0 / 3.0);
   C Fx, Fy;
   body_force_cell<C>(p, x, y, ph.n + 1, Fx, Fy);
