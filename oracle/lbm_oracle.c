@@ -47,7 +47,11 @@
  *     tau = 1, 1.009 at tau = 0.55), the constant one none.
  *   - grad(rho) at a wall uses a ghost value: free surface 2 rho_b - rho_in
  *     (fs_order = 1) or rho_b (fs_order = 0), rigid wall rho_b; periodic axes
- *     wrap.
+ *     wrap.  The rigid ghost makes the wall a mirror plane (a field uniform
+ *     along the wall evolves as half of its mirror-extended periodic
+ *     domain); the free-surface ghost makes the force summed over the solid
+ *     equal to the surface term of the divergence theorem with the wall
+ *     density of Eq. 39's order.
  *   - A diagonal link that leaves the domain through both a horizontal and a
  *     vertical wall takes the rule of the horizontal (top/bottom) wall.
  *   - Source: g(x) = exp(-|x - x_s|^2 / (2 sigma^2)) for |x - x_s| <= r_cut,

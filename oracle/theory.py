@@ -63,3 +63,26 @@ def ricker_dt(t: float, f: float, t0: float) -> float:
     s = t - t0
     a = c * s * s
     return (-4.0 * c * s - 2.0 * c * s * (1.0 - 2.0 * a)) * math.exp(-a)
+
+
+def rayleigh_xi_scheme(nu: float) -> float:
+    """xi = (v_R / v_S)^2 of the surface wave that the free-surface rule of
+    Sec. 6.2 supports.
+
+    That rule imposes P_air n = 0 at the wall (Eqs. 37-42: only the
+    tangential stress of P_air is kept).  P is conserved by the collision
+    (Eq. 22) and moves with the equilibrium third moment
+    b^2 (j d + d j + j.d), so to leading order P = -2 mu eps(u) + b^2 rho I
+    with rho = -rho0 div u and mu = rho0 b^2.  P n = 0 on a wall of normal
+    n = e_y therefore reads mu div u + 2 mu d_y u_y = 0 and eps_xy = 0: the
+    traction-free condition with lambda replaced by mu (identical for
+    lambda = mu, nu = 0.25).  Rayleigh's ansatz (potentials decaying as
+    exp(-q y), exp(-s y)) gives the determinant condition
+    (2 - xi)(2 - 3 r xi) = 4 sqrt(1 - xi) sqrt(1 - r xi), r = v_S^2 / v_P^2;
+    it reduces to :func:`rayleigh_xi`'s equation at r = 1/3."""
+    r = 1.0 / vp_over_vs(nu) ** 2
+
+    def g(xi):
+        return (2.0 - xi) * (2.0 - 3.0 * r * xi) - 4.0 * math.sqrt(1.0 - xi) * math.sqrt(1.0 - xi * r)
+
+    return brentq(g, 1e-6, 1.0 - 1e-12, xtol=1e-15)

@@ -13,6 +13,11 @@ import pytest
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 SRC = os.path.join(ROOT, "oracle", "lbm_oracle.c")
 
+# the free-surface branch of the density ghost on a horizontal (y) and on a
+# vertical (x) wall
+_FS1_Y = "if (bc == BC_FREE && p->fs_order == 1)\n      return 2.0 * rho[(size_t)yb"
+_FS1_X = "if (bc == BC_FREE && p->fs_order == 1)\n      return 2.0 * rho[(size_t)y * p->nx + xb]"
+
 MUTANTS = {
     # elastic force with the wrong sign (Eq. 9)
     "lambda_sign": ("Gx = Lambda * bb * gx_rho;", "Gx = -Lambda * bb * gx_rho;"),
@@ -46,6 +51,23 @@ MUTANTS = {
     "min_image": ("if (p->bc_left == BC_PERIODIC) dx -= p->nx * floor(dx / p->nx + 0.5);", ""),
     # sponge depth off by one (absorbing-layer reading)
     "sponge_depth": ("d[0] = p->sp_top - y;", "d[0] = p->sp_top - y + 1;"),
+    # density ghosts of Eq. 10 at walls (reading): rigid wall extrapolated
+    # linearly instead of mirrored, on a horizontal and on a vertical wall
+    "ghost_rigid_linear_y": (_FS1_Y, _FS1_Y.replace("bc == BC_FREE && p->fs_order == 1",
+                                                    "bc != BC_FREE || p->fs_order == 1")),
+    "ghost_rigid_linear_x": (_FS1_X, _FS1_X.replace("bc == BC_FREE && p->fs_order == 1",
+                                                    "bc != BC_FREE || p->fs_order == 1")),
+    # ghost set to zero (rigid wall and constant-order free surface)
+    "ghost_zero_y": ("    return rho[(size_t)yb * p->nx + x];", "    return 0.0;"),
+    "ghost_zero_x": ("    return rho[(size_t)y * p->nx + xb];", "    return 0.0;"),
+    # ghost set to zero (linear-order free surface)
+    "ghost_zero_fs1_y": ("return 2.0 * rho[(size_t)yb * p->nx + x] - rho[(size_t)yin * p->nx + x];",
+                         "return 0.0;"),
+    "ghost_zero_fs1_x": ("return 2.0 * rho[(size_t)y * p->nx + xb] - rho[(size_t)y * p->nx + xin];",
+                         "return 0.0;"),
+    # free-surface ghosts of the two extrapolation orders swapped
+    "ghost_fs_swap_y": (_FS1_Y, _FS1_Y.replace("p->fs_order == 1", "p->fs_order == 0")),
+    "ghost_fs_swap_x": (_FS1_X, _FS1_X.replace("p->fs_order == 1", "p->fs_order == 0")),
 }
 
 
@@ -63,6 +85,7 @@ def test_pins_catch_mutant(name, tmp_path):
     env = dict(os.environ, LBM_ORACLE_LIB=str(lib))
     r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider",
                         os.path.join(ROOT, "tests", "test_oracle_lattice.py"),
-                        os.path.join(ROOT, "tests", "test_oracle_step.py")],
+                        os.path.join(ROOT, "tests", "test_oracle_step.py"),
+                        os.path.join(ROOT, "tests", "test_oracle_walls.py")],
                        env=env, cwd=ROOT, capture_output=True, text=True, timeout=600)
     assert r.returncode != 0, f"no pin failed for mutant {name}:\n{r.stdout[-2000:]}"
