@@ -101,10 +101,9 @@ typedef struct {
   int max_sources;       /* capacity reserved in the workspace (>= 0)         */
   int max_receivers;     /* capacity reserved in the workspace (>= 0)         */
   int max_steps_traced;  /* receiver samples kept: steps [0, max) after reset */
-  int kernel_variant;    /* step kernel: 0 = default (the faster one measured:
-                          * currently 1), 1 = one thread per cell with direct
-                          * loads, 2 = TMA-staged tiles (FP32 storage only;
-                          * LBM_ERR_UNSUPPORTED otherwise) */
+  int kernel_variant;    /* step kernel: 0 = default, 1 = one thread per cell
+                          * with direct loads (the only variant; 0 selects
+                          * it) */
   int store_scale_log2;  /* 16-bit storage keeps f * 2^k (k in [-60, 60]) so
                           * that the populations' range fits FP16; ignored
                           * for FP32/FP64 */
@@ -177,9 +176,8 @@ lbm_status lbm_elastic_step(lbm_elastic_t *h, int nsteps);
  * FP32, and for 16-bit storage when every Lambda is zero; 1 for FP64
  * (bound by the FP64 arithmetic rather than by memory) and for 16-bit
  * storage with the density-gradient force (issue-bound, where the larger
- * two-step window costs more than the bytes it saves).  Two-step launches
- * need the TMA-staged kernel off; the persistent form also needs every
- * Lambda zero and grid sizes that leave no tile one cell wide or high
+ * two-step window costs more than the bytes it saves).  The persistent
+ * form needs every Lambda zero and grid sizes that leave no tile one cell wide or high
  * (nx mod 30 != 1, ny mod 14 != 1), else it takes two-step launches; an
  * odd remainder takes a one-step launch.  All settings give bit-identical
  * states and traces.  Returns LBM_ERR_ARG for any other value. */
@@ -251,7 +249,9 @@ lbm_status lbm_elastic_sync(lbm_elastic_t *h);
 lbm_status lbm_elastic_destroy(lbm_elastic_t *h);
 
 /* Message of the last failing call on h ("" if none).  Valid until the next
- * call on h.  With h == NULL: the last failure of lbm_elastic_create. */
+ * call on h.  With h == NULL: the last failure, on the calling thread, of a
+ * call made without a handle (lbm_elastic_create,
+ * lbm_elastic_moment_sums_noalloc); each thread keeps its own message. */
 const char *lbm_elastic_last_error(const lbm_elastic_t *h);
 
 /* Static name of a status code. */
@@ -306,10 +306,11 @@ lbm_status lbm_elastic_moment_sums_noalloc(const void *f9, const void *u2, int s
  * launch for many steps.  The step of every cell is the single-grid step
  * (Sec. 2, Eq. 18, with the boundaries of Sec. 6 and the sources of Sec. 5),
  * so a shot advanced in a batch gives the same result as the shot advanced
- * alone.  Each step is split into tiles of 32 x rows cells (64 x rows with
- * two cells per thread) of all shots;
- * how the tiles are launched is the batch's launch configuration, which
- * lbm_batch_autotune chooses by timing the candidates on the batch itself.
+ * alone.  Each step is split into tiles of 32 x rows cells of all shots, or
+ * each pair of steps into the tiles of the two-step kernels (the
+ * intermediate step in shared memory); how the tiles are launched is the
+ * batch's launch configuration, which lbm_batch_autotune chooses by timing
+ * the candidates on the batch itself.
  *
  * Requirements: every shot has the same storage type and u_fp64 setting.
  * The shots must not be stepped or changed by other calls while a batched
@@ -344,9 +345,15 @@ typedef struct {
   int barrier_extra;     /* PERSISTENT, for tests of the time-out: arrivals each
                             barrier waits for beyond the grid size (> 0: every
                             wait runs out).  Normally 0.                        */
-  int cells_per_thread;  /* 1, or 2 with rows = 8: a thread updates two
-                            horizontally adjacent cells with paired loads and
-                            stores (tiles 64 x rows)                          */
+  int steps_per_tile;    /* 1: one time step per launch (PERSISTENT: per grid
+                            barrier) on tiles of 32 x rows cells; 2: two time
+                            steps per launch on the tiles of the two-step
+                            kernels (30 x 14 cells, 28 x 12 with the
+                            density-gradient force; rows unused), the
+                            intermediate populations in shared memory, and an
+                            odd remainder as one one-step launch.  GRAPH's
+                            graph_steps then counts launches; PERSISTENT's
+                            steps_per_launch still counts time steps.        */
 } lbm_batch_launch;
 
 /* Workspace bytes for a batch of these n shots. */
@@ -356,7 +363,7 @@ size_t lbm_batch_workspace_bytes(lbm_elastic_t *const *shots, int n);
  * lbm_batch_workspace_bytes bytes, 256-byte aligned.  cuda_stream: the
  * stream every batched call uses (0 = legacy default).  Errors: LBM_ERR_ARG
  * (null shot, n < 1, mixed storage types), LBM_ERR_WORKSPACE; the message is
- * then in lbm_batch_last_error(NULL). */
+ * then in lbm_batch_last_error(NULL) (kept per calling thread). */
 lbm_status lbm_batch_create(lbm_elastic_t *const *shots, int n, void *d_workspace, size_t bytes,
                             void *cuda_stream, lbm_batch_t **out);
 
@@ -365,11 +372,14 @@ lbm_status lbm_batch_create(lbm_elastic_t *const *shots, int n, void *d_workspac
 lbm_status lbm_batch_set_launch(lbm_batch_t *b, const lbm_batch_launch *l);
 lbm_status lbm_batch_get_launch(const lbm_batch_t *b, lbm_batch_launch *l);
 
-/* Times each candidate configuration (the three modes x rows 4, 8 x cells
- * per thread 1, 2 (2 with rows 8) x both orders: 18) for 1 + steps_per_trial
- * steps of the batch itself and keeps the fastest.  This ADVANCES every shot by (1 + steps_per_trial) x the number
- * of candidates steps.  *us_per_step (may be NULL) receives the best time
- * per step in microseconds.  Synchronises the stream. */
+/* Times each candidate configuration (the three modes x both orders x
+ * {one step per tile with rows 4 or 8, two steps per tile}: 18) on the batch
+ * itself, two untimed steps and then steps_per_trial steps (rounded up to
+ * even) timed, and keeps the fastest.  This ADVANCES every shot by
+ * 18 x (2 + steps_per_trial rounded up to even) steps.  *us_per_step (may
+ * be NULL) receives the best time per step in microseconds.  Synchronises
+ * the stream.  LBM_BATCH_AUTO runs it with steps_per_trial 2 (72 steps) on
+ * the first call of at least 96 steps. */
 lbm_status lbm_batch_autotune(lbm_batch_t *b, int steps_per_trial, double *us_per_step);
 
 /* Advances every shot by nsteps >= 0 steps (asynchronous). */
@@ -420,7 +430,7 @@ size_t lbm_adjoint_workspace_bytes(const lbm_elastic_t *h, int nsteps, int check
 
 /* Errors: LBM_ERR_ARG, LBM_ERR_UNSUPPORTED (F16/BF16 storage, or FP64 u with
  * FP32 populations), LBM_ERR_WORKSPACE (too small or not 256-byte aligned);
- * message in lbm_adjoint_last_error(NULL). */
+ * message in lbm_adjoint_last_error(NULL) (kept per calling thread). */
 lbm_status lbm_adjoint_create(lbm_elastic_t *h, int nsteps, int checkpoint_every,
                               void *d_workspace, size_t bytes, lbm_adjoint_t **out);
 

@@ -23,7 +23,7 @@ STATUS = {0: "LBM_OK", 1: "LBM_WARN_VS_NOT_B", -1: "LBM_ERR_ARG", -2: "LBM_ERR_U
           -6: "LBM_ERR_TIMEOUT", -7: "LBM_ERR_CAPACITY"}
 STORAGE = {"f64": 0, "f32": 1, "f16": 2, "bf16": 3}
 BC = {"periodic": 0, "free": 1, "rigid": 2}
-KERNEL = {"auto": 0, "simple": 1, "tma": 2}
+KERNEL = {"auto": 0, "simple": 1}
 
 #: the exported symbols, as declared in include/lbm_elastic.h
 SYMBOLS = [
@@ -79,7 +79,7 @@ class BatchLaunch(ctypes.Structure):
         ("mode", ctypes.c_int), ("rows", ctypes.c_int), ("order", ctypes.c_int),
         ("graph_steps", ctypes.c_int), ("steps_per_launch", ctypes.c_int),
         ("ctas_per_sm", ctypes.c_int), ("barrier_cycles", ctypes.c_longlong),
-        ("barrier_extra", ctypes.c_int), ("cells_per_thread", ctypes.c_int),
+        ("barrier_extra", ctypes.c_int), ("steps_per_tile", ctypes.c_int),
     ]
 
 
@@ -474,7 +474,7 @@ class Batch:
         return {"mode": inv[l.mode], "rows": l.rows, "order": l.order,
                 "graph_steps": l.graph_steps, "steps_per_launch": l.steps_per_launch,
                 "ctas_per_sm": l.ctas_per_sm, "barrier_cycles": l.barrier_cycles,
-                "barrier_extra": l.barrier_extra, "cells_per_thread": l.cells_per_thread}
+                "barrier_extra": l.barrier_extra, "steps_per_tile": l.steps_per_tile}
 
     def set_launch(self, **kw):
         cur = self.launch
@@ -482,7 +482,7 @@ class Batch:
         l = BatchLaunch(BATCH_MODE[cur["mode"]], int(cur["rows"]), int(cur["order"]),
                         int(cur["graph_steps"]), int(cur["steps_per_launch"]),
                         int(cur["ctas_per_sm"]), int(cur["barrier_cycles"]),
-                        int(cur["barrier_extra"]), int(cur["cells_per_thread"]))
+                        int(cur["barrier_extra"]), int(cur["steps_per_tile"]))
         self._check(self.L.lbm_batch_set_launch(self.h, ctypes.byref(l)))
 
     def autotune(self, steps_per_trial: int = 3) -> float:

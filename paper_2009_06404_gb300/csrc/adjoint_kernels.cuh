@@ -430,6 +430,13 @@ __device__ __forceinline__ C gtot_s(const AdjSmem<C> &S, bool lam_any, int hx, i
 
 template <class C>
 __global__ void __launch_bounds__(kAdjThreads, LBM_ADJ_MIN_BLOCKS) adj_fused_kernel(const AdjParams a) {
+#if LBM_PDL
+  // programmatic dependent launch: wait for the previous kernel (the
+  // adjoint of the step after this one, or the recomputation) to complete,
+  // then let the next adjoint step's blocks be scheduled as SMs free up
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;");
+#endif
   const StepParams &p = a.p;
   __shared__ AdjSmem<C> S;
   const int t = threadIdx.y * 32 + threadIdx.x;
@@ -612,7 +619,16 @@ template <class C>
 cudaError_t adj_step_t(const AdjParams &a, bool fused, cudaStream_t s) {
   const dim3 block(32, 8), grid((a.p.nx + 31) / 32, (a.p.ny + 7) / 8);
   if (fused) {
-    adj_fused_kernel<C><<<dim3(grid.x, (a.p.ny + kAdjTH - 1) / kAdjTH), dim3(32, kAdjTH), 0, s>>>(a);
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid.x, (a.p.ny + kAdjTH - 1) / kAdjTH);
+    cfg.blockDim = dim3(32, kAdjTH);
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = LBM_PDL ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, adj_fused_kernel<C>, a);
   } else {
     adj_local_kernel<C><<<grid, block, 0, s>>>(a);
     if (a.lam_any) adj_div_kernel<C><<<grid, block, 0, s>>>(a);

@@ -4,26 +4,26 @@
 
 namespace lbm {
 
-cudaError_t batch_launch_16(bool bf16, bool u64, int R, int cpt, bool persistent,
+cudaError_t batch_launch_16(bool bf16, bool u64, int R, int tps, bool persistent,
                             const BatchArgs &a, int count, int grid, bool pdl, cudaStream_t s) {
   if (bf16) {
     if (u64)
-      return batch_launch_r<__nv_bfloat16, float, double>(R, cpt, persistent, a, count, grid,
+      return batch_launch_r<__nv_bfloat16, float, double>(R, tps, persistent, a, count, grid,
                                                           pdl, s);
-    return batch_launch_r<__nv_bfloat16, float, float>(R, cpt, persistent, a, count, grid, pdl,
+    return batch_launch_r<__nv_bfloat16, float, float>(R, tps, persistent, a, count, grid, pdl,
                                                        s);
   }
   if (u64)
-    return batch_launch_r<__half, float, double>(R, cpt, persistent, a, count, grid, pdl, s);
-  return batch_launch_r<__half, float, float>(R, cpt, persistent, a, count, grid, pdl, s);
+    return batch_launch_r<__half, float, double>(R, tps, persistent, a, count, grid, pdl, s);
+  return batch_launch_r<__half, float, float>(R, tps, persistent, a, count, grid, pdl, s);
 }
 
-int batch_occupancy_16(bool bf16, bool u64, int R, int cpt) {
+int batch_occupancy_16(bool bf16, bool u64, int R, int tps) {
   if (bf16)
-    return u64 ? batch_occupancy_r<__nv_bfloat16, float, double>(R, cpt)
-               : batch_occupancy_r<__nv_bfloat16, float, float>(R, cpt);
-  return u64 ? batch_occupancy_r<__half, float, double>(R, cpt)
-             : batch_occupancy_r<__half, float, float>(R, cpt);
+    return u64 ? batch_occupancy_r<__nv_bfloat16, float, double>(R, tps)
+               : batch_occupancy_r<__nv_bfloat16, float, float>(R, tps);
+  return u64 ? batch_occupancy_r<__half, float, double>(R, tps)
+             : batch_occupancy_r<__half, float, float>(R, tps);
 }
 
 }  // namespace lbm

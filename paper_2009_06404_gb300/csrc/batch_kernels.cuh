@@ -1,14 +1,18 @@
 // Batched step: many independent grids ("shots") advanced together.  The
-// work of one step is a flat list of tiles (shot, block column, block row)
-// of 32 x R cells (64 x R with two cells per thread); each tile runs the
-// same block update as the single-grid kernel, with its shot's parameters
-// staged in shared memory.  Two launch forms share it: one launch per step
-// over all tiles (stream launches or a CUDA graph), and a persistent
-// cooperative launch that claims tiles from an atomic queue and separates
-// the steps with a grid barrier.
+// work of one launch is a flat list of tiles (shot, block column, block row);
+// each tile runs the same block update as the single-grid kernels, with its
+// shot's parameters staged in shared memory.  Tiles come in two kinds: one
+// time step on 32 x R cells (the one-step block update), or two time steps
+// on the tile of the two-step kernels (30 x 14 cells without the
+// density-gradient force, 28 x 12 with it; the intermediate populations stay
+// in shared memory).  Two launch forms share them: one launch per step (or
+// per two steps) over all tiles, as stream launches or a CUDA graph, and a
+// persistent cooperative launch that claims tiles from an atomic queue and
+// separates the steps with a grid barrier.
 #pragma once
 
 #include "lbm_kernels.cuh"
+#include "step2_lam.cuh"
 
 namespace lbm {
 
@@ -74,25 +78,71 @@ __device__ __forceinline__ void load_shot(const BatchArgs &a, int s, int k, Step
   __syncthreads();
 }
 
-// One tile: 32 x R cells, one per thread (CPT 1), or 64 x R cells, two
-// horizontally adjacent cells per thread (CPT 2, paired loads and stores).
-template <class T, class C, class U, int R, int CPT>
-__device__ __forceinline__ void batch_tile(const StepParams &sp, int lam, int bx, int by) {
-  if constexpr (CPT == 2) {
-    if (lam) step_block_pair<T, C, U, true, R>(sp, bx, by);
-    else step_block_pair<T, C, U, false, R>(sp, bx, by);
-  } else {
-    if (lam) step_block<T, C, U, true, 0, R>(sp, bx, by);
-    else step_block<T, C, U, false, 0, R>(sp, bx, by);
+// Stages the parameters of shot s for the two steps of phase hdr->kbase + k
+// of this call (steps n0 + 2 phase and n0 + 2 phase + 1; one buffer swap per
+// phase) in shared memory (every thread of the block calls it).
+template <int NT>
+__device__ __forceinline__ void load_shot2(const BatchArgs &a, int s, int k, StepParams &sp,
+                                           int &lam) {
+  const int t = threadIdx.y * 32 + threadIdx.x;
+  const int *src = (const int *)&a.shots[s].p;
+  int *dst = (int *)&sp;
+  for (int w = t; w < (int)(sizeof(StepParams) / 4); w += NT) dst[w] = src[w];
+  __syncthreads();
+  if (t == 0) {
+    const BatchShot &b = a.shots[s];
+    const BatchDyn d = a.dyn[s];
+    const long long ph = a.hdr->kbase + k;
+    const int cur = (int)((d.cur0 + ph) & 1);
+    sp.fin = b.f[cur];
+    sp.fout = (void *)b.f[cur ^ 1];
+    sp.n = d.n0 + 2 * ph;
+    const long long slot = d.traced0 + 2 * ph;
+    // phase2() checks each of the two slots against trace_end
+    sp.trace_slot = (sp.nrec > 0 && slot < b.trace_max) ? (int)slot : -1;
+    sp.trace_end = b.trace_max;
+    lam = b.lam;
   }
+  __syncthreads();
+}
+
+// One-step tile: 32 x R cells, one per thread.
+template <class T, class C, class U, int R>
+__device__ __forceinline__ void batch_tile(const StepParams &sp, int lam, int bx, int by) {
+  if (lam) step_block<T, C, U, true, 0, R>(sp, bx, by);
+  else step_block<T, C, U, false, 0, R>(sp, bx, by);
+}
+
+// Two-step tiles: both kinds are blocks of 32 x 16 threads.
+static_assert(kF2Warps == kL2H && kF2W == kL2W && kF2H == kL2H,
+              "the two kinds of two-step tile share one block shape");
+constexpr int kBatch2Threads = 32 * kF2Warps;
+
+// Shared memory of a two-step tile: the window of either kind, and the
+// density buffer of the density-gradient kind behind it.
+template <class T, class C>
+struct Batch2Smem {
+  static constexpr int kWin = 9 * kL2H * kL2W;
+  static constexpr size_t kBytes = kWin * sizeof(T) + sizeof(C) * kL2RH * kL2RW;
+};
+
+template <class T, class C, class U>
+__device__ __forceinline__ void batch_tile2(const StepParams &sp, int lam, int bx, int by,
+                                            char *smem) {
+  T *win = (T *)smem;
+  if (lam)
+    step2_lam_tile<T, C, U>(sp, bx, by, win,
+                            (C(*)[kL2RW])(smem + Batch2Smem<T, C>::kWin * sizeof(T)));
+  else
+    step2_tile<T, C, U>(sp, bx, by, win, 0);
 }
 
 // Resident blocks per SM the register budget of a tile kind is set for.
-template <int R, int CPT> constexpr int batch_min_blocks() { return CPT == 2 ? 4 : 48 / R; }
+template <int R> constexpr int batch_min_blocks() { return 48 / R; }
 
 // One step (index hdr->kbase + k of this call) over every tile.
-template <class T, class C, class U, int R, int CPT>
-__global__ void __launch_bounds__(32 * R, (batch_min_blocks<R, CPT>()))
+template <class T, class C, class U, int R>
+__global__ void __launch_bounds__(32 * R, (batch_min_blocks<R>()))
     batch_step_kernel(const BatchArgs a, int k) {
 #if LBM_PDL
   asm volatile("griddepcontrol.wait;" ::: "memory");
@@ -102,7 +152,23 @@ __global__ void __launch_bounds__(32 * R, (batch_min_blocks<R, CPT>()))
   __shared__ int lam;
   const int4 tl = a.tiles[blockIdx.x];
   load_shot<32 * R>(a, tl.x, k, sp, lam);
-  batch_tile<T, C, U, R, CPT>(sp, lam, tl.y, tl.z);
+  batch_tile<T, C, U, R>(sp, lam, tl.y, tl.z);
+}
+
+// Two steps (phase hdr->kbase + k of this call) over every two-step tile.
+template <class T, class C, class U>
+__global__ void __launch_bounds__(kBatch2Threads, LBM_STEP2_MIN_BLOCKS)
+    batch_step2_kernel(const BatchArgs a, int k) {
+#if LBM_PDL
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;");
+#endif
+  __shared__ StepParams sp;
+  __shared__ int lam;
+  __shared__ __align__(16) char smem[Batch2Smem<T, C>::kBytes];
+  const int4 tl = a.tiles[blockIdx.x];
+  load_shot2<kBatch2Threads>(a, tl.x, k, sp, lam);
+  batch_tile2<T, C, U>(sp, lam, tl.y, tl.z, smem);
 }
 
 __device__ __forceinline__ unsigned long long load_acquire(const unsigned long long *p) {
@@ -111,17 +177,44 @@ __device__ __forceinline__ unsigned long long load_acquire(const unsigned long l
   return v;
 }
 
-// nsteps steps in one launch.  Blocks claim tiles from hdr->queue (each
-// block makes exactly one failing claim per step, so the claims of step k
-// start at k (ntiles + gridDim.x)) and meet at a grid barrier after each
-// step.  The barrier wait is bounded: past barrier_cycles it sets bit 1 of
-// hdr->err and the block returns.  Needs a cooperative launch (all blocks
-// resident).
-template <class T, class C, class U, int R, int CPT>
-__global__ void __launch_bounds__(32 * R, (batch_min_blocks<R, CPT>()))
+// Grid barrier k of a persistent launch, by thread 0 of each block: arrive,
+// then wait (bounded by barrier_cycles; past it bit 1 of hdr->err is set and
+// the block is told to quit).  Every thread calls it; it holds one block
+// barrier.  Returns whether the block must quit.
+__device__ __forceinline__ bool batch_grid_barrier(const BatchArgs &a, int k, int *quit) {
+  if (threadIdx.x == 0 && threadIdx.y == 0) {
+    *quit = 0;
+    __threadfence();  // this block's stores before its arrival
+    atomicAdd(&a.hdr->arrive, 1ULL);
+    const unsigned long long target = (unsigned long long)(k + 1) * a.barrier_count;
+    const long long t0 = clock64();
+    while (load_acquire(&a.hdr->arrive) < target) {
+      if (clock64() - t0 > a.barrier_cycles) {
+        atomicOr(&a.hdr->err, 2);
+        *quit = 1;
+        break;
+      }
+    }
+    __threadfence();  // the other blocks' stores before this block's loads
+  }
+  __syncthreads();
+  return *quit != 0;
+}
+
+// nsteps steps (TPS = 1) or two-step phases (TPS = 2) in one launch.  Blocks
+// claim tiles from hdr->queue (each block makes exactly one failing claim
+// per step, so the claims of step k start at k (ntiles + gridDim.x)) and meet
+// at a grid barrier after each step.  The barrier wait is bounded: past
+// barrier_cycles it sets bit 1 of hdr->err and the block returns.  Needs a
+// cooperative launch (all blocks resident).
+template <class T, class C, class U, int R, int TPS>
+__global__ void __launch_bounds__(TPS == 2 ? kBatch2Threads : 32 * R,
+                                  TPS == 2 ? LBM_STEP2_MIN_BLOCKS : batch_min_blocks<R>())
     batch_persistent_kernel(const BatchArgs a, int nsteps) {
   __shared__ StepParams sp;
   __shared__ int lam, tile, quit;
+  __shared__ __align__(16) char smem[TPS == 2 ? Batch2Smem<T, C>::kBytes : 16];
+  constexpr int NT = TPS == 2 ? kBatch2Threads : 32 * R;
   const int t = threadIdx.y * 32 + threadIdx.x;
   const unsigned long long per_step = (unsigned long long)a.ntiles + gridDim.x;
   for (int k = 0; k < nsteps; ++k) {
@@ -132,87 +225,81 @@ __global__ void __launch_bounds__(32 * R, (batch_min_blocks<R, CPT>()))
       const int ti = tile;
       if (ti >= a.ntiles) break;  // the same for the whole block
       const int4 tl = a.tiles[ti];
-      load_shot<32 * R>(a, tl.x, k, sp, lam);
-      batch_tile<T, C, U, R, CPT>(sp, lam, tl.y, tl.z);
-      __syncthreads();  // every thread is done with sp before the next claim
-    }
-    if (t == 0) {
-      quit = 0;
-      __threadfence();  // this block's stores before its arrival
-      atomicAdd(&a.hdr->arrive, 1ULL);
-      const unsigned long long target = (unsigned long long)(k + 1) * a.barrier_count;
-      const long long t0 = clock64();
-      while (load_acquire(&a.hdr->arrive) < target) {
-        if (clock64() - t0 > a.barrier_cycles) {
-          atomicOr(&a.hdr->err, 2);
-          quit = 1;
-          break;
-        }
+      if constexpr (TPS == 2) {
+        load_shot2<NT>(a, tl.x, k, sp, lam);
+        batch_tile2<T, C, U>(sp, lam, tl.y, tl.z, smem);
+      } else {
+        load_shot<NT>(a, tl.x, k, sp, lam);
+        batch_tile<T, C, U, R>(sp, lam, tl.y, tl.z);
       }
-      __threadfence();  // the other blocks' stores before this block's loads
+      __syncthreads();  // every thread is done with sp and smem before the next claim
     }
-    __syncthreads();
-    if (quit) return;
+    if (batch_grid_barrier(a, k, &quit)) return;
   }
 }
 
 // Advances hdr->kbase by g (the last node of a captured group of steps).
 __global__ void batch_advance_kernel(BatchHdr *h, int g);
 
-// Launch entry points, one translation unit per storage type.  R: 4 or 8;
-// cpt: cells per thread, 1 or 2 (2 with R = 8 only).
-cudaError_t batch_launch_f64(int R, int cpt, bool persistent, const BatchArgs &a, int count,
+// Launch entry points, one translation unit per storage type.  tps: time
+// steps per tile, 1 (tiles of 32 x R cells, R = 4 or 8) or 2 (the two-step
+// tiles; R unused).
+cudaError_t batch_launch_f64(int R, int tps, bool persistent, const BatchArgs &a, int count,
                              int grid, bool pdl, cudaStream_t s);
-cudaError_t batch_launch_f32(bool u64, int R, int cpt, bool persistent, const BatchArgs &a,
+cudaError_t batch_launch_f32(bool u64, int R, int tps, bool persistent, const BatchArgs &a,
                              int count, int grid, bool pdl, cudaStream_t s);
-cudaError_t batch_launch_16(bool bf16, bool u64, int R, int cpt, bool persistent,
+cudaError_t batch_launch_16(bool bf16, bool u64, int R, int tps, bool persistent,
                             const BatchArgs &a, int count, int grid, bool pdl, cudaStream_t s);
-int batch_occupancy_f64(int R, int cpt);
-int batch_occupancy_f32(bool u64, int R, int cpt);
-int batch_occupancy_16(bool bf16, bool u64, int R, int cpt);
+int batch_occupancy_f64(int R, int tps);
+int batch_occupancy_f32(bool u64, int R, int tps);
+int batch_occupancy_16(bool bf16, bool u64, int R, int tps);
 
-// Launches one form of the batched kernel: persistent (count = steps, grid
-// = resident blocks, cooperative) or one step (count = k, grid = tiles).
-template <class T, class C, class U, int R, int CPT>
+// Launches one form of the batched kernel: persistent (count = steps or
+// phases, grid = resident blocks, cooperative) or one step / phase (count =
+// its index k, grid = tiles).
+template <class T, class C, class U, int R, int TPS>
 cudaError_t batch_launch_t(bool persistent, const BatchArgs &a, int count, int grid, bool pdl,
                            cudaStream_t s) {
+  const dim3 block = TPS == 2 ? dim3(32, kF2Warps) : dim3(32, R);
   if (persistent) {
     void *args[] = {(void *)&a, (void *)&count};
-    return cudaLaunchCooperativeKernel((const void *)batch_persistent_kernel<T, C, U, R, CPT>,
-                                       dim3(grid), dim3(32, R), args, 0, s);
+    return cudaLaunchCooperativeKernel((const void *)batch_persistent_kernel<T, C, U, R, TPS>,
+                                       dim3(grid), block, args, 0, s);
   }
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(grid);
-  cfg.blockDim = dim3(32, R);
+  cfg.blockDim = block;
   cfg.stream = s;
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
   attr[0].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = attr;
   cfg.numAttrs = (pdl && LBM_PDL) ? 1 : 0;
-  return cudaLaunchKernelEx(&cfg, batch_step_kernel<T, C, U, R, CPT>, a, count);
+  if constexpr (TPS == 2) return cudaLaunchKernelEx(&cfg, batch_step2_kernel<T, C, U>, a, count);
+  else return cudaLaunchKernelEx(&cfg, batch_step_kernel<T, C, U, R>, a, count);
 }
 
-template <class T, class C, class U, int R, int CPT>
+template <class T, class C, class U, int R, int TPS>
 int batch_occupancy_t() {
   int n = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, batch_persistent_kernel<T, C, U, R, CPT>,
-                                                    32 * R, 0) != cudaSuccess)
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+          &n, batch_persistent_kernel<T, C, U, R, TPS>, TPS == 2 ? kBatch2Threads : 32 * R,
+          0) != cudaSuccess)
     return 0;
   return n;
 }
 
 template <class T, class C, class U>
-cudaError_t batch_launch_r(int R, int cpt, bool persistent, const BatchArgs &a, int count,
+cudaError_t batch_launch_r(int R, int tps, bool persistent, const BatchArgs &a, int count,
                            int grid, bool pdl, cudaStream_t s) {
-  if (cpt == 2) return batch_launch_t<T, C, U, 8, 2>(persistent, a, count, grid, pdl, s);
+  if (tps == 2) return batch_launch_t<T, C, U, 8, 2>(persistent, a, count, grid, pdl, s);
   if (R == 4) return batch_launch_t<T, C, U, 4, 1>(persistent, a, count, grid, pdl, s);
   return batch_launch_t<T, C, U, 8, 1>(persistent, a, count, grid, pdl, s);
 }
 
 template <class T, class C, class U>
-int batch_occupancy_r(int R, int cpt) {
-  if (cpt == 2) return batch_occupancy_t<T, C, U, 8, 2>();
+int batch_occupancy_r(int R, int tps) {
+  if (tps == 2) return batch_occupancy_t<T, C, U, 8, 2>();
   return R == 4 ? batch_occupancy_t<T, C, U, 4, 1>() : batch_occupancy_t<T, C, U, 8, 1>();
 }
 

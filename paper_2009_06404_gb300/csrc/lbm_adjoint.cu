@@ -18,7 +18,10 @@ namespace {
 constexpr size_t kAdjAlign = 256;
 // steps whose Lambda-gradient shares are summed in the compute type before
 // they are added to the FP64 sum (step 0 always flushes)
-constexpr int kFlushSteps = 16;
+#ifndef LBM_ADJ_FLUSH_STEPS
+#define LBM_ADJ_FLUSH_STEPS 16
+#endif
+constexpr int kFlushSteps = LBM_ADJ_FLUSH_STEPS;
 
 size_t aup(size_t v) { return (v + kAdjAlign - 1) / kAdjAlign * kAdjAlign; }
 
@@ -61,7 +64,8 @@ AdjLayout adj_layout(const lbm_elastic_t *h, int nsteps, int K) {
   return A;
 }
 
-std::string g_adj_create_error;
+// per thread: calls without a handle on different threads must not race on it
+thread_local std::string g_adj_create_error;
 
 // Dense FP64 [n][ny][nx] planes <-> padded planes of type C with the given
 // row and plane strides.

@@ -61,7 +61,7 @@ bool config_ok(const lbm_elastic_config *c, std::string *why) {
     return bad("free_surface_order must be 0 or 1");
   if (c->max_sources < 0 || c->max_receivers < 0 || c->max_steps_traced < 0)
     return bad("capacities must be >= 0");
-  if (c->kernel_variant < 0 || c->kernel_variant > 2) return bad("unknown kernel_variant");
+  if (c->kernel_variant < 0 || c->kernel_variant > 1) return bad("unknown kernel_variant");
   if (c->store_scale_log2 < -60 || c->store_scale_log2 > 60)
     return bad("store_scale_log2 must lie in [-60, 60]");
   return true;
@@ -255,7 +255,8 @@ __global__ void __launch_bounds__(kRedThreads) moments_final_kernel(const double
 
 namespace {
 
-std::string g_create_error;
+// per thread: calls without a handle on different threads must not race on it
+thread_local std::string g_create_error;
 
 lbm_status fail(lbm_elastic_t *h, lbm_status s, const std::string &msg) {
   if (h) h->err = msg;
@@ -478,102 +479,6 @@ lbm_status clear_state(lbm_elastic_t *h) {
   return LBM_OK;
 }
 
-typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *,
-                                  const cuuint64_t *, const cuuint64_t *, const cuuint32_t *,
-                                  const cuuint32_t *, CUtensorMapInterleave, CUtensorMapSwizzle,
-                                  CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
-
-// cuTensorMapEncodeTiled from the driver, looked up once through the runtime.
-EncodeTiledFn encode_tiled() {
-  static EncodeTiledFn fn = nullptr;
-  static std::once_flag once;
-  std::call_once(once, [] {
-    void *ptr = nullptr;
-    cudaDriverEntryPointQueryResult q;
-    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &ptr, 12000, cudaEnableDefault,
-                                         &q) == cudaSuccess &&
-        q == cudaDriverEntryPointSuccess)
-      fn = (EncodeTiledFn)ptr;
-  });
-  return fn;
-}
-
-// Builds the tensor maps of the TMA-staged kernel; false if TMA cannot be used.
-const CUtensorMapL2promotion kTmaPromotion =
-    LBM_TMA_L2_PROMOTION == 0 ? CU_TENSOR_MAP_L2_PROMOTION_NONE
-    : LBM_TMA_L2_PROMOTION == 1 ? CU_TENSOR_MAP_L2_PROMOTION_L2_128B
-                                : CU_TENSOR_MAP_L2_PROMOTION_L2_256B;
-
-bool setup_tma(lbm_elastic_t *h, std::string *why) {
-  const lbm_elastic_config &c = h->cfg;
-  const Layout &L = h->L;
-  if (c.storage != LBM_F32) {
-    *why = "the TMA-staged kernel covers FP32 storage only";
-    return false;
-  }
-  EncodeTiledFn enc = encode_tiled();
-  if (!enc) {
-    *why = "cuTensorMapEncodeTiled is not available";
-    return false;
-  }
-  int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess ||
-      cudaDeviceGetAttribute(&h->nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
-    *why = "cannot query the device";
-    return false;
-  }
-  int major = 0;
-  cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev);
-  if (major < 9) {
-    *why = "TMA needs compute capability 9.0 or newer";
-    return false;
-  }
-  const int es = (int)L.tsize;
-  const int halo = tma_halo_x(es);
-  for (int b = 0; b < 2; ++b)
-    for (int hh = 1; hh <= 2; ++hh) {
-      // dims listed fastest first; [y][plane][x] when rows are interleaved
-      const cuuint64_t dims[3] = {(cuuint64_t)c.nx, L.finter ? 9u : (cuuint64_t)c.ny,
-                                  L.finter ? (cuuint64_t)c.ny : 9u};
-      const cuuint64_t strides[2] = {
-          (cuuint64_t)(L.finter ? L.fplane : L.frow) * es,
-          (cuuint64_t)(L.finter ? L.frow : L.fplane) * es};
-      const cuuint32_t box[3] = {(cuuint32_t)(kTileW + 2 * halo),
-                                 L.finter ? 9u : (cuuint32_t)(kTileH + 2 * hh),
-                                 L.finter ? (cuuint32_t)(kTileH + 2 * hh) : 9u};
-      const cuuint32_t estr[3] = {1, 1, 1};
-      CUresult r = enc(&h->maps.f[b][hh - 1], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, h->ws + L.f[b],
-                       dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                       CU_TENSOR_MAP_SWIZZLE_NONE, kTmaPromotion,
-                       CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-      if (r != CUDA_SUCCESS) {
-        *why = "cuTensorMapEncodeTiled failed for the populations";
-        return false;
-      }
-    }
-  {
-    const int us = (int)L.usize;
-    const cuuint64_t dims[3] = {(cuuint64_t)c.nx, (cuuint64_t)c.ny, 2};
-    const cuuint64_t strides[2] = {(cuuint64_t)L.pitch * us, (cuuint64_t)L.plane * us};
-    const cuuint32_t box[3] = {(cuuint32_t)kTileW, (cuuint32_t)kTileH, 2};
-    const cuuint32_t estr[3] = {1, 1, 1};
-    CUresult r = enc(&h->maps.u, us == 8 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64
-                                         : CU_TENSOR_MAP_DATA_TYPE_FLOAT32,
-                     3, h->ws + L.u, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                     CU_TENSOR_MAP_SWIZZLE_NONE, kTmaPromotion,
-                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-    if (r != CUDA_SUCCESS) {
-      *why = "cuTensorMapEncodeTiled failed for the displacement";
-      return false;
-    }
-  }
-  if (tma_prepare(c.storage, L.usize == 8) != cudaSuccess) {
-    *why = "cannot reserve the kernel's shared memory";
-    return false;
-  }
-  return true;
-}
-
 }  // namespace
 
 // ------------------------------------------------------------ C ABI
@@ -591,11 +496,6 @@ lbm_status lbm::handle_step(lbm_elastic_t *h, void *grad_out) {
     h->lambda_nonzero = true;
     st = launch_step(h, p, 0, h->cfg.ny);
     h->lambda_nonzero = keep;
-  } else if (h->use_tma) {
-    const cudaError_t e = launch_step_tma(p, h->maps, h->cur, h->cfg.storage, h->L.usize == 8,
-                                          h->lambda_nonzero, h->nsm, h->stream);
-    st = e != cudaSuccess ? cuda_fail(h, e, "TMA step kernel launch")
-                          : check_launch(h, "TMA step kernel launch");
   } else {
     st = launch_step(h, p, 0, h->cfg.ny);
   }
@@ -637,7 +537,7 @@ constexpr long long kPersistWaitCycles = 4000000000LL;
 // conditions, and no tile one cell wide or high (a tile's pulls then reach
 // only its eight neighbours).
 static bool persistent_ok(const lbm_elastic_t *h) {
-  return !h->lambda_nonzero && !h->use_tma && h->cfg.nx % kF2Cols != 1 &&
+  return !h->lambda_nonzero && h->cfg.nx % kF2Cols != 1 &&
          h->cfg.ny % kF2Rows != 1;
 }
 
@@ -737,15 +637,6 @@ lbm_status lbm_elastic_create(const lbm_elastic_config *cfg, void *d_workspace,
                                     h->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
     if (e != cudaSuccess) s = cuda_fail(h, e, "create");
-  }
-  // The TMA-staged kernel is built on request only: on the half-space
-  // workload it measures slower than the direct-load kernel.
-  if (s == LBM_OK && cfg->kernel_variant == 2) {
-    std::string why;
-    h->use_tma = setup_tma(h, &why);
-    cudaGetLastError();  // a failed optional query leaves no sticky state behind
-    if (!h->use_tma && cfg->kernel_variant == 2)
-      s = fail(h, LBM_ERR_UNSUPPORTED, "TMA-staged kernel unavailable: " + why);
   }
   if (s != LBM_OK) {
     g_create_error = h->err;
@@ -951,7 +842,7 @@ lbm_status lbm_elastic_step(lbm_elastic_t *h, int nsteps) {
   if (spl == 0 && persistent_ok(h) && nsteps >= 2) {
     if (lbm_status st = handle_step2_run(h, nsteps / 2)) return st;
     s = nsteps / 2 * 2;
-  } else if (spl != 1 && !h->use_tma) {
+  } else if (spl != 1) {
     for (; s + 2 <= nsteps; s += 2)
       if (lbm_status st = handle_step2(h)) return st;
   }

@@ -28,11 +28,27 @@ long long tiles_for(const std::vector<lbm_elastic_t *> &shots, int R) {
   return t;
 }
 
+// Two-step tiles of a shot: 30 x 14 cells, or 28 x 12 with the
+// density-gradient force.
+void tile2_size(const lbm_elastic_t *h, int *W, int *H) {
+  *W = h->lambda_nonzero ? kL2Cols : kF2Cols;
+  *H = h->lambda_nonzero ? kL2Rows : kF2Rows;
+}
+
+// Two-step tiles of the batch if every shot took the smaller (gradient-force)
+// tile: an upper bound whatever the material.
+long long tiles2_max(const std::vector<lbm_elastic_t *> &shots) {
+  long long t = 0;
+  for (const lbm_elastic_t *h : shots)
+    t += (long long)((h->cfg.nx + kL2Cols - 1) / kL2Cols) * ((h->cfg.ny + kL2Rows - 1) / kL2Rows);
+  return t;
+}
+
 struct Offsets {
-  size_t hdr = 0, shots = 0, dyn = 0, tiles = 0, total = 0;
+  size_t hdr = 0, shots = 0, dyn = 0, tiles = 0, tiles2 = 0, total = 0;
 };
 
-Offsets offsets(int n, long long max_tiles) {
+Offsets offsets(int n, long long max_tiles, long long max_tiles2) {
   Offsets o;
   size_t off = 0;
   o.hdr = off;
@@ -43,11 +59,18 @@ Offsets offsets(int n, long long max_tiles) {
   off = up(off + (size_t)n * sizeof(BatchDyn));
   o.tiles = off;
   off = up(off + (size_t)max_tiles * sizeof(int4));
+  o.tiles2 = off;
+  off = up(off + (size_t)max_tiles2 * sizeof(int4));
   o.total = off;
   return o;
 }
 
-std::string g_batch_create_error;
+Offsets offsets_for(const std::vector<lbm_elastic_t *> &v) {
+  return offsets((int)v.size(), std::max(tiles_for(v, 4), tiles_for(v, 8)), tiles2_max(v));
+}
+
+// per thread: calls without a handle on different threads must not race on it
+thread_local std::string g_batch_create_error;
 
 }  // namespace
 
@@ -62,11 +85,15 @@ struct lbm_batch {
   int nsm = 0;
   lbm_batch_launch launch;
   bool tuned = false;
-  // tile list on the device
-  int ntiles = 0, tiles_rows = 0, tiles_order = -1, tiles_cpt = 0;
-  // captured graph of graph_steps steps for the current tile list
+  // tile lists on the device: one-step tiles, and two-step tiles (their
+  // geometry depends on each shot's Lambda, kept in tiles2_lam)
+  int ntiles = 0, tiles_rows = 0, tiles_order = -1;
+  int ntiles2 = 0, tiles2_order = -1;
+  std::vector<char> tiles2_lam;
+  // captured graph of graph_steps launches for the current tile list of
+  // graph_tps time steps per tile
   cudaGraphExec_t graph = nullptr;
-  int graph_steps = 0;
+  int graph_steps = 0, graph_tps = 0;
   long long launches = 0;
   std::vector<BatchShot> shot_host;
   std::vector<BatchDyn> dyn_host;
@@ -94,12 +121,12 @@ lbm_status bcuda(lbm_batch_t *b, cudaError_t e, const char *what) {
 
 BatchHdr *hdr_of(lbm_batch_t *b) { return (BatchHdr *)(b->ws + b->off.hdr); }
 
-BatchArgs args_of(lbm_batch_t *b) {
+BatchArgs args_of(lbm_batch_t *b, int tps) {
   BatchArgs a;
   a.shots = (const BatchShot *)(b->ws + b->off.shots);
   a.dyn = (const BatchDyn *)(b->ws + b->off.dyn);
-  a.tiles = (const int4 *)(b->ws + b->off.tiles);
-  a.ntiles = b->ntiles;
+  a.tiles = (const int4 *)(b->ws + (tps == 2 ? b->off.tiles2 : b->off.tiles));
+  a.ntiles = tps == 2 ? b->ntiles2 : b->ntiles;
   a.hdr = hdr_of(b);
   a.barrier_count = 0;
   a.barrier_cycles =
@@ -111,8 +138,7 @@ bool launch_ok(const lbm_batch_launch &l) {
   return l.mode >= LBM_BATCH_AUTO && l.mode <= LBM_BATCH_PERSISTENT &&
          (l.rows == 4 || l.rows == 8) && (l.order == 0 || l.order == 1) && l.graph_steps >= 1 &&
          l.steps_per_launch >= 1 && l.ctas_per_sm >= 0 && l.barrier_cycles >= 0 &&
-         l.barrier_extra >= 0 &&
-         (l.cells_per_thread == 1 || (l.cells_per_thread == 2 && l.rows == 8));
+         l.barrier_extra >= 0 && (l.steps_per_tile == 1 || l.steps_per_tile == 2);
 }
 
 // Whether tile (x0, y0) of W x R cells of shot h is likely to take the
@@ -127,14 +153,24 @@ bool tile_is_edge(const lbm_elastic_t *h, int x0, int y0, int W, int R) {
   return (h->nsrc > 0 && hit(h->src_box)) || (h->nrec > 0 && hit(h->rec_box));
 }
 
-lbm_status upload_tiles(lbm_batch_t *b, int R, int order, int cpt) {
-  if (b->tiles_rows == R && b->tiles_order == order && b->tiles_cpt == cpt) return LBM_OK;
-  const int W = 32 * cpt;
+void drop_graph(lbm_batch_t *b) {
+  if (b->graph) {
+    cudaGraphExecDestroy(b->graph);
+    b->graph = nullptr;
+  }
+}
+
+// Tiles of W x R cells of every shot (W, R from size(h)), shot by shot in
+// row-major order, or (order 1) those likely to take the general path first.
+template <class F>
+void list_tiles(lbm_batch_t *b, int order, F size) {
   std::vector<int4> &t = b->tile_host;
   t.clear();
   for (int pass = 0; pass < (order == 1 ? 2 : 1); ++pass) {
     for (int s = 0; s < (int)b->shots.size(); ++s) {
       const lbm_elastic_t *h = b->shots[s];
+      int W, R;
+      size(h, &W, &R);
       const int gx = (h->cfg.nx + W - 1) / W, gy = (h->cfg.ny + R - 1) / R;
       for (int by = 0; by < gy; ++by)
         for (int bx = 0; bx < gx; ++bx) {
@@ -143,16 +179,36 @@ lbm_status upload_tiles(lbm_batch_t *b, int R, int order, int cpt) {
         }
     }
   }
-  b->ntiles = (int)t.size();
-  BATCH_CUDA(b, cudaMemcpyAsync(b->ws + b->off.tiles, t.data(), t.size() * sizeof(int4),
-                                cudaMemcpyHostToDevice, b->stream));
+}
+
+lbm_status upload_tiles(lbm_batch_t *b, int R, int order) {
+  if (b->tiles_rows == R && b->tiles_order == order) return LBM_OK;
+  list_tiles(b, order, [R](const lbm_elastic_t *, int *W, int *H) {
+    *W = 32;
+    *H = R;
+  });
+  b->ntiles = (int)b->tile_host.size();
+  BATCH_CUDA(b, cudaMemcpyAsync(b->ws + b->off.tiles, b->tile_host.data(),
+                                b->tile_host.size() * sizeof(int4), cudaMemcpyHostToDevice,
+                                b->stream));
   b->tiles_rows = R;
   b->tiles_order = order;
-  b->tiles_cpt = cpt;
-  if (b->graph) {
-    cudaGraphExecDestroy(b->graph);
-    b->graph = nullptr;
-  }
+  if (b->graph_tps == 1) drop_graph(b);
+  return LBM_OK;
+}
+
+lbm_status upload_tiles2(lbm_batch_t *b, int order) {
+  std::vector<char> lam(b->shots.size());
+  for (size_t s = 0; s < b->shots.size(); ++s) lam[s] = b->shots[s]->lambda_nonzero ? 1 : 0;
+  if (b->tiles2_order == order && b->tiles2_lam == lam) return LBM_OK;
+  list_tiles(b, order, [](const lbm_elastic_t *h, int *W, int *H) { tile2_size(h, W, H); });
+  b->ntiles2 = (int)b->tile_host.size();
+  BATCH_CUDA(b, cudaMemcpyAsync(b->ws + b->off.tiles2, b->tile_host.data(),
+                                b->tile_host.size() * sizeof(int4), cudaMemcpyHostToDevice,
+                                b->stream));
+  b->tiles2_order = order;
+  b->tiles2_lam = lam;
+  if (b->graph_tps == 2) drop_graph(b);
   return LBM_OK;
 }
 
@@ -182,31 +238,33 @@ lbm_status prepare_call(lbm_batch_t *b) {
   return LBM_OK;
 }
 
-// The shots' host state after nsteps batched steps.
-void advance_shots(lbm_batch_t *b, int nsteps) {
+// The shots' host state after nlaunch batched launches of tps time steps
+// each (one buffer swap per launch).
+void advance_shots(lbm_batch_t *b, int nlaunch, int tps) {
+  const long long nsteps = (long long)nlaunch * tps;
   for (lbm_elastic_t *h : b->shots) {
     h->step += nsteps;
-    h->cur ^= (nsteps & 1);
+    h->cur ^= (nlaunch & 1);
     if (h->nrec > 0)
       h->traced = (int)std::min<long long>((long long)h->traced + nsteps, h->cfg.max_steps_traced);
   }
 }
 
-cudaError_t launch_form(lbm_batch_t *b, bool persistent, const BatchArgs &a, int count, int grid,
-                        bool pdl, cudaStream_t s) {
-  const int R = b->launch.rows, cpt = b->launch.cells_per_thread;
-  if (b->storage == LBM_F64) return batch_launch_f64(R, cpt, persistent, a, count, grid, pdl, s);
+cudaError_t launch_form(lbm_batch_t *b, int tps, bool persistent, const BatchArgs &a, int count,
+                        int grid, bool pdl, cudaStream_t s) {
+  const int R = b->launch.rows;
+  if (b->storage == LBM_F64) return batch_launch_f64(R, tps, persistent, a, count, grid, pdl, s);
   if (b->storage == LBM_F32)
-    return batch_launch_f32(b->u64, R, cpt, persistent, a, count, grid, pdl, s);
-  return batch_launch_16(b->storage == LBM_BF16, b->u64, R, cpt, persistent, a, count, grid, pdl,
+    return batch_launch_f32(b->u64, R, tps, persistent, a, count, grid, pdl, s);
+  return batch_launch_16(b->storage == LBM_BF16, b->u64, R, tps, persistent, a, count, grid, pdl,
                          s);
 }
 
-int occupancy(lbm_batch_t *b) {
-  const int R = b->launch.rows, cpt = b->launch.cells_per_thread;
-  if (b->storage == LBM_F64) return batch_occupancy_f64(R, cpt);
-  if (b->storage == LBM_F32) return batch_occupancy_f32(b->u64, R, cpt);
-  return batch_occupancy_16(b->storage == LBM_BF16, b->u64, R, cpt);
+int occupancy(lbm_batch_t *b, int tps) {
+  const int R = b->launch.rows;
+  if (b->storage == LBM_F64) return batch_occupancy_f64(R, tps);
+  if (b->storage == LBM_F32) return batch_occupancy_f32(b->u64, R, tps);
+  return batch_occupancy_16(b->storage == LBM_BF16, b->u64, R, tps);
 }
 
 lbm_status counted(lbm_batch_t *b, cudaError_t e, const char *what) {
@@ -216,24 +274,26 @@ lbm_status counted(lbm_batch_t *b, cudaError_t e, const char *what) {
   return LBM_OK;
 }
 
-lbm_status run_stream(lbm_batch_t *b, int nsteps) {
-  const BatchArgs a = args_of(b);
-  for (int k = 0; k < nsteps; ++k)
-    if (lbm_status st = counted(b, launch_form(b, false, a, k, b->ntiles, true, b->stream), "batch step"))
+// n launches of tps time steps each, one per launch.
+lbm_status run_stream(lbm_batch_t *b, int n, int tps) {
+  const BatchArgs a = args_of(b, tps);
+  for (int k = 0; k < n; ++k)
+    if (lbm_status st = counted(b, launch_form(b, tps, false, a, k, a.ntiles, true, b->stream),
+                                "batch step"))
       return st;
   return LBM_OK;
 }
 
-// Captures G step launches and the kbase advance into a graph.  The step
-// launches carry the programmatic-dependent-launch attribute when the
-// capture accepts it, else they are captured plainly.
-cudaError_t capture_graph(lbm_batch_t *b, int G, bool pdl, cudaGraphExec_t *out) {
-  const BatchArgs a = args_of(b);
+// Captures G launches of tps time steps each and the kbase advance into a
+// graph.  The launches carry the programmatic-dependent-launch attribute
+// when the capture accepts it, else they are captured plainly.
+cudaError_t capture_graph(lbm_batch_t *b, int G, int tps, bool pdl, cudaGraphExec_t *out) {
+  const BatchArgs a = args_of(b, tps);
   cudaGraph_t g = nullptr;
   cudaError_t e = cudaStreamBeginCapture(b->capture, cudaStreamCaptureModeThreadLocal);
   if (e != cudaSuccess) return e;
   for (int k = 0; k < G && e == cudaSuccess; ++k)
-    e = launch_form(b, false, a, k, b->ntiles, pdl, b->capture);
+    e = launch_form(b, tps, false, a, k, a.ntiles, pdl, b->capture);
   if (e == cudaSuccess) {
     batch_advance_kernel<<<1, 1, 0, b->capture>>>(hdr_of(b), G);
     e = cudaGetLastError();
@@ -245,57 +305,59 @@ cudaError_t capture_graph(lbm_batch_t *b, int G, bool pdl, cudaGraphExec_t *out)
   return e;
 }
 
-lbm_status build_graph(lbm_batch_t *b, int G) {
-  if (b->graph && b->graph_steps == G) return LBM_OK;
-  if (b->graph) {
-    cudaGraphExecDestroy(b->graph);
-    b->graph = nullptr;
-  }
+lbm_status build_graph(lbm_batch_t *b, int G, int tps) {
+  if (b->graph && b->graph_steps == G && b->graph_tps == tps) return LBM_OK;
+  drop_graph(b);
   // captured on a private stream (the legacy default stream cannot be
   // captured); the graph is launched on the batch's stream
   if (!b->capture) BATCH_CUDA(b, cudaStreamCreateWithFlags(&b->capture, cudaStreamNonBlocking));
   cudaGraphExec_t x = nullptr;
-  cudaError_t e = capture_graph(b, G, true, &x);
+  cudaError_t e = capture_graph(b, G, tps, true, &x);
   if (e != cudaSuccess) {
     cudaGetLastError();  // clear, and capture without the attribute
     x = nullptr;
-    e = capture_graph(b, G, false, &x);
+    e = capture_graph(b, G, tps, false, &x);
   }
   if (e != cudaSuccess) return bcuda(b, e, "batch graph capture");
   b->graph = x;
   b->graph_steps = G;
+  b->graph_tps = tps;
   return LBM_OK;
 }
 
-lbm_status run_graph(lbm_batch_t *b, int nsteps) {
+lbm_status run_graph(lbm_batch_t *b, int n, int tps) {
   const int G = b->launch.graph_steps;
-  if (nsteps >= G) {
-    if (lbm_status st = build_graph(b, G)) return st;
-    for (int r = 0; r + G <= nsteps; r += G) {
+  if (n >= G) {
+    if (lbm_status st = build_graph(b, G, tps)) return st;
+    for (int r = 0; r + G <= n; r += G) {
       BATCH_CUDA(b, cudaGraphLaunch(b->graph, b->stream));
       b->launches += G + 1;
     }
   }
-  // the remainder: plain launches after the graphs' steps (kbase holds them)
-  const BatchArgs a = args_of(b);
-  for (int k = 0; k < nsteps % G; ++k)
-    if (lbm_status st = counted(b, launch_form(b, false, a, k, b->ntiles, true, b->stream), "batch step"))
+  // the remainder: plain launches after the graphs' launches (kbase holds them)
+  const BatchArgs a = args_of(b, tps);
+  for (int k = 0; k < n % G; ++k)
+    if (lbm_status st = counted(b, launch_form(b, tps, false, a, k, a.ntiles, true, b->stream),
+                                "batch step"))
       return st;
   return LBM_OK;
 }
 
-lbm_status run_persistent(lbm_batch_t *b, int nsteps) {
-  const int occ = occupancy(b);
+// n steps (tps 1) or two-step phases (tps 2) in cooperative launches of at
+// most steps_per_launch time steps each.
+lbm_status run_persistent(lbm_batch_t *b, int n, int tps) {
+  const int occ = occupancy(b, tps);
   if (occ < 1) return bfail(b, LBM_ERR_CUDA, "batch persistent kernel: no resident block fits");
   const int per_sm = b->launch.ctas_per_sm > 0 ? std::min(b->launch.ctas_per_sm, occ) : occ;
   const int grid = b->nsm * per_sm;
-  BatchArgs a = args_of(b);
+  BatchArgs a = args_of(b, tps);
   a.barrier_count = (unsigned)(grid + b->launch.barrier_extra);
-  for (int done = 0; done < nsteps;) {
-    const int m = std::min(b->launch.steps_per_launch, nsteps - done);
+  const int per_launch = std::max(1, b->launch.steps_per_launch / tps);
+  for (int done = 0; done < n;) {
+    const int m = std::min(per_launch, n - done);
     // queue and arrival counters restart with each launch
     BATCH_CUDA(b, cudaMemsetAsync(hdr_of(b), 0, offsetof(BatchHdr, kbase), b->stream));
-    if (lbm_status st = counted(b, launch_form(b, true, a, m, grid, false, b->stream),
+    if (lbm_status st = counted(b, launch_form(b, tps, true, a, m, grid, false, b->stream),
                                    "batch persistent"))
       return st;
     batch_advance_kernel<<<1, 1, 0, b->stream>>>(hdr_of(b), m);
@@ -305,32 +367,48 @@ lbm_status run_persistent(lbm_batch_t *b, int nsteps) {
   return LBM_OK;
 }
 
-lbm_status run(lbm_batch_t *b, int nsteps, int mode) {
-  if (nsteps == 0) return LBM_OK;
-  if (lbm_status st =
-          upload_tiles(b, b->launch.rows, b->launch.order, b->launch.cells_per_thread))
+// n launches of tps time steps each in the given form, from the shots'
+// current state.
+lbm_status run_launches(lbm_batch_t *b, int n, int tps, int mode) {
+  if (n == 0) return LBM_OK;
+  if (lbm_status st = tps == 2 ? upload_tiles2(b, b->launch.order)
+                               : upload_tiles(b, b->launch.rows, b->launch.order))
     return st;
   if (lbm_status st = prepare_call(b)) return st;
   lbm_status st;
-  if (mode == LBM_BATCH_STREAM) st = run_stream(b, nsteps);
-  else if (mode == LBM_BATCH_PERSISTENT) st = run_persistent(b, nsteps);
-  else st = run_graph(b, nsteps);
+  if (mode == LBM_BATCH_STREAM) st = run_stream(b, n, tps);
+  else if (mode == LBM_BATCH_PERSISTENT) st = run_persistent(b, n, tps);
+  else st = run_graph(b, n, tps);
   if (st) return st;
-  advance_shots(b, nsteps);
+  advance_shots(b, n, tps);
   return LBM_OK;
 }
 
+// nsteps time steps: with two steps per tile, nsteps / 2 two-step launches
+// and, for an odd count, one one-step launch.
+lbm_status run(lbm_batch_t *b, int nsteps, int mode) {
+  if (b->launch.steps_per_tile == 2) {
+    if (lbm_status st = run_launches(b, nsteps / 2, 2, mode)) return st;
+    return run_launches(b, nsteps % 2, 1, mode);
+  }
+  return run_launches(b, nsteps, 1, mode);
+}
+
+// Times every launch candidate on the batch itself: per candidate two
+// untimed steps (tile upload, graph capture) and trial steps (rounded up to
+// even) timed.  Advances the shots by 18 (2 + trial) steps.
 lbm_status tune(lbm_batch_t *b, int trial, double *best_us) {
   const lbm_batch_launch keep = b->launch;
   struct Cand {
-    int mode, rows, order, cpt;
+    int mode, rows, order, tps;
   };
+  trial += trial & 1;
   std::vector<Cand> cands;
-  for (int mode : {LBM_BATCH_STREAM, LBM_BATCH_GRAPH, LBM_BATCH_PERSISTENT})
+  for (int mode : {LBM_BATCH_STREAM, LBM_BATCH_GRAPH, LBM_BATCH_PERSISTENT}) {
     for (int rows : {8, 4})
-      for (int cpt : {1, 2})
-        if (cpt == 1 || rows == 8)
-          for (int order : {1, 0}) cands.push_back({mode, rows, order, cpt});
+      for (int order : {1, 0}) cands.push_back({mode, rows, order, 1});
+    for (int order : {1, 0}) cands.push_back({mode, 8, order, 2});
+  }
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   BATCH_CUDA(b, cudaEventCreate(&e0));
   BATCH_CUDA(b, cudaEventCreate(&e1));
@@ -341,12 +419,11 @@ lbm_status tune(lbm_batch_t *b, int trial, double *best_us) {
     b->launch.mode = c.mode;
     b->launch.rows = c.rows;
     b->launch.order = c.order;
-    b->launch.cells_per_thread = c.cpt;
-    b->launch.graph_steps = trial;
+    b->launch.steps_per_tile = c.tps;
+    b->launch.graph_steps = trial / c.tps;
     b->launch.steps_per_launch = std::max(keep.steps_per_launch, trial);
-    // one untimed step (tile upload, graph capture), then the timed ones
-    if ((st = run(b, 1, c.mode))) break;
-    if (c.mode == LBM_BATCH_GRAPH && (st = build_graph(b, trial))) break;
+    if ((st = run(b, 2, c.mode))) break;
+    if (c.mode == LBM_BATCH_GRAPH && (st = build_graph(b, trial / c.tps, c.tps))) break;
     cudaEventRecord(e0, b->stream);
     if ((st = run(b, trial, c.mode))) break;
     cudaEventRecord(e1, b->stream);
@@ -369,7 +446,7 @@ lbm_status tune(lbm_batch_t *b, int trial, double *best_us) {
   b->launch.mode = win.mode;
   b->launch.rows = win.rows;
   b->launch.order = win.order;
-  b->launch.cells_per_thread = win.cpt;
+  b->launch.steps_per_tile = win.tps;
   b->tuned = true;
   if (best_us) *best_us = best;
   return LBM_OK;
@@ -384,7 +461,7 @@ size_t lbm_batch_workspace_bytes(lbm_elastic_t *const *shots, int n) {
   std::vector<lbm_elastic_t *> v(shots, shots + n);
   for (lbm_elastic_t *h : v)
     if (!h) return 0;
-  return offsets(n, std::max(tiles_for(v, 4), tiles_for(v, 8))).total;
+  return offsets_for(v).total;
 }
 
 lbm_status lbm_batch_create(lbm_elastic_t *const *shots, int n, void *d_workspace, size_t bytes,
@@ -403,15 +480,18 @@ lbm_status lbm_batch_create(lbm_elastic_t *const *shots, int n, void *d_workspac
     return bfail(nullptr, LBM_ERR_WORKSPACE, "batch workspace too small");
   if ((uintptr_t)d_workspace % kBatchAlign)
     return bfail(nullptr, LBM_ERR_WORKSPACE, "batch workspace not 256-byte aligned");
-  if (tiles_for(std::vector<lbm_elastic_t *>(shots, shots + n), 4) >= (1LL << 31))
-    return bfail(nullptr, LBM_ERR_ARG, "too many tiles");
+  {
+    const std::vector<lbm_elastic_t *> v(shots, shots + n);
+    if (tiles_for(v, 4) >= (1LL << 31) || tiles2_max(v) >= (1LL << 31))
+      return bfail(nullptr, LBM_ERR_ARG, "too many tiles");
+  }
   lbm_batch_t *b = new (std::nothrow) lbm_batch();
   if (!b) return bfail(nullptr, LBM_ERR_ARG, "out of host memory");
   b->shots.assign(shots, shots + n);
   b->storage = shots[0]->cfg.storage;
   b->u64 = shots[0]->L.usize == 8 && b->storage != LBM_F64;
   b->ws = (char *)d_workspace;
-  b->off = offsets(n, std::max(tiles_for(b->shots, 4), tiles_for(b->shots, 8)));
+  b->off = offsets_for(b->shots);
   b->stream = (cudaStream_t)cuda_stream;
   b->shot_host.resize(n);
   b->dyn_host.resize(n);
@@ -427,7 +507,7 @@ lbm_status lbm_batch_create(lbm_elastic_t *const *shots, int n, void *d_workspac
   b->launch.ctas_per_sm = 0;
   b->launch.barrier_cycles = 0;
   b->launch.barrier_extra = 0;
-  b->launch.cells_per_thread = 1;
+  b->launch.steps_per_tile = 1;
   if (cudaMemsetAsync(d_workspace, 0, sizeof(BatchHdr), b->stream) != cudaSuccess) {
     delete b;
     return bfail(nullptr, LBM_ERR_CUDA, "batch workspace clear failed");
@@ -460,9 +540,9 @@ lbm_status lbm_batch_step(lbm_batch_t *b, int nsteps) {
   if (!b) return LBM_ERR_ARG;
   if (nsteps < 0) return bfail(b, LBM_ERR_ARG, "nsteps < 0");
   if (b->launch.mode == LBM_BATCH_AUTO && !b->tuned) {
-    // 18 candidates x (1 + 3) steps
+    // 18 candidates x (2 + 2) steps
     if (nsteps >= kAutoMinSteps) {
-      if (lbm_status st = tune(b, 3, nullptr)) return st;
+      if (lbm_status st = tune(b, 2, nullptr)) return st;
       nsteps -= 72;
     } else {
       return run(b, nsteps, LBM_BATCH_GRAPH);

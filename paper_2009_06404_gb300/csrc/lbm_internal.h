@@ -7,7 +7,6 @@
 
 #include "lbm_elastic.h"
 #include "lbm_kernels.cuh"
-#include "step_tma.cuh"
 
 namespace lbm {
 
@@ -30,8 +29,6 @@ struct Layout {
 
 // One grid: configuration, workspace layout and host-side state.
 struct lbm_elastic {
-  lbm::TmaMaps maps;                // tensor maps of the TMA-staged kernel
-  bool use_tma = false;
   int nsm = 0;                 // multiprocessors of the device
   lbm_elastic_config cfg;
   lbm::Layout L;

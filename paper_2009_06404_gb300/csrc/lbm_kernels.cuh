@@ -165,50 +165,6 @@ __device__ __forceinline__ C unit_scale(const StepParams &p) {
   return sizeof(T) == 2 ? C(p.iscale_f) : C(1);
 }
 
-// Loads and stores of two horizontally adjacent populations at once (the
-// first at an even x, so the pair is aligned): float2 / double2 / half2 /
-// bfloat162, with the same conversions and rounding as the single ones.
-template <class T> struct Pair2;
-template <> struct Pair2<float> { using type = float2; };
-template <> struct Pair2<double> { using type = double2; };
-template <> struct Pair2<__half> { using type = __half2; };
-template <> struct Pair2<__nv_bfloat16> { using type = __nv_bfloat162; };
-
-__device__ __forceinline__ void unpack2(float2 v, float &a, float &b) { a = v.x; b = v.y; }
-__device__ __forceinline__ void unpack2(double2 v, double &a, double &b) { a = v.x; b = v.y; }
-__device__ __forceinline__ void unpack2(__half2 v, float &a, float &b) {
-  const float2 f = __half22float2(v);
-  a = f.x;
-  b = f.y;
-}
-__device__ __forceinline__ void unpack2(__nv_bfloat162 v, float &a, float &b) {
-  const float2 f = __bfloat1622float2(v);
-  a = f.x;
-  b = f.y;
-}
-__device__ __forceinline__ float2 pack2(float a, float b, float2 *) { return make_float2(a, b); }
-__device__ __forceinline__ double2 pack2(double a, double b, double2 *) {
-  return make_double2(a, b);
-}
-__device__ __forceinline__ __half2 pack2(float a, float b, __half2 *) {
-  return __floats2half2_rn(a, b);
-}
-__device__ __forceinline__ __nv_bfloat162 pack2(float a, float b, __nv_bfloat162 *) {
-  return __floats2bfloat162_rn(a, b);
-}
-
-template <class T, class C>
-__device__ __forceinline__ void ldp2(const T *ptr, const StepParams &, C &a, C &b) {
-  using P2 = typename Pair2<T>::type;
-  unpack2(__ldcg(reinterpret_cast<const P2 *>(ptr)), a, b);
-}
-
-template <class T, class C>
-__device__ __forceinline__ void stp2(T *ptr, C a, C b, const StepParams &) {
-  using P2 = typename Pair2<T>::type;
-  *reinterpret_cast<P2 *>(ptr) = pack2(a, b, (P2 *)nullptr);
-}
-
 // Product rounded on its own (never fused with a following addition), and a
 // fused multiply-add, so that every path of the step rounds these
 // expressions the same way whatever the compiler would contract.
@@ -893,53 +849,6 @@ __device__ __noinline__ void general_block_lam(const StepParams &p, int x0, int 
 template <class T, class C, class U, bool LAM, int MODE, int R>
 __device__ __forceinline__ void step_block(const StepParams &p, int bx, int by);
 
-// Blocks run roughly in launch order, a few block rows at a time.  A block
-// asks L2 for the rows that the block LBM_PREFETCH_ROWS block rows later in
-// that order will read (its nine population rows with the halo, and its
-// displacement rows): hint instructions that hold no registers, so more of
-// the step's reads are in flight than the registers of the resident warps
-// allow, and the later block's loads hit L2.
-#ifndef LBM_PREFETCH_ROWS
-#define LBM_PREFETCH_ROWS 0
-#endif
-template <class T, class U, int R>
-__device__ __forceinline__ void prefetch_ahead(const StepParams &p, int bx, int k) {
-  const int kk = k + LBM_PREFETCH_ROWS;
-  if (kk >= (int)gridDim.y) return;
-  int by = kk;
-  if (p.reverse) {
-#if LBM_ORDER == 1
-    by = kk > 0 ? (int)gridDim.y - kk : 0;
-#else
-    by = (int)gridDim.y - 1 - kk;
-#endif
-  }
-  const int t = threadIdx.y * 32 + threadIdx.x;
-  // x segment [32 bx - 1, 32 bx + 33), clipped to the padded row
-  const int xs = max(bx * 32 - 1, 0), xe = min(bx * 32 + 33, p.pitch);
-  int y, seg_bytes;
-  const char *base;
-  if (t < 9 * (R + 2)) {
-    // population plane i of rows y0 - 1 .. y0 + R of the later block
-    const int i = t % 9;
-    y = by * R - 1 + t / 9;
-    if (y < 0 || y >= p.ny) return;
-    base = (const char *)p.fin + ((long long)y * p.frow + (long long)i * p.fplane + xs) * sizeof(T);
-    seg_bytes = (xe - xs) * (int)sizeof(T);
-  } else if (t < 9 * (R + 2) + 2 * R) {
-    const int q = t - 9 * (R + 2);
-    y = by * R + q / 2;
-    if (y >= p.ny) return;
-    base = (const char *)p.u +
-           ((long long)(q & 1) * p.plane + (long long)y * p.pitch + bx * 32) * sizeof(U);
-    seg_bytes = (min(bx * 32 + 32, p.pitch) - bx * 32) * (int)sizeof(U);
-  } else {
-    return;
-  }
-  asm volatile("prefetch.global.L2 [%0];" ::"l"(base));
-  asm volatile("prefetch.global.L2 [%0];" ::"l"(base + seg_bytes - 1));
-}
-
 template <class T, class C, class U, bool LAM, int MODE>
 __global__ void __launch_bounds__(LAM ? 32 * kLamRows : 256,
                                   LAM ? LBM_STEP_MIN_BLOCKS_LAM : LBM_STEP_MIN_BLOCKS)
@@ -966,9 +875,6 @@ __global__ void __launch_bounds__(LAM ? 32 * kLamRows : 256,
     by = gridDim.y - 1 - by;
 #endif
   }
-#if LBM_PREFETCH_ROWS > 0
-  if (MODE == 0) prefetch_ahead<T, U, LAM ? kLamRows : 8>(p, bx, blockIdx.y);
-#endif
   step_block<T, C, U, LAM, MODE, LAM ? kLamRows : 8>(p, bx, by);
 }
 
@@ -1057,179 +963,6 @@ __device__ __forceinline__ void step_block(const StepParams &p, int bx, int by) 
   u[p.plane + c] = uy0 + U(mul_rn(jy, irho));
   if (!((M.rho + jx + jy) * C(0) == C(0))) atomicOr(p.err, 1);
 }
-
-// ------------------------------------------------------------ two cells per thread
-//
-// The step with each thread updating the two cells (x, x + 1), x even, of a
-// 64-cell row segment: every population and displacement load and store is
-// one aligned pair access (half the instructions of the one-cell form), the
-// populations pulled across x come from the neighbouring lane by a shuffle,
-// and the warp's two ends load the one value beyond the segment.  Bulk
-// blocks only; blocks near walls, sources or receivers run the one-cell
-// general path on their two 32-cell halves.  Each cell's arithmetic is the
-// one-cell form's.
-
-// The pulled populations i of cells (xa, xa + 1), xa = x0 + 2 lane, of row y.
-template <class T, class C>
-__device__ __forceinline__ void pull_pair(const StepParams &p, const T *fin, int i, int xa, int y,
-                                          int lane, C &va, C &vb) {
-  const int cx = cxd(i);
-  const T *row = fin + ((y - cyd(i)) * p.frow + i * p.fplane);
-  C lo, hi;
-  ldp2<T, C>(row + xa, p, lo, hi);
-  if (cx == 0) {
-    va = lo;
-    vb = hi;
-  } else if (cx == 1) {  // from x - 1: (xa - 1, xa)
-    C prev = __shfl_up_sync(0xffffffffu, hi, 1);
-    if (lane == 0) prev = ldp<T, C>(row + xa - 1, p);
-    va = prev;
-    vb = lo;
-  } else {  // from x + 1: (xa + 1, xa + 2)
-    C next = __shfl_down_sync(0xffffffffu, lo, 1);
-    if (lane == 31) next = ldp<T, C>(row + xa + 2, p);
-    va = hi;
-    vb = next;
-  }
-}
-
-template <class U> struct UPair;
-template <> struct UPair<float> { using type = float2; };
-template <> struct UPair<double> { using type = double2; };
-
-template <class T, class C, class U, bool LAM, int R>
-__device__ __forceinline__ void step_block_pair(const StepParams &p, int bx, int by) {
-  static_assert(128 + 2 * R <= 32 * R, "one ring cell per thread at most");
-  const int lane = threadIdx.x, ty = threadIdx.y;
-  const int x0 = bx * 64, y0 = by * R, y = y0 + ty;
-  const int m = LAM ? 2 : 1;
-  if (block_is_special<64>(p, x0, y0, R, m)) {
-    // the same for every thread of the block
-    if (LAM) {
-      general_block_lam<T, C, U, 0, R>(p, x0, y0, p.ny);
-      __syncthreads();  // both halves use the same shared-memory tile
-      general_block_lam<T, C, U, 0, R>(p, x0 + 32, y0, p.ny);
-    } else {
-      general_cell<T, C, U, 0>(p, x0 + lane, y, p.ny);
-      general_cell<T, C, U, 0>(p, x0 + 32 + lane, y, p.ny);
-    }
-    return;
-  }
-  const int xa = x0 + 2 * lane;
-  const T *fin = (const T *)p.fin;
-  C fa[9], fb[9];
-#pragma unroll
-  for (int i = 0; i < 9; ++i) pull_pair<T, C>(p, fin, i, xa, y, lane, fa[i], fb[i]);
-  // ring of the block for the density gradient: rows above and below (128
-  // cells), columns left and right (2 R), pulled with the cells' own
-  const int t = ty * 32 + lane;
-  int hx = 0, hy = 0;
-  C hf[LAM ? 9 : 1];
-  if (LAM && t < 128 + 2 * R) {
-    if (t < 128) {
-      hx = t & 63;
-      hy = t < 64 ? -1 : R;
-    } else {
-      hx = (t & 1) ? 64 : -1;
-      hy = (t - 128) >> 1;
-    }
-    const T *b = fin + ((y0 + hy) * p.frow + x0 + hx);
-#pragma unroll
-    for (int i = 0; i < (LAM ? 9 : 1); ++i)
-      hf[i] = ldp<T, C>(b + (i * p.fplane - cyd(i) * p.frow - cxd(i)), p);
-  }
-  const int c = y * p.pitch + xa;
-  U *u = (U *)p.u;
-  using UP = typename UPair<U>::type;
-  const UP ux0 = __ldcg(reinterpret_cast<const UP *>(u + c));
-  const UP uy0 = __ldcg(reinterpret_cast<const UP *>(u + p.plane + c));
-  const C irha = irho_at<T, C>(p, xa, y), irhb = irho_at<T, C>(p, xa + 1, y);
-  const Moments<C> Ma = cell_moments<C>(fa), Mb = cell_moments<C>(fb);
-  C Gxa = C(0), Gya = C(0), Gxb = C(0), Gyb = C(0);
-  if (LAM) {
-    // streamed densities (the plain sums, as on every path) of the block and
-    // its ring in shared memory; every block here is bulk: uniform barrier
-    __shared__ C rho_s[R + 2][66];
-    rho_s[ty + 1][2 * lane + 1] =
-        fa[0] + fa[1] + fa[2] + fa[3] + fa[4] + fa[5] + fa[6] + fa[7] + fa[8];
-    rho_s[ty + 1][2 * lane + 2] =
-        fb[0] + fb[1] + fb[2] + fb[3] + fb[4] + fb[5] + fb[6] + fb[7] + fb[8];
-    if (t < 128 + 2 * R) {
-      C r = C(0);
-#pragma unroll
-      for (int i = 0; i < (LAM ? 9 : 1); ++i) r += hf[i];
-      rho_s[hy + 1][hx + 1] = r;
-    }
-    __syncthreads();
-    const int ca = 2 * lane + 1, cb = ca + 1;
-    const C gxa = C(0.5) * (rho_s[ty + 1][ca + 1] - rho_s[ty + 1][ca - 1]);
-    const C gya = C(0.5) * (rho_s[ty + 2][ca] - rho_s[ty][ca]);
-    const C gxb = C(0.5) * (rho_s[ty + 1][cb + 1] - rho_s[ty + 1][cb - 1]);
-    const C gyb = C(0.5) * (rho_s[ty + 2][cb] - rho_s[ty][cb]);
-    if (p.grad_out) {
-      C *g = (C *)p.grad_out;
-      g[c] = gxa;
-      g[c + 1] = gxb;
-      g[p.plane + c] = gya;
-      g[p.plane + c + 1] = gyb;
-    }
-    C la, lb;
-    if (p.mat_per_cell) {
-      la = ((const C *)p.lam)[c];
-      lb = ((const C *)p.lam)[c + 1];
-    } else {
-      la = lb = ((const C *)p.lam)[y];
-    }
-    la *= C(1.0 / 3.0);
-    lb *= C(1.0 / 3.0);
-    Gxa = mul_rn(la, gxa);
-    Gya = mul_rn(la, gya);
-    Gxb = mul_rn(lb, gxb);
-    Gyb = mul_rn(lb, gyb);
-  }
-  const bool spg = x0 < p.sp_left || x0 + 64 > p.nx - p.sp_right || y0 < p.sp_top ||
-                   y0 + R > p.ny - p.sp_bottom;
-  C fsa[9], fsb[9], jxa, jya, jxb, jyb;
-  bulk_collide<C>(p, Ma, Gxa, Gya, spg, xa, y, fsa, jxa, jya);
-  bulk_collide<C>(p, Mb, Gxb, Gyb, spg, xa + 1, y, fsb, jxb, jyb);
-  T *fout = (T *)p.fout + (y * p.frow + xa);
-#pragma unroll
-  for (int i = 0; i < 9; ++i) stp2<T, C>(fout + i * p.fplane, fsa[i], fsb[i], p);
-  UP nx_, ny_;
-  nx_.x = ux0.x + U(mul_rn(jxa, irha));
-  nx_.y = ux0.y + U(mul_rn(jxb, irhb));
-  ny_.x = uy0.x + U(mul_rn(jya, irha));
-  ny_.y = uy0.y + U(mul_rn(jyb, irhb));
-  *reinterpret_cast<UP *>(u + c) = nx_;
-  *reinterpret_cast<UP *>(u + p.plane + c) = ny_;
-  if (!((Ma.rho + jxa + jya + Mb.rho + jxb + jyb) * C(0) == C(0))) atomicOr(p.err, 1);
-}
-
-#ifndef LBM_PAIR_MIN_BLOCKS
-#define LBM_PAIR_MIN_BLOCKS 4
-#endif
-
-template <class T, class C, class U, bool LAM>
-__global__ void __launch_bounds__(256, LBM_PAIR_MIN_BLOCKS) step_pair_kernel(const StepParams p) {
-#if LBM_PDL
-  asm volatile("griddepcontrol.wait;" ::: "memory");
-  asm volatile("griddepcontrol.launch_dependents;");
-#endif
-  int bx = blockIdx.x, by = blockIdx.y;
-  if (p.reverse) {
-#if LBM_ORDER == 1
-    if (by > 0) by = gridDim.y - by;
-    bx = gridDim.x - 1 - bx;
-#else
-    bx = gridDim.x - 1 - bx;
-    by = gridDim.y - 1 - by;
-#endif
-  }
-  step_block_pair<T, C, U, LAM, LAM ? kLamRows : 8>(p, bx, by);
-}
-
-// Grid of the two-cells-per-thread kernel for the rows a 32-wide grid covered.
-inline dim3 pair_grid(dim3 g, int nx) { return dim3((nx + 63) / 64, g.y, 1); }
 
 // Launch entry points, one translation unit per storage type.
 void launch_step_f64(const StepParams &p, bool lam, int mode, dim3 grid, dim3 block,

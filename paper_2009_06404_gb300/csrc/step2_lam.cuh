@@ -327,6 +327,21 @@ __device__ __noinline__ void lam_general(const StepParams &p, const Phase2 &ph, 
   if (ph.slot_b >= 0) record_receiver<U>(p, ph.slot_b, x, y, ux, uy, vx, vy);
 }
 
+// Steps n = p.n and n + 1 of the tile (bx, by) with the density-gradient
+// force, by the 32 x kL2H threads of a block (tile, rho_s: its shared
+// memory).  Every thread calls it; it holds three block barriers.
+template <class T, class C, class U>
+__device__ __forceinline__ void step2_lam_tile(const StepParams &p, int bx, int by, T *tile,
+                                               C (*rho_s)[kL2RW]) {
+  const Phase2 ph = phase2(p, 0);
+  const int x0 = bx * kL2Cols, y0 = by * kL2Rows;
+  if (lam_tile_special(p, x0, y0, ph.slot_a)) {
+    lam_general<T, C, U>(p, ph, x0, y0, tile, rho_s);
+    return;
+  }
+  lam_bulk<T, C, U>(p, ph, x0, y0, tile, rho_s);
+}
+
 // Steps n = p.n and n + 1 from p.fin to p.fout with the density-gradient
 // force, one block of 32 x kL2H threads per 28 x kL2Rows tile.  p.reverse:
 // the tiles in reverse order (the top tile row still first).
@@ -344,13 +359,7 @@ __global__ void __launch_bounds__(32 * kL2H, LBM_STEP2L_MIN_BLOCKS)
     if (by > 0) by = gridDim.y - by;
     bx = gridDim.x - 1 - bx;
   }
-  const Phase2 ph = phase2(p, 0);
-  const int x0 = bx * kL2Cols, y0 = by * kL2Rows;
-  if (lam_tile_special(p, x0, y0, ph.slot_a)) {
-    lam_general<T, C, U>(p, ph, x0, y0, tile, rho_s);
-    return;
-  }
-  lam_bulk<T, C, U>(p, ph, x0, y0, tile, rho_s);
+  step2_lam_tile<T, C, U>(p, bx, by, tile, rho_s);
 }
 
 inline dim3 step2_lam_grid(int nx, int ny) {

@@ -4,23 +4,14 @@
 #include "step_fused.cuh"
 #include "step2_lam.cuh"
 
-#ifndef LBM_PAIR_32
-#define LBM_PAIR_32 0
-#endif
-
 namespace lbm {
 
 template <class U>
 static void launch_u(const StepParams &p, bool lam, int mode, dim3 grid, dim3 block,
                      cudaStream_t s) {
   if (mode == 0) {
-#if LBM_PAIR_32
-    if (lam) launch_pdl(step_pair_kernel<float, float, U, true>, pair_grid(grid, p.nx), block, s, p);
-    else launch_pdl(step_pair_kernel<float, float, U, false>, pair_grid(grid, p.nx), block, s, p);
-#else
     if (lam) launch_pdl(step_kernel<float, float, U, true, 0>, grid, block, s, p);
     else launch_pdl(step_kernel<float, float, U, false, 0>, grid, block, s, p);
-#endif
   } else {
     if (lam) step_kernel<float, float, U, true, 1><<<grid, block, 0, s>>>(p);
     else step_kernel<float, float, U, false, 1><<<grid, block, 0, s>>>(p);

@@ -86,15 +86,19 @@ def _assert_same(a, b, what):
 
 MODES = [("stream", 8, 0, 1), ("stream", 4, 1, 1), ("graph", 8, 1, 1), ("graph", 4, 0, 1),
          ("persistent", 8, 1, 1), ("persistent", 4, 0, 1),
-         ("stream", 8, 1, 2), ("graph", 8, 0, 2), ("persistent", 8, 1, 2)]
+         ("stream", 8, 1, 2), ("stream", 8, 0, 2), ("graph", 8, 0, 2), ("graph", 4, 1, 2),
+         ("persistent", 8, 1, 2), ("persistent", 8, 0, 2)]
 
 
-@pytest.mark.parametrize("storage", ["f64", "f32", "f16"])
-@pytest.mark.parametrize("mode,rows,order,cpt", MODES)
-def test_batch_equals_shots_alone(storage, mode, rows, order, cpt):
-    """Every launch form, tile height, order and cells per thread gives, bit
-    for bit, what each shot gives when stepped alone (the step of a cell does
-    not depend on the tile it is in, nor on the thread that updates it)."""
+@pytest.mark.parametrize("storage", ["f64", "f32", "f16", "bf16"])
+@pytest.mark.parametrize("mode,rows,order,tps", MODES)
+def test_batch_equals_shots_alone(storage, mode, rows, order, tps):
+    """Every launch form, tile height, order and number of time steps per
+    tile gives, bit for bit, what each shot gives when stepped alone (the
+    step of a cell does not depend on the tile it is in, nor on whether its
+    intermediate step went through shared memory).  23 steps: with two steps
+    per tile the odd one is a one-step launch; graphs of 5 launches and
+    persistent launches of 7 steps leave remainders."""
     ws = _shot_workloads(storage)
     alone = _make(ws, storage)
     for s in alone:
@@ -103,8 +107,8 @@ def test_batch_equals_shots_alone(storage, mode, rows, order, cpt):
     shots = _make(ws, storage)
     b = _pkg().Batch(shots)
     b.set_launch(mode=mode, rows=rows, order=order, graph_steps=5, steps_per_launch=7,
-                 cells_per_thread=cpt)
-    assert b.launch["cells_per_thread"] == cpt
+                 steps_per_tile=tps)
+    assert b.launch["steps_per_tile"] == tps
     b.step(23)
     b.sync()
     for i, s in enumerate(shots):
@@ -124,7 +128,7 @@ def test_batch_interleaved_with_single_steps():
     b.set_launch(mode="graph", graph_steps=3)
     b.step(5)
     shots[1].step(3)
-    b.set_launch(mode="persistent", steps_per_launch=2)
+    b.set_launch(mode="persistent", steps_per_launch=2, steps_per_tile=2)
     b.step(4)
     shots[0].step(3)
     shots[2].step(3)
@@ -154,17 +158,18 @@ def test_batch_matches_oracle():
 
 def test_batch_autotune_advances_and_matches():
     """The autotuner times every candidate on the batch itself: the shots
-    advance by (1 + trial) x 18 steps and still equal shots stepped alone."""
-    ws = _shot_workloads("f32", nsteps=60)
+    advance by (2 + trial, rounded up to even) x 18 steps and still equal
+    shots stepped alone."""
+    ws = _shot_workloads("f32", nsteps=80)
     shots = _make(ws, "f32")
     b = _pkg().Batch(shots)
-    us = b.autotune(2)
+    us = b.autotune(1)
     b.sync()
     assert us > 0
     assert b.launch["mode"] in ("stream", "graph", "persistent")
-    assert b.launch["cells_per_thread"] in (1, 2)
+    assert b.launch["steps_per_tile"] in (1, 2)
     n = shots[0].step_index
-    assert n == 54 and all(s.step_index == n for s in shots)
+    assert n == 72 and all(s.step_index == n for s in shots)
     alone = _make(ws, "f32")
     for s in alone:
         s.step(n)
@@ -224,6 +229,6 @@ def test_batch_rejects_mixed_storage_and_bad_launch():
     assert e.value.status == -1
     b = pkg.Batch([a])
     for bad in ({"rows": 16}, {"order": 2}, {"graph_steps": 0}, {"steps_per_launch": 0},
-                {"cells_per_thread": 3}, {"cells_per_thread": 2, "rows": 4}):
+                {"steps_per_tile": 3}, {"steps_per_tile": 0}):
         with pytest.raises(pkg.LBMError):
             b.set_launch(**bad)

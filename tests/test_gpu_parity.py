@@ -111,7 +111,7 @@ def _random_case(nx, ny, bc, sponge, nu_rows, per_cell, seed, storage, fs_order=
                        receivers=rec)
 
 
-STORAGE_KERNELS = [("f64", "simple"), ("f32", "simple"), ("f32", "tma")]
+STORAGE_KERNELS = [("f64", "simple"), ("f32", "simple")]
 
 
 @pytest.mark.parametrize("storage,kernel", STORAGE_KERNELS)
@@ -385,31 +385,6 @@ def test_per_row_equals_per_cell_material_bitwise():
         sim.step(7)
         out.append(sim.get_state())
     assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][1], out[1][1])
-
-
-@pytest.mark.parametrize("nu", [0.25, 0.3])
-def test_tma_kernel_equals_simple_kernel_layered(nu):
-    """The TMA-staged and the one-thread-per-cell FP32 kernels agree to a few
-    FP32 roundings on a layered half-space with sources and receivers, with
-    and without the density-gradient force, over 50 steps."""
-    wl = _wl()
-    w = wl.layered_halfspace(517, 133, 50, seed=9, sponge=12, nrec=16, storage="f32")
-    if nu == 0.25:
-        rho0, lam, mu = wl.homogeneous(w.ny, 0.25)
-        w = w.with_(rho0=rho0, lam=lam, mu=mu)
-    out = []
-    for kernel in ("simple", "tma"):
-        sim = _pkg().from_workload(w, kernel=kernel)
-        sim.step(w.nsteps)
-        out.append((sim.get_state(), sim.read_traces()))
-    (a, ua), ta = out[0]
-    (b, ub), tb = out[1]
-    assert max_rel(b, a) <= 1e-5 and max_rel(ub, ua) <= 1e-5 and max_rel(tb, ta) <= 1e-5
-
-
-def test_tma_kernel_needs_fp32():
-    with pytest.raises(_pkg().LBMError):
-        _pkg().ElasticLBM(64, 32, storage="f64", kernel="tma")
 
 
 # ------------------------------------------------------------ 16-bit storage

@@ -86,3 +86,26 @@ def test_create_rejects_bad_workspace(lib):
 def test_status_strings(lib):
     assert lib.lbm_elastic_status_string(-5) == b"LBM_ERR_NONFINITE"
     assert lib.lbm_elastic_status_string(0) == b"LBM_OK"
+
+
+def test_handle_less_error_message_is_per_thread(lib):
+    """Calls made without a handle keep their failure message per calling
+    thread, so two threads failing at once each read their own."""
+    import threading
+    c = _cfg()
+    need = lib.lbm_elastic_workspace_bytes(ctypes.byref(c))
+    got = {}
+    barrier = threading.Barrier(2)
+
+    def worker(name, ws, size):
+        h = ctypes.c_void_p()
+        barrier.wait()
+        for _ in range(200):
+            lib.lbm_elastic_create(ctypes.byref(c), ws, size, None, ctypes.byref(h))
+        got[name] = lib.lbm_elastic_last_error(None)
+
+    t1 = threading.Thread(target=worker, args=("null", None, need))
+    t2 = threading.Thread(target=worker, args=("small", 4096, need - 1))
+    t1.start(); t2.start(); t1.join(); t2.join()
+    assert b"NULL" in got["null"] and b"small" not in got["null"]
+    assert b"small" in got["small"] and b"NULL" not in got["small"]

@@ -26,29 +26,31 @@ def lib():
     return binding.load_library()
 
 
-@pytest.mark.parametrize("storage,code,tdtype", [("f64", 0, torch.float64),
-                                                  ("f32", 1, torch.float32)])
-def test_noalloc_sums_match_workspace_sums(lib, storage, code, tdtype):
+@pytest.mark.parametrize("storage,code,tdtype,u_fp64", [("f64", 0, torch.float64, 0),
+                                                         ("f32", 1, torch.float32, 0),
+                                                         ("f32", 1, torch.float32, 1)])
+def test_noalloc_sums_match_workspace_sums(lib, storage, code, tdtype, u_fp64):
     import paper_2009_06404_gb300 as pkg
     from paper_2009_06404_gb300 import workloads as wl
     nx, ny = 301, 170
     fs0, u0 = wl.random_state(nx, ny, seed=12)
-    sim = pkg.ElasticLBM(nx, ny, storage=storage)
+    sim = pkg.ElasticLBM(nx, ny, storage=storage, u_fp64=bool(u_fp64))
     sim.set_state(fs0, u0)
     ref = sim.moment_sums()
     # caller-held state with a padded row (pitch > nx); the padding holds
     # values that must not enter the sums
     pitch = 320
+    udtype = torch.float64 if (u_fp64 or storage == "f64") else tdtype
     f9 = torch.full((9, ny, pitch), 7.0, dtype=tdtype, device="cuda")
-    u2 = torch.full((2, ny, pitch), 7.0, dtype=tdtype, device="cuda")
+    u2 = torch.full((2, ny, pitch), 7.0, dtype=udtype, device="cuda")
     f9[:, :, :nx] = torch.tensor(fs0, dtype=tdtype)
-    u2[:, :, :nx] = torch.tensor(u0, dtype=tdtype)
+    u2[:, :, :nx] = torch.tensor(u0, dtype=udtype)
     stream = torch.cuda.current_stream().cuda_stream
     scale = np.abs(ref) + 1e-300
     for _ in range(2):
         out = (ctypes.c_double * 7)()
-        st = lib.lbm_elastic_moment_sums_noalloc(f9.data_ptr(), u2.data_ptr(), code, 0, nx, ny,
-                                                 pitch, ctypes.addressof(out), 0, stream)
+        st = lib.lbm_elastic_moment_sums_noalloc(f9.data_ptr(), u2.data_ptr(), code, u_fp64, nx,
+                                                 ny, pitch, ctypes.addressof(out), 0, stream)
         assert st == 0, lib.lbm_elastic_last_error(None)
         got = np.array(out[:])
         assert np.all(np.abs(got - ref) <= 1e-12 * scale), (got, ref)
@@ -56,8 +58,8 @@ def test_noalloc_sums_match_workspace_sums(lib, storage, code, tdtype):
     dev_out = torch.zeros(7, dtype=torch.float64, device="cuda")
     for _ in range(2):
         dev_out.zero_()
-        st = lib.lbm_elastic_moment_sums_noalloc(f9.data_ptr(), u2.data_ptr(), code, 0, nx, ny,
-                                                 pitch, dev_out.data_ptr(), 1, stream)
+        st = lib.lbm_elastic_moment_sums_noalloc(f9.data_ptr(), u2.data_ptr(), code, u_fp64, nx,
+                                                 ny, pitch, dev_out.data_ptr(), 1, stream)
         assert st == 0
         torch.cuda.synchronize()
         assert np.all(np.abs(dev_out.cpu().numpy() - ref) <= 1e-12 * scale)
