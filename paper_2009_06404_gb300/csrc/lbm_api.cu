@@ -105,6 +105,10 @@ Layout make_layout(const lbm_elastic_config *c) {
   L.tiles2x = (c->nx + kF2Cols - 1) / kF2Cols;
   L.tiles2y = (c->ny + kF2Rows - 1) / kF2Rows;
   L.done = take((size_t)L.tiles2x * L.tiles2y * sizeof(unsigned));
+  L.ntiles2 = (long long)L.tiles2x * L.tiles2y;
+  L.ntiles2l = (long long)((c->nx + kL2Cols - 1) / kL2Cols) * ((c->ny + kL2Rows - 1) / kL2Rows);
+  L.order2 = take((size_t)L.ntiles2 * sizeof(int2));
+  L.order2l = take((size_t)L.ntiles2l * sizeof(int2));
   size_t stage = (size_t)L.stage_rows * c->nx * 11 * sizeof(double);
   size_t mat_stage = (size_t)3 * c->ny * sizeof(double);
   L.stage = take(stage > mat_stage ? stage : mat_stage);
@@ -308,6 +312,73 @@ double store_scale(const lbm_elastic_config &c) {
                                                          : 1.0;
 }
 
+// The two-step tiles of one geometry (W x H cells; m: the distance to an
+// edge or seam within which a tile takes a slower path) in launch order:
+// the tiles near an edge or seam, that a source footprint reaches, or that
+// hold a receiver first, then the others, each group in row-major order.
+// Appends to out; returns the size of the first group.  Only the order of
+// the work depends on it, never a result.
+int order_tiles(const lbm_elastic_t *h, int W, int H, int m, std::vector<int2> &out) {
+  const int nx = h->cfg.nx, ny = h->cfg.ny;
+  const bool perx = h->cfg.bc_left == LBM_BC_PERIODIC, pery = h->cfg.bc_top == LBM_BC_PERIODIC;
+  const int gx = (nx + W - 1) / W, gy = (ny + H - 1) / H;
+  std::vector<char> slow((size_t)gx * gy, 0);
+  for (int by = 0; by < gy; ++by)
+    for (int bx = 0; bx < gx; ++bx) {
+      const int x0 = bx * W, y0 = by * H;
+      if (x0 < m || x0 + W > nx - m || y0 < m || y0 + H > ny - m) slow[(size_t)by * gx + bx] = 1;
+    }
+  // tile indices along one axis whose cells, widened by m + 1, overlap
+  // [lo, hi] (wrapped on a periodic axis, each at most once)
+  auto span = [](long long lo, long long hi, int T, int g, bool per, std::vector<int> &v) {
+    v.clear();
+    const long long a = lo >= 0 ? lo / T : -((-lo + T - 1) / T);
+    const long long b = hi >= 0 ? hi / T : -((-hi + T - 1) / T);
+    for (long long t = a; t <= b && (long long)v.size() < g; ++t) {
+      long long k = t;
+      if (per) k = ((k % g) + g) % g;
+      else if (k < 0 || k >= g) continue;
+      v.push_back((int)k);
+    }
+  };
+  std::vector<int> xs, ys;
+  for (const SourceDev &q : h->src_host) {
+    span((long long)q.xc - q.rb - m - 1, (long long)q.xc + q.rb + m + 1, W, gx, perx, xs);
+    span((long long)q.yc - q.rb - m - 1, (long long)q.yc + q.rb + m + 1, H, gy, pery, ys);
+    for (int ty : ys)
+      for (int tx : xs) slow[(size_t)ty * gx + tx] = 1;
+  }
+  for (size_t r = 0; 2 * r + 1 < h->rec_host.size(); ++r)
+    slow[(size_t)(h->rec_host[2 * r + 1] / H) * gx + h->rec_host[2 * r] / W] = 1;
+  int first = 0;
+  for (int pass = 0; pass < 2; ++pass)
+    for (int by = 0; by < gy; ++by)
+      for (int bx = 0; bx < gx; ++bx)
+        if ((slow[(size_t)by * gx + bx] != 0) == (pass == 0)) {
+          out.push_back(make_int2(bx, by));
+          if (pass == 0) ++first;
+        }
+  return first;
+}
+
+// Builds both tile order lists and copies them into the workspace on the
+// handle's stream (the host copy stays in the handle).
+lbm_status upload_tile_order(lbm_elastic_t *h) {
+  std::vector<int2> &o = h->order_host;
+  o.clear();
+  h->order2_first = order_tiles(h, kF2Cols, kF2Rows, 2, o);
+  h->order2l_first = order_tiles(h, kL2Cols, kL2Rows, 4, o);
+  const Layout &L = h->L;
+  if ((long long)o.size() != L.ntiles2 + L.ntiles2l)
+    return fail(h, LBM_ERR_CUDA, "internal: tile order lists of the wrong size");
+  LBM_CUDA(h, cudaMemcpyAsync(h->ws + L.order2, o.data(), (size_t)L.ntiles2 * sizeof(int2),
+                              cudaMemcpyHostToDevice, h->stream));
+  LBM_CUDA(h, cudaMemcpyAsync(h->ws + L.order2l, o.data() + L.ntiles2,
+                              (size_t)L.ntiles2l * sizeof(int2), cudaMemcpyHostToDevice,
+                              h->stream));
+  return LBM_OK;
+}
+
 StepParams base_params(lbm_elastic_t *h) {
   const lbm_elastic_config &c = h->cfg;
   const Layout &L = h->L;
@@ -356,6 +427,10 @@ StepParams base_params(lbm_elastic_t *h) {
   p.n = h->step;
   p.trace_slot = -1;
   p.trace_end = h->cfg.max_steps_traced;
+  p.tiles2 = at<int2>(h, L.order2);
+  p.tiles2l = at<int2>(h, L.order2l);
+  p.tiles2_first = h->order2_first;
+  p.tiles2l_first = h->order2l_first;
   p.rec_tile_ptr = at<int>(h, L.rec_ptr);
   p.rec_xy = at<int>(h, L.rec_xy);
   p.rec_id = at<int>(h, L.rec_id);
@@ -632,6 +707,7 @@ lbm_status lbm_elastic_create(const lbm_elastic_config *cfg, void *d_workspace,
     }
     s = check_launch(h, "material fill launch");
   }
+  if (s == LBM_OK) s = upload_tile_order(h);
   if (s == LBM_OK) {
     cudaError_t e = cudaMemsetAsync(h->ws + L.rec_ptr, 0, ((size_t)L.rec_tiles + 1) * sizeof(int),
                                     h->stream);
@@ -757,7 +833,7 @@ lbm_status lbm_elastic_set_sources(lbm_elastic_t *h, const lbm_source *src, int 
                                 cudaMemcpyHostToDevice, h->stream));
   LBM_CUDA(h, cudaStreamSynchronize(h->stream));
   h->nsrc = n;
-  return LBM_OK;
+  return upload_tile_order(h);
 }
 
 lbm_status lbm_elastic_set_sponges(lbm_elastic_t *h, int top, int bottom, int left, int right,
@@ -819,7 +895,8 @@ lbm_status lbm_elastic_set_receivers(lbm_elastic_t *h, const int *xy, int n) {
   }
   h->nrec = n;
   h->traced = 0;
-  return LBM_OK;
+  h->rec_host.assign(xy, xy + 2 * (size_t)n);
+  return upload_tile_order(h);
 }
 
 lbm_status lbm_elastic_reset(lbm_elastic_t *h) {

@@ -22,6 +22,8 @@ struct Layout {
   int rec_tiles_x = 0, rec_tiles = 0, stage_rows = 0;
   size_t done = 0;                // persistent two-step form: per-tile phase counters
   int tiles2x = 0, tiles2y = 0;   // its tiles per row and per column
+  size_t order2 = 0, order2l = 0; // two-step tiles in launch order (int2), both geometries
+  long long ntiles2 = 0, ntiles2l = 0;
   long long mat_count = 0;
 };
 
@@ -45,6 +47,9 @@ struct lbm_elastic {
   int persist_blocks = -1;     // resident blocks per SM of the persistent kernel (-1: unknown)
   long long launches = 0;
   std::vector<lbm::SourceDev> src_host;
+  std::vector<int> rec_host;        // receivers (x, y), as set
+  std::vector<int2> order_host;     // the tile order lists last uploaded
+  int order2_first = 0, order2l_first = 0;
   int src_box[4] = {0, -1, 0, -1};  // x0, x1, y0, y1 of all source footprints
   int rec_box[4] = {0, -1, 0, -1};  // x0, x1, y0, y1 of all receivers
   std::string err;

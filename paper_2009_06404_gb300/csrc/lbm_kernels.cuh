@@ -90,6 +90,13 @@ struct StepParams {
   // every cell is stored here, x component then y component plane
   // ([2][ny][pitch], compute type)
   void *grad_out;
+  // two-step launches: each block's tile from a list in launch order -- the
+  // [first] tiles that take a slower path (near an edge or seam, a source or
+  // a receiver) first, then the others in row-major order, reversed when
+  // reverse is set; one list per tile geometry (without and with the
+  // density-gradient force)
+  const int2 *tiles2, *tiles2l;
+  int tiles2_first, tiles2l_first;
   // fields mode only
   int row0, nrows;
   double *out[8];           // ux uy vx vy rho pxx pxy pyy, [nrows][nx] each

@@ -343,8 +343,8 @@ __device__ __forceinline__ void step2_lam_tile(const StepParams &p, int bx, int 
 }
 
 // Steps n = p.n and n + 1 from p.fin to p.fout with the density-gradient
-// force, one block of 32 x kL2H threads per 28 x kL2Rows tile.  p.reverse:
-// the tiles in reverse order (the top tile row still first).
+// force, one block of 32 x kL2H threads per 28 x kL2Rows tile (the tiles in
+// the order of p.tiles2l).
 template <class T, class C, class U>
 __global__ void __launch_bounds__(32 * kL2H, LBM_STEP2L_MIN_BLOCKS)
     step2_lam_kernel(const StepParams p) {
@@ -354,16 +354,12 @@ __global__ void __launch_bounds__(32 * kL2H, LBM_STEP2L_MIN_BLOCKS)
 #endif
   __shared__ T tile[9 * kL2H * kL2W];
   __shared__ C rho_s[kL2RH][kL2RW];
-  int bx = blockIdx.x, by = blockIdx.y;
-  if (p.reverse) {
-    if (by > 0) by = gridDim.y - by;
-    bx = gridDim.x - 1 - bx;
-  }
-  step2_lam_tile<T, C, U>(p, bx, by, tile, rho_s);
+  const int2 t = tile_of_block(p.tiles2l, p.tiles2l_first, gridDim.x, blockIdx.x, p.reverse);
+  step2_lam_tile<T, C, U>(p, t.x, t.y, tile, rho_s);
 }
 
 inline dim3 step2_lam_grid(int nx, int ny) {
-  return dim3((nx + kL2Cols - 1) / kL2Cols, (ny + kL2Rows - 1) / kL2Rows, 1);
+  return dim3(((nx + kL2Cols - 1) / kL2Cols) * ((ny + kL2Rows - 1) / kL2Rows), 1, 1);
 }
 inline dim3 step2_lam_block() { return dim3(32, kL2H, 1); }
 

@@ -441,10 +441,21 @@ __device__ __forceinline__ void step2_tile(const StepParams &p, int bx, int by, 
   if (!((M.rho + jx + jy) * C(0) == C(0))) atomicOr(p.err, 1);
 }
 
+// The tile of block b of a two-step launch: list[b] for the first `first`
+// blocks (the tiles that take a slower path start first, so their longer
+// run overlaps the bulk instead of trailing the launch), then the rest of
+// the list in order, or in reverse order when `reverse` is set (alternate
+// launches: the rows written last by one launch, still in L2, are the first
+// the next one reads).  One block per tile (n blocks).
+__device__ __forceinline__ int2 tile_of_block(const int2 *list, int first, int n, int b,
+                                              int reverse) {
+  if (reverse && b >= first) b = first + (n - 1 - b);
+  return list[b];
+}
+
 // Steps n = p.n and n + 1 from p.fin to p.fout, one block per kF2Cols x
-// kF2Rows tile; blocks of 32 x kF2Warps threads.  p.reverse: visit the
-// tiles in the reverse order (the top tile row still first), as the
-// one-step kernel does on alternate steps.
+// kF2Rows tile (the tiles in the order of p.tiles2); blocks of 32 x
+// kF2Warps threads.
 template <class T, class C, class U>
 __global__ void __launch_bounds__(32 * kF2Warps, LBM_STEP2_MIN_BLOCKS)
     step2_kernel(const StepParams p) {
@@ -453,12 +464,8 @@ __global__ void __launch_bounds__(32 * kF2Warps, LBM_STEP2_MIN_BLOCKS)
   asm volatile("griddepcontrol.launch_dependents;");
 #endif
   __shared__ T tile[9 * kF2H * kF2W];
-  int bx = blockIdx.x, by = blockIdx.y;
-  if (p.reverse) {
-    if (by > 0) by = gridDim.y - by;
-    bx = gridDim.x - 1 - bx;
-  }
-  step2_tile<T, C, U>(p, bx, by, tile, 0);
+  const int2 t = tile_of_block(p.tiles2, p.tiles2_first, gridDim.x, blockIdx.x, p.reverse);
+  step2_tile<T, C, U>(p, t.x, t.y, tile, 0);
 }
 
 // ------------------------------------------------------------ persistent form
@@ -554,9 +561,10 @@ __global__ void __launch_bounds__(32 * kF2Warps, LBM_STEP2_MIN_BLOCKS)
   }
 }
 
-// Launch configuration of the two-step kernel for an nx x ny grid.
+// Launch configuration of the two-step kernel for an nx x ny grid: one
+// block per tile.
 inline dim3 step2_grid(int nx, int ny) {
-  return dim3((nx + kF2Cols - 1) / kF2Cols, (ny + kF2Rows - 1) / kF2Rows, 1);
+  return dim3(((nx + kF2Cols - 1) / kF2Cols) * ((ny + kF2Rows - 1) / kF2Rows), 1, 1);
 }
 inline dim3 step2_block() { return dim3(32, kF2Warps, 1); }
 
