@@ -428,6 +428,36 @@ __device__ __forceinline__ C gtot_s(const AdjSmem<C> &S, bool lam_any, int hx, i
   return g;
 }
 
+// Block b of a gx x gy grid of blocks, the blocks on the grid's edge first
+// (their cells take the wall rules and hold the receivers: they run longer,
+// and started last they would trail the launch), then the interior ones in
+// row-major order.
+__device__ __forceinline__ void edge_blocks_first(int b, int gx, int gy, int &bx, int &by) {
+  if (gx < 3 || gy < 3) {
+    bx = b % gx;
+    by = b / gx;
+    return;
+  }
+  const int side = gy - 2, per = 2 * gx + 2 * side;
+  if (b < gx) {
+    bx = b;
+    by = 0;
+  } else if (b < 2 * gx) {
+    bx = b - gx;
+    by = gy - 1;
+  } else if (b < 2 * gx + side) {
+    bx = 0;
+    by = 1 + (b - 2 * gx);
+  } else if (b < per) {
+    bx = gx - 1;
+    by = 1 + (b - 2 * gx - side);
+  } else {
+    const int i = b - per;
+    bx = 1 + i % (gx - 2);
+    by = 1 + i / (gx - 2);
+  }
+}
+
 template <class C>
 __global__ void __launch_bounds__(kAdjThreads, LBM_ADJ_MIN_BLOCKS) adj_fused_kernel(const AdjParams a) {
 #if LBM_PDL
@@ -440,7 +470,10 @@ __global__ void __launch_bounds__(kAdjThreads, LBM_ADJ_MIN_BLOCKS) adj_fused_ker
   const StepParams &p = a.p;
   __shared__ AdjSmem<C> S;
   const int t = threadIdx.y * 32 + threadIdx.x;
-  const int x0 = blockIdx.x * kAdjTW, y0 = blockIdx.y * kAdjTH;
+  int bxi, byi;
+  edge_blocks_first(blockIdx.x, (p.nx + kAdjTW - 1) / kAdjTW, (p.ny + kAdjTH - 1) / kAdjTH, bxi,
+                    byi);
+  const int x0 = bxi * kAdjTW, y0 = byi * kAdjTH;
   const bool perx = p.bc_left == BC_PERIODIC, pery = p.bc_top == BC_PERIODIC;
   const bool src_blk = a.g_amp != nullptr && p.nsrc > 0 && x0 <= p.src_x1 &&
                        x0 + kAdjTW - 1 >= p.src_x0 && y0 <= p.src_y1 &&
@@ -620,7 +653,7 @@ cudaError_t adj_step_t(const AdjParams &a, bool fused, cudaStream_t s) {
   const dim3 block(32, 8), grid((a.p.nx + 31) / 32, (a.p.ny + 7) / 8);
   if (fused) {
     cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(grid.x, (a.p.ny + kAdjTH - 1) / kAdjTH);
+    cfg.gridDim = dim3(grid.x * ((a.p.ny + kAdjTH - 1) / kAdjTH));
     cfg.blockDim = dim3(32, kAdjTH);
     cfg.stream = s;
     cudaLaunchAttribute attr[1];

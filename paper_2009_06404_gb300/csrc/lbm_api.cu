@@ -803,24 +803,26 @@ lbm_status lbm_elastic_set_sources(lbm_elastic_t *h, const lbm_source *src, int 
     q.ax_f = (float)q.ax;
     q.ay_f = (float)q.ay;
   }
-  // bounding box of every footprint (the whole axis when it wraps around)
+  // bounding box of every footprint: clipped to the grid on a non-periodic
+  // axis, the whole axis when it wraps around a periodic one
   int bx0 = h->cfg.nx, bx1 = -1, by0 = h->cfg.ny, by1 = -1;
+  const bool perx = h->cfg.bc_left == LBM_BC_PERIODIC, pery = h->cfg.bc_top == LBM_BC_PERIODIC;
   for (const SourceDev &q : v) {
     const long long lo_x = (long long)q.xc - q.rb, hi_x = (long long)q.xc + q.rb;
     const long long lo_y = (long long)q.yc - q.rb, hi_y = (long long)q.yc + q.rb;
-    if (lo_x < 0 || hi_x >= h->cfg.nx) {
+    if (perx && (lo_x < 0 || hi_x >= h->cfg.nx)) {
       bx0 = 0;
       bx1 = h->cfg.nx - 1;
     } else {
-      bx0 = std::min<long long>(bx0, lo_x);
-      bx1 = std::max<long long>(bx1, hi_x);
+      bx0 = (int)std::min<long long>(bx0, std::max<long long>(lo_x, 0));
+      bx1 = (int)std::max<long long>(bx1, std::min<long long>(hi_x, h->cfg.nx - 1));
     }
-    if (lo_y < 0 || hi_y >= h->cfg.ny) {
+    if (pery && (lo_y < 0 || hi_y >= h->cfg.ny)) {
       by0 = 0;
       by1 = h->cfg.ny - 1;
     } else {
-      by0 = std::min<long long>(by0, lo_y);
-      by1 = std::max<long long>(by1, hi_y);
+      by0 = (int)std::min<long long>(by0, std::max<long long>(lo_y, 0));
+      by1 = (int)std::max<long long>(by1, std::min<long long>(hi_y, h->cfg.ny - 1));
     }
   }
   h->src_box[0] = bx0;

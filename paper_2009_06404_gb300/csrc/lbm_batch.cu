@@ -201,7 +201,26 @@ lbm_status upload_tiles2(lbm_batch_t *b, int order) {
   std::vector<char> lam(b->shots.size());
   for (size_t s = 0; s < b->shots.size(); ++s) lam[s] = b->shots[s]->lambda_nonzero ? 1 : 0;
   if (b->tiles2_order == order && b->tiles2_lam == lam) return LBM_OK;
-  list_tiles(b, order, [](const lbm_elastic_t *h, int *W, int *H) { tile2_size(h, W, H); });
+  if (order == 1) {
+    // every shot's slower tiles first (its own launch order: near an edge or
+    // seam, a source or a receiver), then the others
+    std::vector<int4> &t = b->tile_host;
+    t.clear();
+    for (int pass = 0; pass < 2; ++pass)
+      for (int s = 0; s < (int)b->shots.size(); ++s) {
+        const lbm_elastic_t *h = b->shots[s];
+        const size_t base = h->lambda_nonzero ? (size_t)h->L.ntiles2 : 0;
+        const size_t count = h->lambda_nonzero ? (size_t)h->L.ntiles2l : (size_t)h->L.ntiles2;
+        const size_t first = h->lambda_nonzero ? h->order2l_first : h->order2_first;
+        const size_t a = pass == 0 ? 0 : first, e = pass == 0 ? first : count;
+        for (size_t k = a; k < e; ++k) {
+          const int2 q = h->order_host[base + k];
+          t.push_back(make_int4(s, q.x, q.y, 0));
+        }
+      }
+  } else {
+    list_tiles(b, order, [](const lbm_elastic_t *h, int *W, int *H) { tile2_size(h, W, H); });
+  }
   b->ntiles2 = (int)b->tile_host.size();
   BATCH_CUDA(b, cudaMemcpyAsync(b->ws + b->off.tiles2, b->tile_host.data(),
                                 b->tile_host.size() * sizeof(int4), cudaMemcpyHostToDevice,

@@ -200,52 +200,83 @@ struct GridPops {
 // Moments rho and the diagonal stress components of the post-collision
 // populations at one in-domain cell (the collision conserves rho and P, so
 // these equal the moments at time t of Eqs. 39-42).
+// rho and the diagonal stress components of nine populations (the sums in
+// one fixed order on every path).
+template <class C>
+__device__ __forceinline__ void rho_pdiag(const C *v, C &rho, C &pxx, C &pyy) {
+  rho = v[0] + v[1] + v[2] + v[3] + v[4] + v[5] + v[6] + v[7] + v[8];
+  pxx = v[1] + v[3] + v[5] + v[6] + v[7] + v[8];
+  pyy = v[2] + v[4] + v[5] + v[6] + v[7] + v[8];
+}
+
 template <class T, class C, class A>
 __device__ void cell_rho_pdiag(const StepParams &p, const A &a, int x, int y, C &rho, C &pxx,
                                C &pyy) {
   C v[9];
 #pragma unroll
   for (int i = 0; i < 9; ++i) v[i] = a.template load<C>(i, x, y);
-  rho = v[0] + v[1] + v[2] + v[3] + v[4] + v[5] + v[6] + v[7] + v[8];
-  pxx = v[1] + v[3] + v[5] + v[6] + v[7] + v[8];
-  pyy = v[2] + v[4] + v[5] + v[6] + v[7] + v[8];
+  rho_pdiag<C>(v, rho, pxx, pyy);
+}
+
+// The air state of a free-surface wall with outward normal (nxo, nyo)
+// (Eqs. 37-42): rho_air and P^n_air = P_air - rho_air b^2 I, P_air keeping
+// only the tangential stress (P_xx on a horizontal wall, P_yy on a vertical
+// one), from the moments of the boundary cell (b) and, for the linear
+// extrapolation half a cell out (Eq. 39), of the cell inside it (i).
+template <class C>
+struct AirState {
+  C rho_air, pnxx, pnyy;
+};
+template <class C>
+__device__ __forceinline__ AirState<C> air_state(const StepParams &p, int nyo, C rb, C pxxb,
+                                                 C pyyb, C ri, C pxxi, C pyyi) {
+  // The products and sums are rounded in a fixed order (explicit fused
+  // multiply-adds), so the value does not depend on how the compiler
+  // contracts the expression where the link is a constant (an unrolled
+  // caller) or a run-time value.
+  AirState<C> s;
+  C ptan;  // tangential stress: P_xx on a horizontal wall, P_yy on a vertical one
+  if (p.fs_order == 1) {
+    // 0.5 x is exact
+    s.rho_air = fma_rn(C(1.5), rb, C(-0.5) * ri);
+    ptan = nyo != 0 ? fma_rn(C(1.5), pxxb, C(-0.5) * pxxi) : fma_rn(C(1.5), pyyb, C(-0.5) * pyyi);
+  } else {
+    // constant extrapolation: the boundary cell's own values
+    s.rho_air = rb;
+    ptan = nyo != 0 ? pxxb : pyyb;
+  }
+  const C third = C(1.0 / 3.0);
+  s.pnxx = fma_rn(-s.rho_air, third, nyo != 0 ? ptan : C(0));
+  s.pnyy = fma_rn(-s.rho_air, third, nyo != 0 ? C(0) : ptan);
+  return s;
+}
+
+// Anti-bounce-back value of the population entering opposite to k, whose
+// outgoing post-collision population is fk: -f*_k + 2 w_k (rho_air +
+// P^n_air : H_k / (2 b^4)) (Eq. 38).
+template <class C>
+__device__ __forceinline__ C abb_value(const AirState<C> &s, int k, C fk) {
+  const C third = C(1.0 / 3.0);
+  const int cx = cxd(k), cy = cyd(k);
+  const C h = fma_rn(C(cx * cx) - third, s.pnxx, mul_rn(C(cy * cy) - third, s.pnyy));
+  return fma_rn(C(2) * wd<C>(k), fma_rn(C(4.5), h, s.rho_air), -fk);
 }
 
 // Population i entering boundary cell (x, y) through a wall of kind bc with
 // outward normal (nxo, nyo).  Rigid: half-way bounce-back (Eq. 36).  Free
 // surface: anti-bounce-back with rho_air and the tangential stress
-// extrapolated linearly from x_b and x_in = x_b - n; P_air has no other
-// component (Eqs. 37-42).
+// extrapolated from x_b and x_in = x_b - n; P_air has no other component
+// (Eqs. 37-42).
 template <class T, class C, class A>
 __device__ C wall_value(const StepParams &p, const A &a, int bc, int nxo, int nyo, int i, int x,
                         int y) {
   const int k = oppd(i);
   const C fk = a.template load<C>(k, x, y);
   if (bc == BC_RIGID) return fk;
-  C rb, pxxb, pyyb, ri, pxxi, pyyi;
+  C rb, pxxb, pyyb, ri = C(0), pxxi = C(0), pyyi = C(0);
   cell_rho_pdiag<T, C>(p, a, x, y, rb, pxxb, pyyb);
-  // The products and sums are rounded in a fixed order (explicit fused
-  // multiply-adds), so the value does not depend on how the compiler
-  // contracts the expression where the link i is a constant (an unrolled
-  // caller) or a run-time value.
-  C rho_air, ptan;  // tangential stress: P_xx on a horizontal wall, P_yy on a vertical one
-  if (p.fs_order == 1) {
-    // linear extrapolation half a cell out (Eq. 39); 0.5 x is exact
-    cell_rho_pdiag<T, C>(p, a, x - nxo, y - nyo, ri, pxxi, pyyi);
-    rho_air = fma_rn(C(1.5), rb, C(-0.5) * ri);
-    ptan = nyo != 0 ? fma_rn(C(1.5), pxxb, C(-0.5) * pxxi)
-                    : fma_rn(C(1.5), pyyb, C(-0.5) * pyyi);
-  } else {
-    // constant extrapolation: the boundary cell's own values
-    rho_air = rb;
-    ptan = nyo != 0 ? pxxb : pyyb;
-  }
-  const C third = C(1.0 / 3.0);
-  const C pnxx = fma_rn(-rho_air, third, nyo != 0 ? ptan : C(0));
-  const C pnyy = fma_rn(-rho_air, third, nyo != 0 ? C(0) : ptan);
-  const int cx = cxd(k), cy = cyd(k);
-  const C h = fma_rn(C(cx * cx) - third, pnxx, mul_rn(C(cy * cy) - third, pnyy));
-  return fma_rn(C(2) * wd<C>(k), fma_rn(C(4.5), h, rho_air), -fk);
+  if (p.fs_order == 1) cell_rho_pdiag<T, C>(p, a, x - nxo, y - nyo, ri, pxxi, pyyi);
+  return abb_value<C>(air_state<C>(p, nyo, rb, pxxb, pyyb, ri, pxxi, pyyi), k, fk);
 }
 
 // Pull of population i into (x, y) on a boundary cell (general path): the
@@ -280,6 +311,71 @@ __device__ __noinline__ C pull_general(const StepParams &p, const T *f, int i, i
   return pull_general_a<T, C>(p, GridPops<T>{f, p.fplane, p.frow}, i, x, y);
 }
 
+// pull_general_a out of line, for any population source.
+template <class T, class C, class A>
+__device__ __noinline__ C pull_link(const StepParams &p, const A a, int i, int x, int y) {
+  return pull_general_a<T, C>(p, a, i, x, y);
+}
+
+// All nine streamed populations of the in-grid cell (x, y) by the rules of
+// pull_general_a (wrapped pulls across periodic seams, the wall rule for
+// links that cross a non-periodic edge), with every load issued before any
+// wall value is formed: a cell on one wall loads its own nine post-collision
+// populations (and, for the linear free-surface rule, those of the cell
+// inside it) once and forms the air state once for its three wall links.
+// The values are those of pull_general_a, bit for bit.  A cell on two walls
+// (a corner) takes the per-link rule.  Out of line: the register budget of
+// the step kernels' bulk paths stays the budget of this function too.
+template <class T, class C, class A>
+__device__ __noinline__ void pull_cell(const StepParams &p, const A a, int x, int y, C *f) {
+  const bool wt = y == 0 && p.bc_top != BC_PERIODIC;
+  const bool wb = y == p.ny - 1 && p.bc_bottom != BC_PERIODIC;
+  const bool wl = x == 0 && p.bc_left != BC_PERIODIC;
+  const bool wr = x == p.nx - 1 && p.bc_right != BC_PERIODIC;
+  const int nw = (int)wt + (int)wb + (int)wl + (int)wr;
+  if (nw > 1) {
+#pragma unroll
+    for (int i = 0; i < 9; ++i) f[i] = pull_link<T, C, A>(p, a, i, x, y);
+    return;
+  }
+  // pulls that cross no wall (wrapped across periodic seams)
+  const int nxo = wl ? -1 : (wr ? 1 : 0), nyo = wt ? -1 : (wb ? 1 : 0);
+#pragma unroll
+  for (int i = 0; i < 9; ++i) {
+    if (cxd(i) * nxo + cyd(i) * nyo < 0) continue;  // crosses the wall
+    int sx = x - cxd(i), sy = y - cyd(i);
+    if (A::kWrap) {
+      sx = sx < 0 ? sx + p.nx : (sx >= p.nx ? sx - p.nx : sx);
+      sy = sy < 0 ? sy + p.ny : (sy >= p.ny ? sy - p.ny : sy);
+    }
+    f[i] = a.template load<C>(i, sx, sy);
+  }
+  if (nw == 0) return;
+  // the three links through the wall
+  const int bc = wt ? p.bc_top : (wb ? p.bc_bottom : (wl ? p.bc_left : p.bc_right));
+  C own[9];
+#pragma unroll
+  for (int k = 0; k < 9; ++k) own[k] = a.template load<C>(k, x, y);
+  if (bc == BC_RIGID) {
+#pragma unroll
+    for (int i = 0; i < 9; ++i)
+      if (cxd(i) * nxo + cyd(i) * nyo < 0) f[i] = own[oppd(i)];
+    return;
+  }
+  C rb, pxxb, pyyb, ri = C(0), pxxi = C(0), pyyi = C(0);
+  if (p.fs_order == 1) {
+    C inn[9];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) inn[k] = a.template load<C>(k, x - nxo, y - nyo);
+    rho_pdiag<C>(inn, ri, pxxi, pyyi);
+  }
+  rho_pdiag<C>(own, rb, pxxb, pyyb);
+  const AirState<C> air = air_state<C>(p, nyo, rb, pxxb, pyyb, ri, pxxi, pyyi);
+#pragma unroll
+  for (int i = 0; i < 9; ++i)
+    if (cxd(i) * nxo + cyd(i) * nyo < 0) f[i] = abb_value<C>(air, oppd(i), own[oppd(i)]);
+}
+
 // All nine streamed populations of (x, y).
 template <class T, class C>
 __device__ __forceinline__ void gather(const StepParams &p, const T *f, int x, int y, C *fo) {
@@ -288,8 +384,7 @@ __device__ __forceinline__ void gather(const StepParams &p, const T *f, int x, i
 #pragma unroll
     for (int i = 0; i < 9; ++i) fo[i] = ldp<T, C>(b + (i * p.fplane - cyd(i) * p.frow - cxd(i)), p);
   } else {
-#pragma unroll
-    for (int i = 0; i < 9; ++i) fo[i] = pull_general<T, C>(p, f, i, x, y);
+    pull_cell<T, C>(p, GridPops<T>{f, p.fplane, p.frow}, x, y, fo);
   }
 }
 
@@ -668,7 +763,7 @@ __device__ __noinline__ void boundary_cell(const StepParams &p, C Fx, C Fy, int 
   const T *fin = (const T *)p.fin;
   C f[9];
 #pragma unroll
-  for (int i = 0; i < 9; ++i) f[i] = pull_general<T, C>(p, fin, i, xc, yc);
+  pull_cell<T, C>(p, GridPops<T>{fin, p.fplane, p.frow}, xc, yc, f);
   C gx = C(0), gy = C(0);
   if (LAM) {
     const C rho = f[0] + f[1] + f[2] + f[3] + f[4] + f[5] + f[6] + f[7] + f[8];

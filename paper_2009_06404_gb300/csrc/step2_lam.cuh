@@ -104,12 +104,6 @@ struct LamTilePops {
   }
 };
 
-template <class T, class C>
-__device__ __noinline__ C pull_general_lam_tile(const StepParams &p, const T *tile, int ox, int oy,
-                                                int i, int x, int y) {
-  return pull_general_a<T, C>(p, LamTilePops<T>{tile, ox, oy}, i, x, y);
-}
-
 // With p.grad_out set (the adjoint's recording runs): the centred density
 // gradient of step n + k (k = 0, 1) of cell index c, into the k-th of two
 // consecutive records of two planes each ([2][2][ny][pitch], compute type),
@@ -288,9 +282,7 @@ __device__ __noinline__ void lam_general(const StepParams &p, const Phase2 &ph, 
         for (int i = 0; i < 9; ++i)
           f[i] = ld<T, C>(tile + ((i * kL2H + w - cyd(i)) * kL2W + lane - cxd(i)));
       } else {
-#pragma unroll
-        for (int i = 0; i < 9; ++i)
-          f[i] = pull_general_lam_tile<T, C>(p, tile, x0 - 2, y0 - 2, i, x, y);
+        pull_cell<T, C>(p, LamTilePops<T>{tile, x0 - 2, y0 - 2}, x, y, f);
       }
       rho = f[0] + f[1] + f[2] + f[3] + f[4] + f[5] + f[6] + f[7] + f[8];
     }

@@ -71,13 +71,6 @@ struct TilePops {
   }
 };
 
-// Pull of population i into (x, y) from the window (general path; out of
-// line like the global-memory pull_general).
-template <class T, class C>
-__device__ __noinline__ C pull_general_tile(const StepParams &p, const T *tile, int ox, int oy,
-                                            int i, int x, int y) {
-  return pull_general_a<T, C>(p, TilePops<T>{tile, ox, oy}, i, x, y);
-}
 
 // What changes from one two-step phase to the next: phase k of a run reads
 // what phase k - 1 wrote (the two buffers alternate), advances steps
@@ -224,8 +217,7 @@ __device__ __noinline__ void step2_general(const StepParams &p, int x0, int y0, 
       for (int i = 0; i < 9; ++i)
         f[i] = ldp<T, C>(b + (i * p.fplane - cyd(i) * p.frow - cxd(i)), p);
     } else {
-#pragma unroll
-      for (int i = 0; i < 9; ++i) f[i] = pull_general<T, C>(p, fin, i, wx, wy);
+      pull_cell<T, C>(p, GridPops<T>{fin, p.fplane, p.frow}, wx, wy, f);
     }
     const Moments<C> M = cell_moments<C>(f);
     C jx, jy, Sx, Sy, fs[9];
@@ -254,9 +246,7 @@ __device__ __noinline__ void step2_general(const StepParams &p, int x0, int y0, 
 #pragma unroll
     for (int i = 0; i < 9; ++i) f[i] = ld<T, C>(tp.at(i, x - cxd(i), y - cyd(i)));
   } else {
-#pragma unroll
-    for (int i = 0; i < 9; ++i)
-      f[i] = pull_general_tile<T, C>(p, tile, x0 - 1, y0 - 1, i, x, y);
+    pull_cell<T, C>(p, TilePops<T>{tile, x0 - 1, y0 - 1}, x, y, f);
   }
   const Moments<C> M = cell_moments<C>(f);
   C jx, jy, Sx, Sy, fs[9];
