@@ -557,6 +557,8 @@ template <class C>
 __device__ void body_force_cell(const StepParams &p, int x, int y, long long n, C &Fx, C &Fy) {
   Fx = C(0);
   Fy = C(0);
+  // outside the bounding box of every footprint no source contributes
+  if (x < p.src_x0 || x > p.src_x1 || y < p.src_y0 || y > p.src_y1) return;
   for (int s = 0; s < p.nsrc; ++s) {
     const SourceDev &q = p.src[s];
     int dy = y - q.yc, dx = x - q.xc;
@@ -682,6 +684,8 @@ __device__ __forceinline__ void collide_cell(const Moments<C> &M, C jx, C jy, C 
 template <class U>
 __device__ __forceinline__ void record_receiver(const StepParams &p, int slot, int x, int y,
                                                 U ux, U uy, U vx, U vy) {
+  // no table lookup outside the bounding box of the receivers
+  if (x < p.rec_x0 || x > p.rec_x1 || y < p.rec_y0 || y > p.rec_y1) return;
   const int tile = (y / kRecTileY) * p.rec_tiles_x + x / kRecTileX;
   const int r0 = p.rec_tile_ptr[tile], r1 = p.rec_tile_ptr[tile + 1];
   for (int r = r0; r < r1; ++r) {
