@@ -376,13 +376,27 @@ __device__ __noinline__ void pull_cell(const StepParams &p, const A a, int x, in
     if (cxd(i) * nxo + cyd(i) * nyo < 0) f[i] = abb_value<C>(air, oppd(i), own[oppd(i)]);
 }
 
-// All nine streamed populations of (x, y).
+// Whether no pull of the in-grid cell (x, y) crosses a non-periodic edge
+// (its nine pulls are plain loads, wrapped across periodic seams).
+__device__ __forceinline__ bool off_walls(const StepParams &p, int x, int y) {
+  return (p.bc_left == BC_PERIODIC || (x > 0 && x < p.nx - 1)) &&
+         (p.bc_top == BC_PERIODIC || (y > 0 && y < p.ny - 1));
+}
+
+// All nine streamed populations of the in-grid cell (x, y).
 template <class T, class C>
 __device__ __forceinline__ void gather(const StepParams &p, const T *f, int x, int y, C *fo) {
   if (x > 0 && x < p.nx - 1 && y > 0 && y < p.ny - 1) {
     const T *b = f + (y * p.frow + x);
 #pragma unroll
     for (int i = 0; i < 9; ++i) fo[i] = ldp<T, C>(b + (i * p.fplane - cyd(i) * p.frow - cxd(i)), p);
+  } else if (off_walls(p, x, y)) {
+    // a cell on a periodic seam: the pulls wrapped, inline
+    const int xs[3] = {x > 0 ? x - 1 : p.nx - 1, x, x < p.nx - 1 ? x + 1 : 0};
+    const int ys[3] = {y > 0 ? y - 1 : p.ny - 1, y, y < p.ny - 1 ? y + 1 : 0};
+#pragma unroll
+    for (int i = 0; i < 9; ++i)
+      fo[i] = ldp<T, C>(f + (i * p.fplane + (ys[1 - cyd(i)] * p.frow + xs[1 - cxd(i)])), p);
   } else {
     pull_cell<T, C>(p, GridPops<T>{f, p.fplane, p.frow}, x, y, fo);
   }

@@ -229,16 +229,15 @@ __device__ __noinline__ void lam_general(const StepParams &p, const Phase2 &ph, 
   const T *fin = (const T *)ph.fin;
   C f[9];
   C rho = C(0);
-  if (valid) {
-    gather<T, C>(p, fin, wx, wy, f);
-    rho = f[0] + f[1] + f[2] + f[3] + f[4] + f[5] + f[6] + f[7] + f[8];
-  }
-  rho_s[w + 1][lane + 1] = rho;
+  if (valid) gather<T, C>(p, fin, wx, wy, f);
+  // the ring's densities, their loads issued before the cell's own sum
   if (t < kL2Ring) {
     int hx, hy;
     lam_ring_cell(t, hx, hy);
     rho_s[hy][hx] = rho_wrapped<T, C>(p, fin, x0 - 3 + hx, y0 - 3 + hy);
   }
+  if (valid) rho = f[0] + f[1] + f[2] + f[3] + f[4] + f[5] + f[6] + f[7] + f[8];
+  rho_s[w + 1][lane + 1] = rho;
   __syncthreads();
   U *u = (U *)p.u;
   const int c = y * p.pitch + x;
@@ -277,7 +276,8 @@ __device__ __noinline__ void lam_general(const StepParams &p, const Phase2 &ph, 
   if (w1) {
     rho = C(0);
     if (valid) {
-      if (wx >= 1 && wx < p.nx - 1 && wy >= 1 && wy < p.ny - 1) {
+      if (off_walls(p, wx, wy)) {
+        // the window holds the periodic images at unwrapped coordinates
 #pragma unroll
         for (int i = 0; i < 9; ++i)
           f[i] = ld<T, C>(tile + ((i * kL2H + w - cyd(i)) * kL2W + lane - cxd(i)));

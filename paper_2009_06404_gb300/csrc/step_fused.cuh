@@ -241,7 +241,8 @@ __device__ __noinline__ void step2_general(const StepParams &p, int x0, int y0, 
   Fx *= force_scale<T, C>(p);
   Fy *= force_scale<T, C>(p);
   C f[9];
-  if (x >= 1 && x < p.nx - 1 && y >= 1 && y < p.ny - 1) {
+  if (off_walls(p, x, y)) {
+    // the window holds the periodic images at unwrapped coordinates
     const TilePops<T> tp{tile, x0 - 1, y0 - 1};
 #pragma unroll
     for (int i = 0; i < 9; ++i) f[i] = ld<T, C>(tp.at(i, x - cxd(i), y - cyd(i)));
