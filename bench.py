@@ -446,12 +446,19 @@ def form_precision(torch, pkg, wl, n=8192, steps=2000, time_steps=2000, err_n=10
     against ERROR_BUDGET_REL_L2."""
     scale = {"f32": 0, "f16": 10, "bf16": 0, "f64": 0}
     w = wl.periodic_layered_multisource(n=n, nsteps=time_steps)
-    mlups = {}
+    mlups, alt = {}, {}
     for st in ("f32", "f16", "bf16"):
         sim = pkg.from_workload(w, storage=st, store_scale_log2=scale[st], max_steps_traced=0)
         sim.step(20)
         ms = _timed(torch, lambda: sim.step(time_steps))
         mlups[st] = w.cells * time_steps / ms / 1e3
+        if st == "f16":
+            # the other launch form of 16-bit storage with Lambda != 0 (the
+            # library's default for it is one step per launch)
+            sim.set_steps_per_launch(2)
+            sim.step(20)
+            ms = _timed(torch, lambda: sim.step(min(time_steps, 400)))
+            alt["f16_two_steps_per_launch"] = w.cells * min(time_steps, 400) / ms / 1e3
         sim.sync()
         sim.close()
         del sim
@@ -468,7 +475,7 @@ def form_precision(torch, pkg, wl, n=8192, steps=2000, time_steps=2000, err_n=10
     ok = {st: bool(err_u[st] <= ERROR_BUDGET_REL_L2 and err_v[st] <= ERROR_BUDGET_REL_L2)
           for st in ("f32", "f16", "bf16")}
     return {"workload": f"periodic_layered_{n}x{n}_8layers_16src", "time_steps": time_steps,
-            "mlups": mlups,
+            "mlups": mlups, "mlups_other_launch_form": alt,
             "speedup_vs_f32": {k: mlups[k] / mlups["f32"] for k in ("f16", "bf16")},
             "error": {"vs": f"FP64 GPU run, same generator at {err_n}x{err_n}, {steps} steps "
                             "(equal to the CPU oracle to 1e-12)",
