@@ -403,23 +403,32 @@ __device__ __forceinline__ void gather(const StepParams &p, const T *f, int x, i
 }
 
 template <class T, class C>
-__device__ C rho_at(const StepParams &p, const T *f, int x, int y) {
+__device__ __forceinline__ C rho_at(const StepParams &p, const T *f, int x, int y) {
   C v[9];
   gather<T, C>(p, f, x, y, v);
   return v[0] + v[1] + v[2] + v[3] + v[4] + v[5] + v[6] + v[7] + v[8];
 }
 
+// v wrapped into [0, n) (one period either way by an add, further by a
+// remainder).
+__device__ __forceinline__ int wrap_any(int v, int n) {
+  if (v >= -n && v < 2 * n) return v < 0 ? v + n : (v >= n ? v - n : v);
+  return ((v % n) + n) % n;
+}
+
 // Streamed density at grid coordinate (x, y) with periodic axes wrapped;
 // zero beyond a non-periodic edge (the wall rules below replace it there).
+// Inline, so the loads of a caller's own pulls and these are in flight
+// together.
 template <class T, class C>
-__device__ C rho_wrapped(const StepParams &p, const T *f, int x, int y) {
+__device__ __forceinline__ C rho_wrapped(const StepParams &p, const T *f, int x, int y) {
   if (x < 0 || x >= p.nx) {
     if (p.bc_left != BC_PERIODIC) return C(0);
-    x = ((x % p.nx) + p.nx) % p.nx;
+    x = wrap_any(x, p.nx);
   }
   if (y < 0 || y >= p.ny) {
     if (p.bc_top != BC_PERIODIC) return C(0);
-    y = ((y % p.ny) + p.ny) % p.ny;
+    y = wrap_any(y, p.ny);
   }
   return rho_at<T, C>(p, f, x, y);
 }
@@ -563,34 +572,87 @@ __device__ void body_force(const StepParams &p, int x, int y, C &Fx, C &Fy) {
   }
 }
 
-// The body force of step n at (x, y) computed by one thread alone (no warp
-// cooperation): the sources whose integer bound contains the cell, in
-// ascending order.  Every source that body_force adds and this one skips
-// contributes an exact zero, so the two agree bit for bit.
-template <class C>
-__device__ void body_force_cell(const StepParams &p, int x, int y, long long n, C &Fx, C &Fy) {
-  Fx = C(0);
-  Fy = C(0);
-  // outside the bounding box of every footprint no source contributes
-  if (x < p.src_x0 || x > p.src_x1 || y < p.src_y0 || y > p.src_y1) return;
-  for (int s = 0; s < p.nsrc; ++s) {
-    const SourceDev &q = p.src[s];
-    int dy = y - q.yc, dx = x - q.xc;
-    if (p.bc_top == BC_PERIODIC) {
-      if (dy > p.ny / 2) dy -= p.ny;
-      else if (dy < -(p.ny / 2)) dy += p.ny;
-    }
+// Sources that may reach the cells within hx columns and hy rows of
+// (cx, cy): bit s is set when source s's integer bound (|dx|, |dy| <= rb,
+// minimum image on periodic axes) can contain such a cell; every bit when
+// there are more than 32 sources.  Warp-wide: every lane of the warp calls
+// it, and blocks are 32 threads wide (threadIdx.x is the lane).
+__device__ __forceinline__ unsigned source_mask(const StepParams &p, int cx, int cy, int hx,
+                                                int hy) {
+  if (p.nsrc > 32) return 0xffffffffu;
+  bool hit = false;
+  if ((int)threadIdx.x < p.nsrc) {
+    const SourceDev &q = p.src[threadIdx.x];
+    int dx = cx - q.xc, dy = cy - q.yc;
     if (p.bc_left == BC_PERIODIC) {
       if (dx > p.nx / 2) dx -= p.nx;
       else if (dx < -(p.nx / 2)) dx += p.nx;
     }
-    if (abs(dy) <= q.rb && abs(dx) <= q.rb) {
-      const auto F = source_term(q, x, y, n, p.nx, p.ny, p.bc_left == BC_PERIODIC,
-                                 p.bc_top == BC_PERIODIC, C(0));
-      Fx += C(F.x);
-      Fy += C(F.y);
+    if (p.bc_top == BC_PERIODIC) {
+      if (dy > p.ny / 2) dy -= p.ny;
+      else if (dy < -(p.ny / 2)) dy += p.ny;
     }
+    hit = abs(dx) <= q.rb + hx && abs(dy) <= q.rb + hy;
   }
+  return __ballot_sync(0xffffffffu, hit);
+}
+
+// Source s's share of the body force at (x, y), step n, if its integer
+// bound contains the cell.
+template <class C>
+__device__ __forceinline__ void add_source(const StepParams &p, int s, int x, int y, long long n,
+                                           C &Fx, C &Fy) {
+  const SourceDev &q = p.src[s];
+  int dy = y - q.yc, dx = x - q.xc;
+  if (p.bc_top == BC_PERIODIC) {
+    if (dy > p.ny / 2) dy -= p.ny;
+    else if (dy < -(p.ny / 2)) dy += p.ny;
+  }
+  if (p.bc_left == BC_PERIODIC) {
+    if (dx > p.nx / 2) dx -= p.nx;
+    else if (dx < -(p.nx / 2)) dx += p.nx;
+  }
+  if (abs(dy) <= q.rb && abs(dx) <= q.rb) {
+    const auto F = source_term(q, x, y, n, p.nx, p.ny, p.bc_left == BC_PERIODIC,
+                               p.bc_top == BC_PERIODIC, C(0));
+    Fx += C(F.x);
+    Fy += C(F.y);
+  }
+}
+
+// The body force of step n at (x, y) computed by one thread alone (no warp
+// cooperation): the sources whose integer bound contains the cell, in
+// ascending order, among those of `mask` (a superset of them, e.g. from
+// source_mask).  Every source that body_force adds and this one skips
+// contributes an exact zero, so the two agree bit for bit.  The sum is out
+// of line (its registers stay out of the general paths' budget) and only
+// called inside the bounding box of the footprints.
+template <class C>
+struct ForcePair {
+  C x, y;
+};
+template <class C>
+__device__ __noinline__ ForcePair<C> body_force_sum(const StepParams &p, int x, int y,
+                                                    long long n, unsigned mask) {
+  C Fx = C(0), Fy = C(0);
+  if (p.nsrc > 32) {
+    for (int s = 0; s < p.nsrc; ++s) add_source<C>(p, s, x, y, n, Fx, Fy);
+  } else {
+    for (unsigned m = mask; m != 0u; m &= m - 1u) add_source<C>(p, __ffs(m) - 1, x, y, n, Fx, Fy);
+  }
+  return ForcePair<C>{Fx, Fy};
+}
+
+template <class C>
+__device__ __forceinline__ void body_force_cell(const StepParams &p, int x, int y, long long n,
+                                                C &Fx, C &Fy, unsigned mask = 0xffffffffu) {
+  Fx = C(0);
+  Fy = C(0);
+  // outside the bounding box of every footprint no source contributes
+  if (mask == 0u || x < p.src_x0 || x > p.src_x1 || y < p.src_y0 || y > p.src_y1) return;
+  const ForcePair<C> F = body_force_sum<C>(p, x, y, n, mask);
+  Fx = F.x;
+  Fy = F.y;
 }
 
 template <class C>

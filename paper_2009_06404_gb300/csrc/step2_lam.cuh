@@ -207,6 +207,11 @@ __device__ __forceinline__ void lam_bulk(const StepParams &p, const Phase2 &ph, 
 // as rho_wrapped gives; the wall ghosts replace it), the wall rules for the
 // pulls (from HBM in step n, from the window in step n + 1), the body force
 // per cell and the receivers.  Out of line; every thread calls it.
+//
+// Register budget: the body force of each step is summed (out of line, in
+// the sources' bounding box) before that step's pulls, when little else is
+// live, and the displacement after step n goes through global memory (u +
+// v^n stored, reloaded for + v^{n+1}: the same two roundings).
 template <class T, class C, class U>
 __device__ __noinline__ void lam_general(const StepParams &p, const Phase2 &ph, int x0, int y0,
                                          T *tile, C (*rho_s)[kL2RW]) {
@@ -225,15 +230,23 @@ __device__ __noinline__ void lam_general(const StepParams &p, const Phase2 &ph, 
   const bool w1 = lane >= 1 && lane <= kL2W - 2 && w >= 1 && w <= kL2H - 2;
   const bool core = lane >= 2 && lane <= kL2W - 3 && w >= 2 && w <= kL2H - 3;
   const bool active = core && x < p.nx && y < p.ny;
-  const C om = par<C>(p.omega, p.omega_f), fc = par<C>(p.fcoef, p.fcoef_f);
+  // W2 cells lie within kL2Cols/2 + 2 columns and kL2Rows/2 + 2 rows of the
+  // centre
+  const unsigned smask = source_mask(p, x0 + kL2Cols / 2, y0 + kL2Rows / 2, kL2Cols / 2 + 3,
+                                     kL2Rows / 2 + 3);
+  C Fx = C(0), Fy = C(0);
+  if (valid) body_force_cell<C>(p, wx, wy, ph.n, Fx, Fy, smask);
   const T *fin = (const T *)ph.fin;
   C f[9];
   C rho = C(0);
   if (valid) gather<T, C>(p, fin, wx, wy, f);
-  // the ring's densities, their loads issued before the cell's own sum
-  if (t < kL2Ring) {
+  // the ring's densities, their loads issued before the cell's own sum, by
+  // the block's last threads (the W2 rows farthest from a top wall, and rows
+  // beyond a bottom wall, which have no cell of their own)
+  const int tr = 32 * kL2H - 1 - t;
+  if (tr < kL2Ring) {
     int hx, hy;
-    lam_ring_cell(t, hx, hy);
+    lam_ring_cell(tr, hx, hy);
     rho_s[hy][hx] = rho_wrapped<T, C>(p, fin, x0 - 3 + hx, y0 - 3 + hy);
   }
   if (valid) rho = f[0] + f[1] + f[2] + f[3] + f[4] + f[5] + f[6] + f[7] + f[8];
@@ -241,8 +254,6 @@ __device__ __noinline__ void lam_general(const StepParams &p, const Phase2 &ph, 
   __syncthreads();
   U *u = (U *)p.u;
   const int c = y * p.pitch + x;
-  U ux = U(0), uy = U(0);
-  C irho = C(0);
   if (valid) {
     // step n on W2
     C rxm = rho_s[w + 1][lane], rxp = rho_s[w + 1][lane + 2];
@@ -252,26 +263,29 @@ __device__ __noinline__ void lam_general(const StepParams &p, const Phase2 &ph, 
     const C gx = C(0.5) * (rxp - rxm), gy = C(0.5) * (ryp - rym);
     if (active && p.grad_out) store_grad<C>(p, 0, c, gx, gy);
     const C lb2 = mat_at<C>(p.lam, p.mat_per_cell, wx, wy, p.pitch) * C(1.0 / 3.0);
-    C Fx, Fy;
-    body_force_cell<C>(p, wx, wy, ph.n, Fx, Fy);
     Fx *= force_scale<T, C>(p);
     Fy *= force_scale<T, C>(p);
     const Moments<C> M = cell_moments<C>(f);
     C jx, jy, Sx, Sy, fs[9];
     flux_and_source<C>(M.mx, M.my, mul_rn(lb2, gx), mul_rn(lb2, gy), Fx, Fy,
                        sponge_A<C>(p, wx, wy), jx, jy, Sx, Sy);
-    collide_cell<C>(M, jx, jy, Sx, Sy, om, fc, fs);
+    collide_cell<C>(M, jx, jy, Sx, Sy, par<C>(p.omega, p.omega_f), par<C>(p.fcoef, p.fcoef_f),
+                    fs);
 #pragma unroll
     for (int i = 0; i < 9; ++i) st<T, C>(tile + ((i * kL2H + w) * kL2W + lane), fs[i]);
     if (active) {
-      irho = irho_at<T, C>(p, x, y);
+      const C irho = irho_at<T, C>(p, x, y);
       const U vx = U(mul_rn(jx, irho)), vy = U(mul_rn(jy, irho));
-      ux = __ldcg(u + c) + vx;
-      uy = __ldcg(u + p.plane + c) + vy;
+      const U ux = __ldcg(u + c) + vx, uy = __ldcg(u + p.plane + c) + vy;
+      u[c] = ux;
+      u[p.plane + c] = uy;
       if (ph.slot_a >= 0) record_receiver<U>(p, ph.slot_a, x, y, ux, uy, vx, vy);
     }
   }
   __syncthreads();
+  Fx = C(0);
+  Fy = C(0);
+  if (active) body_force_cell<C>(p, x, y, ph.n + 1, Fx, Fy, smask);
   // streamed densities of step n + 1 on W1 (0 beyond a non-periodic edge)
   if (w1) {
     rho = C(0);
@@ -298,21 +312,19 @@ __device__ __noinline__ void lam_general(const StepParams &p, const Phase2 &ph, 
   const C gx = C(0.5) * (rxp - rxm), gy = C(0.5) * (ryp - rym);
   if (p.grad_out) store_grad<C>(p, 1, c, gx, gy);
   const C lb2 = mat_at<C>(p.lam, p.mat_per_cell, x, y, p.pitch) * C(1.0 / 3.0);
-  C Fx, Fy;
-  body_force_cell<C>(p, x, y, ph.n + 1, Fx, Fy);
   Fx *= force_scale<T, C>(p);
   Fy *= force_scale<T, C>(p);
   const Moments<C> M = cell_moments<C>(f);
   C jx, jy, Sx, Sy, fs[9];
   flux_and_source<C>(M.mx, M.my, mul_rn(lb2, gx), mul_rn(lb2, gy), Fx, Fy, sponge_A<C>(p, x, y),
                      jx, jy, Sx, Sy);
-  collide_cell<C>(M, jx, jy, Sx, Sy, om, fc, fs);
+  collide_cell<C>(M, jx, jy, Sx, Sy, par<C>(p.omega, p.omega_f), par<C>(p.fcoef, p.fcoef_f), fs);
   T *fout = (T *)ph.fout + (y * p.frow + x);
 #pragma unroll
   for (int i = 0; i < 9; ++i) stp<T, C>(fout + i * p.fplane, fs[i], p);
+  const C irho = irho_at<T, C>(p, x, y);
   const U vx = U(mul_rn(jx, irho)), vy = U(mul_rn(jy, irho));
-  ux += vx;
-  uy += vy;
+  const U ux = u[c] + vx, uy = u[p.plane + c] + vy;
   u[c] = ux;
   u[p.plane + c] = uy;
   if (!((M.rho + jx + jy) * C(0) == C(0))) atomicOr(p.err, 1);

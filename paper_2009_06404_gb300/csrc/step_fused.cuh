@@ -180,66 +180,78 @@ __device__ __forceinline__ int tile_kind(const StepParams &p, int x0, int y0, in
 // rules replace them); step n + 1 at the tile's cells.  Out of line so the
 // bulk path carries none of its registers.  Every thread calls it (one
 // barrier).
+//
+// Register budget: each step's pulls come first, when nothing else is live
+// (the out-of-line wall rule then saves no registers around its call), and
+// the displacement after step n goes through global memory (u + v^n stored,
+// reloaded for + v^{n+1}: the same two roundings), so nothing but the
+// block's tile position crosses the barrier.
 template <class T, class C, class U>
 __device__ __noinline__ void step2_general(const StepParams &p, int x0, int y0, T *tile, int k) {
-  const Phase2 ph = phase2(p, k);
-  const int lane = threadIdx.x, w = threadIdx.y;
-  int ex, ey;
-  bool core;
-  window_cell(lane, w, ex, ey, core);
-  const int x = x0 - 1 + ex, y = y0 - 1 + ey;
-  int wx = x, wy = y;
-  bool valid = true;
-  if (x < 0 || x >= p.nx) {
-    if (p.bc_left == BC_PERIODIC) wx = ((x % p.nx) + p.nx) % p.nx;
-    else valid = false;
-  }
-  if (y < 0 || y >= p.ny) {
-    if (p.bc_top == BC_PERIODIC) wy = ((y % p.ny) + p.ny) % p.ny;
-    else valid = false;
-  }
-  const bool active = core && x < p.nx && y < p.ny;
-  const C om = par<C>(p.omega, p.omega_f), fc = par<C>(p.fcoef, p.fcoef_f);
-  U *u = (U *)p.u;
-  const int c = y * p.pitch + x;
-  U ux = U(0), uy = U(0);
-  C irho = C(0);
-  if (valid) {
-    C Fx, Fy;
-    body_force_cell<C>(p, wx, wy, ph.n, Fx, Fy);
-    Fx *= force_scale<T, C>(p);
-    Fy *= force_scale<T, C>(p);
-    const T *fin = (const T *)ph.fin;
-    C f[9];
-    if (wx >= 1 && wx < p.nx - 1 && wy >= 1 && wy < p.ny - 1) {
-      const T *b = fin + (wy * p.frow + wx);
-#pragma unroll
-      for (int i = 0; i < 9; ++i)
-        f[i] = ldp<T, C>(b + (i * p.fplane - cyd(i) * p.frow - cxd(i)), p);
-    } else {
-      pull_cell<T, C>(p, GridPops<T>{fin, p.fplane, p.frow}, wx, wy, f);
+  // window cells lie within kF2Cols/2 + 1 columns and kF2Rows/2 + 1 rows of
+  // the centre
+  const unsigned smask = source_mask(p, x0 + kF2Cols / 2, y0 + kF2Rows / 2, kF2Cols / 2 + 2,
+                                     kF2Rows / 2 + 2);
+  {
+    int ex, ey;
+    bool core;
+    window_cell(threadIdx.x, threadIdx.y, ex, ey, core);
+    const int x = x0 - 1 + ex, y = y0 - 1 + ey;
+    int wx = x, wy = y;
+    bool valid = true;
+    if (x < 0 || x >= p.nx) {
+      if (p.bc_left == BC_PERIODIC) wx = ((x % p.nx) + p.nx) % p.nx;
+      else valid = false;
     }
-    const Moments<C> M = cell_moments<C>(f);
-    C jx, jy, Sx, Sy, fs[9];
-    flux_and_source<C>(M.mx, M.my, C(0), C(0), Fx, Fy, sponge_A<C>(p, wx, wy), jx, jy, Sx, Sy);
-    collide_cell<C>(M, jx, jy, Sx, Sy, om, fc, fs);
+    if (y < 0 || y >= p.ny) {
+      if (p.bc_top == BC_PERIODIC) wy = ((y % p.ny) + p.ny) % p.ny;
+      else valid = false;
+    }
+    if (valid) {
+      const Phase2 ph = phase2(p, k);
+      C Fx, Fy;
+      body_force_cell<C>(p, wx, wy, ph.n, Fx, Fy, smask);
+      const T *fin = (const T *)ph.fin;
+      C f[9];
+      if (wx >= 1 && wx < p.nx - 1 && wy >= 1 && wy < p.ny - 1) {
+        const T *b = fin + (wy * p.frow + wx);
 #pragma unroll
-    for (int i = 0; i < 9; ++i) st<T, C>(tile + ((i * kF2H + ey) * kF2W + ex), fs[i]);
-    if (active) {
-      irho = irho_at<T, C>(p, x, y);
-      const U vx = U(mul_rn(jx, irho)), vy = U(mul_rn(jy, irho));
-      ux = __ldcg(u + c) + vx;
-      uy = __ldcg(u + p.plane + c) + vy;
-      if (ph.slot_a >= 0) record_receiver<U>(p, ph.slot_a, x, y, ux, uy, vx, vy);
+        for (int i = 0; i < 9; ++i)
+          f[i] = ldp<T, C>(b + (i * p.fplane - cyd(i) * p.frow - cxd(i)), p);
+      } else {
+        pull_cell<T, C>(p, GridPops<T>{fin, p.fplane, p.frow}, wx, wy, f);
+      }
+      const Moments<C> M = cell_moments<C>(f);
+      Fx *= force_scale<T, C>(p);
+      Fy *= force_scale<T, C>(p);
+      C jx, jy, Sx, Sy, fs[9];
+      flux_and_source<C>(M.mx, M.my, C(0), C(0), Fx, Fy, sponge_A<C>(p, wx, wy), jx, jy, Sx, Sy);
+      collide_cell<C>(M, jx, jy, Sx, Sy, par<C>(p.omega, p.omega_f), par<C>(p.fcoef, p.fcoef_f),
+                      fs);
+#pragma unroll
+      for (int i = 0; i < 9; ++i) st<T, C>(tile + ((i * kF2H + ey) * kF2W + ex), fs[i]);
+      if (core && x < p.nx && y < p.ny) {
+        const C irho = irho_at<T, C>(p, x, y);
+        const U vx = U(mul_rn(jx, irho)), vy = U(mul_rn(jy, irho));
+        U *u = (U *)p.u;
+        const int c = y * p.pitch + x;
+        const U ux = __ldcg(u + c) + vx, uy = __ldcg(u + p.plane + c) + vy;
+        u[c] = ux;
+        u[p.plane + c] = uy;
+        if (ph.slot_a >= 0) record_receiver<U>(p, ph.slot_a, x, y, ux, uy, vx, vy);
+      }
     }
   }
   __syncthreads();
-  if (!active) return;
+  int ex, ey;
+  bool core;
+  window_cell(threadIdx.x, threadIdx.y, ex, ey, core);
+  const int x = x0 - 1 + ex, y = y0 - 1 + ey;
+  if (!(core && x < p.nx && y < p.ny)) return;
   // step n + 1 of the tile's cell (x, y)
+  const Phase2 ph = phase2(p, k);
   C Fx, Fy;
-  body_force_cell<C>(p, x, y, ph.n + 1, Fx, Fy);
-  Fx *= force_scale<T, C>(p);
-  Fy *= force_scale<T, C>(p);
+  body_force_cell<C>(p, x, y, ph.n + 1, Fx, Fy, smask);
   C f[9];
   if (off_walls(p, x, y)) {
     // the window holds the periodic images at unwrapped coordinates
@@ -250,15 +262,19 @@ __device__ __noinline__ void step2_general(const StepParams &p, int x0, int y0, 
     pull_cell<T, C>(p, TilePops<T>{tile, x0 - 1, y0 - 1}, x, y, f);
   }
   const Moments<C> M = cell_moments<C>(f);
+  Fx *= force_scale<T, C>(p);
+  Fy *= force_scale<T, C>(p);
   C jx, jy, Sx, Sy, fs[9];
   flux_and_source<C>(M.mx, M.my, C(0), C(0), Fx, Fy, sponge_A<C>(p, x, y), jx, jy, Sx, Sy);
-  collide_cell<C>(M, jx, jy, Sx, Sy, om, fc, fs);
+  collide_cell<C>(M, jx, jy, Sx, Sy, par<C>(p.omega, p.omega_f), par<C>(p.fcoef, p.fcoef_f), fs);
   T *fout = (T *)ph.fout + (y * p.frow + x);
 #pragma unroll
   for (int i = 0; i < 9; ++i) stp<T, C>(fout + i * p.fplane, fs[i], p);
+  const C irho = irho_at<T, C>(p, x, y);
   const U vx = U(mul_rn(jx, irho)), vy = U(mul_rn(jy, irho));
-  ux += vx;
-  uy += vy;
+  U *u = (U *)p.u;
+  const int c = y * p.pitch + x;
+  const U ux = u[c] + vx, uy = u[p.plane + c] + vy;
   u[c] = ux;
   u[p.plane + c] = uy;
   if (!((M.rho + jx + jy) * C(0) == C(0))) atomicOr(p.err, 1);
@@ -287,6 +303,13 @@ __device__ __noinline__ void step2_featured(const StepParams &p, int x0, int y0,
   const bool spg = (kind & kTileWrap) || x0 - 1 < p.sp_left || x0 + kF2Cols + 1 > p.nx - p.sp_right ||
                    y0 - 1 < p.sp_top || y0 + kF2Rows + 1 > p.ny - p.sp_bottom;
   const C om = par<C>(p.omega, p.omega_f), fc = par<C>(p.fcoef, p.fcoef_f);
+  // the body force of step n first (an out-of-line sum inside the sources'
+  // bounding box), before the pulls fill the registers
+  const unsigned smask = src ? source_mask(p, x0 + kF2Cols / 2, y0 + kF2Rows / 2,
+                                           kF2Cols / 2 + 2, kF2Rows / 2 + 2)
+                             : 0u;
+  C Fx = C(0), Fy = C(0);
+  if (src) body_force_cell<C>(p, wx, wy, ph.n, Fx, Fy, smask);
   // step n on the window
   const T *fin = (const T *)ph.fin;
   C f[9];
@@ -310,8 +333,7 @@ __device__ __noinline__ void step2_featured(const StepParams &p, int x0, int y0,
     const Moments<C> M = cell_moments<C>(f);
     C jx, jy, fs[9];
     if (src) {  // (a compile-time branch)
-      C Fx, Fy, Sx, Sy;
-      body_force_cell<C>(p, wx, wy, ph.n, Fx, Fy);
+      C Sx, Sy;
       Fx *= force_scale<T, C>(p);
       Fy *= force_scale<T, C>(p);
       flux_and_source<C>(M.mx, M.my, C(0), C(0), Fx, Fy, sponge_A<C>(p, wx, wy), jx, jy, Sx, Sy);
@@ -331,6 +353,7 @@ __device__ __noinline__ void step2_featured(const StepParams &p, int x0, int y0,
   }
   __syncthreads();
   if (!core) return;
+  if (src) body_force_cell<C>(p, x, y, ph.n + 1, Fx, Fy, smask);
   // step n + 1 of the tile's cell, pulled from the window
 #pragma unroll
   for (int i = 0; i < 9; ++i)
@@ -338,8 +361,7 @@ __device__ __noinline__ void step2_featured(const StepParams &p, int x0, int y0,
   const Moments<C> M = cell_moments<C>(f);
   C jx, jy, fs[9];
   if (src) {
-    C Fx, Fy, Sx, Sy;
-    body_force_cell<C>(p, x, y, ph.n + 1, Fx, Fy);
+    C Sx, Sy;
     Fx *= force_scale<T, C>(p);
     Fy *= force_scale<T, C>(p);
     flux_and_source<C>(M.mx, M.my, C(0), C(0), Fx, Fy, sponge_A<C>(p, x, y), jx, jy, Sx, Sy);
