@@ -122,7 +122,7 @@ constexpr int kBatch2Threads = 32 * kF2Warps;
 // density buffer of the density-gradient kind behind it.
 template <class T, class C>
 struct Batch2Smem {
-  static constexpr int kWin = 9 * kL2H * kL2W;
+  static constexpr int kWin = l2_buf<T>() > f2_buf<T>() ? l2_buf<T>() : f2_buf<T>();
   static constexpr size_t kBytes = kWin * sizeof(T) + sizeof(C) * kL2RH * kL2RW;
 };
 

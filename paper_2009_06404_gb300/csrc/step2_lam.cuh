@@ -27,6 +27,17 @@ constexpr int kL2RW = kL2W + 2;         // W3 columns (density buffer)
 constexpr int kL2RH = kL2H + 2;         // W3 rows
 constexpr int kL2Ring = 2 * kL2RW + 2 * kL2H;  // W3 cells outside W2
 static_assert(kL2W == 32, "a W2 row is one warp");
+// Staged region of a general tile: the tile widened by four cells (the W3
+// ring's pulls), aliasing the W2 window buffer until step n's stores.
+template <class T>
+constexpr int l2_stage_w() { return stage_width<T>(kL2Cols, 4); }
+constexpr int kL2SH = kL2Rows + 8;
+template <class T>
+constexpr int l2_buf() {
+  return stages<T>() && 9 * kL2SH * l2_stage_w<T>() > 9 * kL2H * kL2W
+             ? 9 * kL2SH * l2_stage_w<T>()
+             : 9 * kL2H * kL2W;
+}
 static_assert(kL2Ring <= 32 * kL2H, "one ring cell per thread at most");
 
 #ifndef LBM_STEP2L_MIN_BLOCKS
@@ -205,8 +216,10 @@ __device__ __forceinline__ void lam_bulk(const StepParams &p, const Phase2 &ph, 
 // Tiles near an edge or seam, a source or receivers: every cell at its
 // wrapped coordinate, cells beyond a non-periodic edge skipped (density 0,
 // as rho_wrapped gives; the wall ghosts replace it), the wall rules for the
-// pulls (from HBM in step n, from the window in step n + 1), the body force
-// per cell and the receivers.  Out of line; every thread calls it.
+// pulls (in step n from the input populations of the tile widened by four
+// cells, staged in shared memory by one pass of loads; in step n + 1 from
+// the window), the body force per cell and the receivers.  Out of line;
+// every thread calls it (four barriers).
 //
 // Register budget: the body force of each step is summed (out of line, in
 // the sources' bounding box) before that step's pulls, when little else is
@@ -220,11 +233,11 @@ __device__ __noinline__ void lam_general(const StepParams &p, const Phase2 &ph, 
   int wx = x, wy = y;
   bool valid = true;
   if (x < 0 || x >= p.nx) {
-    if (p.bc_left == BC_PERIODIC) wx = ((x % p.nx) + p.nx) % p.nx;
+    if (p.bc_left == BC_PERIODIC) wx = wrap_any(x, p.nx);
     else valid = false;
   }
   if (y < 0 || y >= p.ny) {
-    if (p.bc_top == BC_PERIODIC) wy = ((y % p.ny) + p.ny) % p.ny;
+    if (p.bc_top == BC_PERIODIC) wy = wrap_any(y, p.ny);
     else valid = false;
   }
   const bool w1 = lane >= 1 && lane <= kL2W - 2 && w >= 1 && w <= kL2H - 2;
@@ -236,18 +249,42 @@ __device__ __noinline__ void lam_general(const StepParams &p, const Phase2 &ph, 
                                      kL2Rows / 2 + 3);
   C Fx = C(0), Fy = C(0);
   if (valid) body_force_cell<C>(p, wx, wy, ph.n, Fx, Fy, smask);
-  const T *fin = (const T *)ph.fin;
+  // the input populations of every pull of step n (W2's and the W3 ring's),
+  // staged in the window buffer, which step n's stores overwrite only after
+  // the barrier that follows the pulls
+  constexpr int SW = l2_stage_w<T>();
+  const int sox = stage_origin<T>(x0, 4);
+  if constexpr (stages<T>()) {
+    stage_rows<T, SW, kL2SH, 32 * kL2H>(p, (const T *)ph.fin, sox, y0 - 4, tile);
+    stage_wait();
+  }
+  __syncthreads();
+  const StagePops<T, SW, kL2SH> sg{tile, sox, y0 - 4};
   C f[9];
   C rho = C(0);
-  if (valid) gather<T, C>(p, fin, wx, wy, f);
-  // the ring's densities, their loads issued before the cell's own sum, by
-  // the block's last threads (the W2 rows farthest from a top wall, and rows
-  // beyond a bottom wall, which have no cell of their own)
+  if (valid) {
+    if constexpr (stages<T>()) pull_staged<T, C>(p, sg, x, y, f);
+    else gather<T, C>(p, (const T *)ph.fin, wx, wy, f);
+  }
+  // the ring's densities (zero beyond a non-periodic edge), by the block's
+  // last threads (W2 rows away from a top wall, or beyond a bottom wall)
   const int tr = 32 * kL2H - 1 - t;
   if (tr < kL2Ring) {
     int hx, hy;
     lam_ring_cell(tr, hx, hy);
-    rho_s[hy][hx] = rho_wrapped<T, C>(p, fin, x0 - 3 + hx, y0 - 3 + hy);
+    const int rx = x0 - 3 + hx, ry = y0 - 3 + hy;
+    C r = C(0);
+    if constexpr (stages<T>()) {
+      if ((p.bc_left == BC_PERIODIC || (rx >= 0 && rx < p.nx)) &&
+          (p.bc_top == BC_PERIODIC || (ry >= 0 && ry < p.ny))) {
+        C v[9];
+        pull_staged<T, C>(p, sg, rx, ry, v);
+        r = v[0] + v[1] + v[2] + v[3] + v[4] + v[5] + v[6] + v[7] + v[8];
+      }
+    } else {
+      r = rho_wrapped<T, C>(p, (const T *)ph.fin, rx, ry);
+    }
+    rho_s[hy][hx] = r;
   }
   if (valid) rho = f[0] + f[1] + f[2] + f[3] + f[4] + f[5] + f[6] + f[7] + f[8];
   rho_s[w + 1][lane + 1] = rho;
@@ -356,7 +393,7 @@ __global__ void __launch_bounds__(32 * kL2H, LBM_STEP2L_MIN_BLOCKS)
   asm volatile("griddepcontrol.wait;" ::: "memory");
   asm volatile("griddepcontrol.launch_dependents;");
 #endif
-  __shared__ T tile[9 * kL2H * kL2W];
+  __shared__ __align__(16) T tile[l2_buf<T>()];
   __shared__ C rho_s[kL2RH][kL2RW];
   const int2 t = tile_of_block(p.tiles2l, p.tiles2l_first, gridDim.x, blockIdx.x, p.reverse);
   step2_lam_tile<T, C, U>(p, t.x, t.y, tile, rho_s);

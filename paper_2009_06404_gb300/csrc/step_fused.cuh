@@ -72,6 +72,138 @@ struct TilePops {
 };
 
 
+// The input populations around a general tile, staged in shared memory by
+// one pass of copies so that the general rules (wrapped pulls, wall rules,
+// ring densities) read them from there instead of making a round trip to
+// memory per branch.  Layout [SH][9][SW], the global row-interleaved order:
+// element (0, 0) of plane i is grid cell (ox, oy); cells beyond a periodic
+// seam hold the image's populations at their unwrapped coordinates, cells
+// beyond a non-periodic edge are not copied (the wall rules never read
+// them).
+template <class T, int SW, int SH>
+struct StagePops {
+  const T *f;
+  int ox, oy;
+  static constexpr bool kWrap = false;
+  __device__ __forceinline__ const T *at(int i, int x, int y) const {
+    return f + (((y - oy) * 9 + i) * SW + (x - ox));
+  }
+  template <class C>
+  __device__ __forceinline__ C load(int i, int x, int y) const {
+    return ld<T, C>(at(i, x, y));
+  }
+};
+
+// 16-byte chunks of the staged rows: elements per chunk, the columns a
+// region of width w with margin m needs (its origin rounded down to a
+// chunk), rounded up to whole chunks.
+template <class T>
+constexpr int stage_chunk() { return 16 / (int)sizeof(T); }
+template <class T>
+constexpr int stage_width(int w, int m) {
+  return (w + 2 * m + stage_chunk<T>() - 1 + stage_chunk<T>() - 1) / stage_chunk<T>() *
+         stage_chunk<T>();
+}
+// The origin column of a staged region: x0 - m rounded down to a chunk
+// (floor for negative values too).
+template <class T>
+__device__ __forceinline__ int stage_origin(int x0, int m) {
+  constexpr int E = stage_chunk<T>();
+  const int v = x0 - m;
+  return v >= 0 ? v / E * E : -((-v + E - 1) / E * E);
+}
+
+// Stages SH grid rows from oy (each with its nine planes) of SW columns from
+// ox (a multiple of the chunk) of fin into st (16-byte aligned), by every
+// thread of an NT-thread block: whole chunks inside the grid by 16-byte
+// asynchronous copies to shared memory through L2 (cp.async.cg, no
+// registers held), chunks across an edge element by element (wrapped on a
+// periodic axis, skipped beyond a non-periodic one).  The caller waits with
+// stage_wait() and a block barrier.  With a layout other than the row
+// interleaved one, every chunk goes element by element.
+template <class T, int SW, int SH, int NT>
+__device__ __forceinline__ void stage_rows(const StepParams &p, const T *fin, int ox, int oy,
+                                           T *st) {
+  constexpr int E = stage_chunk<T>(), NC = SW / E, N = SH * 9 * NC;
+  static_assert(SW % E == 0, "whole chunks per staged row");
+  const bool inter = p.frow == 9 * p.fplane;
+  for (int q = threadIdx.y * 32 + threadIdx.x; q < N; q += NT) {
+    const int R = q / NC, c = q - R * NC;
+    const int r = R / 9, i = R - 9 * r;
+    int gy = oy + r;
+    if (gy < 0 || gy >= p.ny) {
+      if (p.bc_top != BC_PERIODIC) continue;
+      gy = wrap_any(gy, p.ny);
+    }
+    const int gx = ox + c * E;
+    T *dst = st + (R * SW + c * E);
+    const T *src = fin + ((long long)gy * p.frow + (long long)i * p.fplane);
+    // a chunk wholly beyond a periodic seam is copied from its image (whole
+    // and aligned when nx is a multiple of the chunk)
+    int wx = gx;
+    if ((wx < 0 || wx >= p.nx) && p.bc_left == BC_PERIODIC) wx = wrap_any(wx, p.nx);
+    if (inter && wx >= 0 && wx + E <= p.nx && wx % E == 0) {
+      const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+      asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(src + wx)
+                   : "memory");
+    } else {
+      // across an edge or seam: element by element, every load issued
+      // before the first shared store
+      T v[E];
+      unsigned okm = 0u;
+#pragma unroll
+      for (int e = 0; e < E; ++e) {
+        int x = gx + e;
+        if (x < 0 || x >= p.nx) {
+          if (p.bc_left != BC_PERIODIC) continue;
+          x = wrap_any(x, p.nx);
+        }
+        v[e] = __ldcg(src + x);
+        okm |= 1u << e;
+      }
+#pragma unroll
+      for (int e = 0; e < E; ++e)
+        if (okm & (1u << e)) dst[e] = v[e];
+    }
+  }
+  asm volatile("cp.async.commit_group;" ::: "memory");
+}
+__device__ __forceinline__ void stage_wait() {
+  asm volatile("cp.async.wait_group 0;" ::: "memory");
+}
+
+// All nine streamed populations of the in-grid cell (x, y) (unwrapped on
+// periodic axes) from a staged region: plain pulls off the walls, the wall
+// rules otherwise (the values of gather, bit for bit).
+template <class T, class C, class A>
+__device__ __forceinline__ void pull_staged(const StepParams &p, const A &a, int x, int y,
+                                            C *f) {
+  if (off_walls(p, x, y)) {
+#pragma unroll
+    for (int i = 0; i < 9; ++i) f[i] = a.template load<C>(i, x - cxd(i), y - cyd(i));
+  } else {
+    pull_cell<T, C>(p, a, x, y, f);
+  }
+}
+
+// Whether the general tiles of storage type T stage their inputs (the
+// staged region of 8-byte populations would pass the 48 KB of static shared
+// memory; FP64 keeps per-cell global pulls).
+template <class T>
+constexpr bool stages() { return sizeof(T) <= 4; }
+
+// Staged region of a Lambda = 0 general tile: the tile widened by two cells
+// (the window's pulls), aliasing the window buffer until step n's stores.
+template <class T>
+constexpr int f2_stage_w() { return stage_width<T>(kF2Cols, 2); }
+constexpr int kF2SH = kF2Rows + 4;
+template <class T>
+constexpr int f2_buf() {
+  return stages<T>() && 9 * kF2SH * f2_stage_w<T>() > 9 * kF2H * kF2W
+             ? 9 * kF2SH * f2_stage_w<T>()
+             : 9 * kF2H * kF2W;
+}
+
 // What changes from one two-step phase to the next: phase k of a run reads
 // what phase k - 1 wrote (the two buffers alternate), advances steps
 // n + 2k and n + 2k + 1, and records into trace slots trace_slot + 2k and
@@ -175,23 +307,35 @@ __device__ __forceinline__ int tile_kind(const StepParams &p, int x0, int y0, in
 }
 
 // Blocks within reach of a wall, seam, source or receiver: every cell runs
-// the general rules.  Step n is evaluated at each window cell's wrapped
-// coordinate (cells beyond a non-periodic edge are never read: the wall
-// rules replace them); step n + 1 at the tile's cells.  Out of line so the
-// bulk path carries none of its registers.  Every thread calls it (one
-// barrier).
+// the general rules.  Step n is evaluated at each window cell (cells beyond
+// a non-periodic edge are never read: the wall rules replace them), its
+// pulls read from the input populations of the tile widened by two cells,
+// staged in the window buffer by one pass of loads; step n + 1 at the
+// tile's cells.  Out of line so the bulk path carries none of its
+// registers.  Every thread calls it (three barriers: staged, staged region
+// read, window written).
 //
-// Register budget: each step's pulls come first, when nothing else is live
-// (the out-of-line wall rule then saves no registers around its call), and
-// the displacement after step n goes through global memory (u + v^n stored,
-// reloaded for + v^{n+1}: the same two roundings), so nothing but the
-// block's tile position crosses the barrier.
+// Register budget: the body force of each step is summed (out of line, in
+// the sources' bounding box) before that step's pulls, and the displacement
+// after step n goes through global memory (u + v^n stored, reloaded for
+// + v^{n+1}: the same two roundings).
 template <class T, class C, class U>
 __device__ __noinline__ void step2_general(const StepParams &p, int x0, int y0, T *tile, int k) {
   // window cells lie within kF2Cols/2 + 1 columns and kF2Rows/2 + 1 rows of
   // the centre
   const unsigned smask = source_mask(p, x0 + kF2Cols / 2, y0 + kF2Rows / 2, kF2Cols / 2 + 2,
                                      kF2Rows / 2 + 2);
+  // the input populations of the window's pulls, staged in the window
+  // buffer (dead until step n's stores, after the second barrier)
+  constexpr int SW = f2_stage_w<T>();
+  const int sox = stage_origin<T>(x0, 2);
+  if constexpr (stages<T>()) {
+    stage_rows<T, SW, kF2SH, 32 * kF2Warps>(p, (const T *)phase2(p, k).fin, sox, y0 - 2, tile);
+    stage_wait();
+  }
+  __syncthreads();
+  C fs[9];
+  bool stored = false;
   {
     int ex, ey;
     bool core;
@@ -200,36 +344,31 @@ __device__ __noinline__ void step2_general(const StepParams &p, int x0, int y0, 
     int wx = x, wy = y;
     bool valid = true;
     if (x < 0 || x >= p.nx) {
-      if (p.bc_left == BC_PERIODIC) wx = ((x % p.nx) + p.nx) % p.nx;
+      if (p.bc_left == BC_PERIODIC) wx = wrap_any(x, p.nx);
       else valid = false;
     }
     if (y < 0 || y >= p.ny) {
-      if (p.bc_top == BC_PERIODIC) wy = ((y % p.ny) + p.ny) % p.ny;
+      if (p.bc_top == BC_PERIODIC) wy = wrap_any(y, p.ny);
       else valid = false;
     }
     if (valid) {
       const Phase2 ph = phase2(p, k);
       C Fx, Fy;
       body_force_cell<C>(p, wx, wy, ph.n, Fx, Fy, smask);
-      const T *fin = (const T *)ph.fin;
       C f[9];
-      if (wx >= 1 && wx < p.nx - 1 && wy >= 1 && wy < p.ny - 1) {
-        const T *b = fin + (wy * p.frow + wx);
-#pragma unroll
-        for (int i = 0; i < 9; ++i)
-          f[i] = ldp<T, C>(b + (i * p.fplane - cyd(i) * p.frow - cxd(i)), p);
+      if constexpr (stages<T>()) {
+        pull_staged<T, C>(p, StagePops<T, SW, kF2SH>{tile, sox, y0 - 2}, x, y, f);
       } else {
-        pull_cell<T, C>(p, GridPops<T>{fin, p.fplane, p.frow}, wx, wy, f);
+        gather<T, C>(p, (const T *)ph.fin, wx, wy, f);
       }
       const Moments<C> M = cell_moments<C>(f);
       Fx *= force_scale<T, C>(p);
       Fy *= force_scale<T, C>(p);
-      C jx, jy, Sx, Sy, fs[9];
+      C jx, jy, Sx, Sy;
       flux_and_source<C>(M.mx, M.my, C(0), C(0), Fx, Fy, sponge_A<C>(p, wx, wy), jx, jy, Sx, Sy);
       collide_cell<C>(M, jx, jy, Sx, Sy, par<C>(p.omega, p.omega_f), par<C>(p.fcoef, p.fcoef_f),
                       fs);
-#pragma unroll
-      for (int i = 0; i < 9; ++i) st<T, C>(tile + ((i * kF2H + ey) * kF2W + ex), fs[i]);
+      stored = true;
       if (core && x < p.nx && y < p.ny) {
         const C irho = irho_at<T, C>(p, x, y);
         const U vx = U(mul_rn(jx, irho)), vy = U(mul_rn(jy, irho));
@@ -242,10 +381,15 @@ __device__ __noinline__ void step2_general(const StepParams &p, int x0, int y0, 
       }
     }
   }
-  __syncthreads();
+  __syncthreads();  // every read of the staged region is done
   int ex, ey;
   bool core;
   window_cell(threadIdx.x, threadIdx.y, ex, ey, core);
+  if (stored) {
+#pragma unroll
+    for (int i = 0; i < 9; ++i) st<T, C>(tile + ((i * kF2H + ey) * kF2W + ex), fs[i]);
+  }
+  __syncthreads();
   const int x = x0 - 1 + ex, y = y0 - 1 + ey;
   if (!(core && x < p.nx && y < p.ny)) return;
   // step n + 1 of the tile's cell (x, y)
@@ -264,7 +408,7 @@ __device__ __noinline__ void step2_general(const StepParams &p, int x0, int y0, 
   const Moments<C> M = cell_moments<C>(f);
   Fx *= force_scale<T, C>(p);
   Fy *= force_scale<T, C>(p);
-  C jx, jy, Sx, Sy, fs[9];
+  C jx, jy, Sx, Sy;
   flux_and_source<C>(M.mx, M.my, C(0), C(0), Fx, Fy, sponge_A<C>(p, x, y), jx, jy, Sx, Sy);
   collide_cell<C>(M, jx, jy, Sx, Sy, par<C>(p.omega, p.omega_f), par<C>(p.fcoef, p.fcoef_f), fs);
   T *fout = (T *)ph.fout + (y * p.frow + x);
@@ -476,7 +620,7 @@ __global__ void __launch_bounds__(32 * kF2Warps, LBM_STEP2_MIN_BLOCKS)
   asm volatile("griddepcontrol.wait;" ::: "memory");
   asm volatile("griddepcontrol.launch_dependents;");
 #endif
-  __shared__ T tile[9 * kF2H * kF2W];
+  __shared__ __align__(16) T tile[f2_buf<T>()];
   const int2 t = tile_of_block(p.tiles2, p.tiles2_first, gridDim.x, blockIdx.x, p.reverse);
   step2_tile<T, C, U>(p, t.x, t.y, tile, 0);
 }
@@ -522,7 +666,7 @@ __device__ __forceinline__ int ld_volatile_int(const int *p) {
 template <class T, class C, class U>
 __global__ void __launch_bounds__(32 * kF2Warps, LBM_STEP2_MIN_BLOCKS)
     step2_persistent_kernel(const Step2Run r) {
-  __shared__ T tile[9 * kF2H * kF2W];
+  __shared__ __align__(16) T tile[f2_buf<T>()];
   __shared__ int stop;
   const int t = threadIdx.y * 32 + threadIdx.x;
   const int ntiles = r.ntx * r.nty;
