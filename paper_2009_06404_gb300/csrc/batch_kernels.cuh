@@ -118,7 +118,8 @@ static_assert(kF2Warps == kL2H && kF2W == kL2W && kF2H == kL2H,
               "the two kinds of two-step tile share one block shape");
 constexpr int kBatch2Threads = 32 * kF2Warps;
 
-// Shared memory of a two-step tile: the window of either kind, and the
+// Shared memory of a two-step tile: the window of either kind (large enough
+// for the staged inputs of a general tile, which it holds first), and the
 // density buffer of the density-gradient kind behind it.
 template <class T, class C>
 struct Batch2Smem {
