@@ -179,8 +179,8 @@ __global__ void __launch_bounds__(256) adj_local_kernel(const AdjParams a) {
     bool hit = false;
     const int s = s0 + lane;
     if (s < p.nsrc) {
-      const SourceDev &q = p.src[s];
-      int dy = yc - q.yc, dx = xmid - q.xc;
+      const int4 qb = src_bound(p, s);
+      int dy = yc - qb.y, dx = xmid - qb.x;
       if (p.bc_top == BC_PERIODIC) {
         if (dy > p.ny / 2) dy -= p.ny;
         else if (dy < -(p.ny / 2)) dy += p.ny;
@@ -189,7 +189,7 @@ __global__ void __launch_bounds__(256) adj_local_kernel(const AdjParams a) {
         if (dx > p.nx / 2) dx -= p.nx;
         else if (dx < -(p.nx / 2)) dx += p.nx;
       }
-      hit = abs(dy) <= q.rb && abs(dx) <= q.rb + 17;
+      hit = abs(dy) <= qb.z && abs(dx) <= qb.z + 17;
     }
     unsigned mask = __ballot_sync(0xffffffffu, hit);
     while (mask) {
@@ -511,8 +511,8 @@ __global__ void __launch_bounds__(kAdjThreads, LBM_ADJ_MIN_BLOCKS) adj_fused_ker
       if (own && src_blk) {
         // dF/dA_s = dir_s g_s(x) r_s(n) (integer footprint test first)
         for (int s = 0; s < p.nsrc; ++s) {
-          const SourceDev &q = p.src[s];
-          int dy = gy - q.yc, dx = gx - q.xc;
+          const int4 qb = src_bound(p, s);
+          int dy = gy - qb.y, dx = gx - qb.x;
           if (pery) {
             if (dy > p.ny / 2) dy -= p.ny;
             else if (dy < -(p.ny / 2)) dy += p.ny;
@@ -521,7 +521,8 @@ __global__ void __launch_bounds__(kAdjThreads, LBM_ADJ_MIN_BLOCKS) adj_fused_ker
             if (dx > p.nx / 2) dx -= p.nx;
             else if (dx < -(p.nx / 2)) dx += p.nx;
           }
-          if (abs(dy) > q.rb || abs(dx) > q.rb) continue;
+          if (abs(dy) > qb.z || abs(dx) > qb.z) continue;
+          const SourceDev &q = p.src[s];
           const double v = ((double)hbx * q.dirx + (double)hby * q.diry) *
                            source_shape(q, gx, gy, p.n, p.nx, p.ny, perx, pery);
           if (v != 0.0) atomicAdd(&a.g_amp[s], v);

@@ -96,6 +96,7 @@ Layout make_layout(const lbm_elastic_config *c) {
   L.lam = take((size_t)L.mat_count * L.csize);
   L.irho = take((size_t)L.mat_count * L.csize);
   L.src = take((size_t)c->max_sources * sizeof(SourceDev) + 8);
+  L.srcb = take((size_t)c->max_sources * sizeof(int4) + 16);
   L.rec_ptr = take(((size_t)L.rec_tiles + 1) * sizeof(int));
   L.rec_xy = take((size_t)c->max_receivers * 2 * sizeof(int) + 8);
   L.rec_id = take((size_t)c->max_receivers * sizeof(int) + 8);
@@ -424,6 +425,7 @@ StepParams base_params(lbm_elastic_t *h) {
   p.mat_per_cell = c.material_per_cell;
   p.src = at<SourceDev>(h, L.src);
   p.nsrc = h->nsrc;
+  p.srcb = at<int4>(h, L.srcb);
   p.n = h->step;
   p.trace_slot = -1;
   p.trace_end = h->cfg.max_steps_traced;
@@ -830,9 +832,14 @@ lbm_status lbm_elastic_set_sources(lbm_elastic_t *h, const lbm_source *src, int 
   h->src_box[2] = by0;
   h->src_box[3] = by1;
   h->src_host = v;
-  if (n)
+  std::vector<int4> bounds((size_t)n);
+  for (int k = 0; k < n; ++k) bounds[k] = make_int4(v[k].xc, v[k].yc, v[k].rb, 0);
+  if (n) {
     LBM_CUDA(h, cudaMemcpyAsync(h->ws + h->L.src, h->src_host.data(), n * sizeof(SourceDev),
                                 cudaMemcpyHostToDevice, h->stream));
+    LBM_CUDA(h, cudaMemcpyAsync(h->ws + h->L.srcb, bounds.data(), n * sizeof(int4),
+                                cudaMemcpyHostToDevice, h->stream));
+  }
   LBM_CUDA(h, cudaStreamSynchronize(h->stream));
   h->nsrc = n;
   return upload_tile_order(h);

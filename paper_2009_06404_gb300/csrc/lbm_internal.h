@@ -17,7 +17,7 @@ struct Layout {
   int finter = 1;                 // population rows interleaved ([y][i][x])
   long long fplane = 0, frow = 0; // population strides (elements)
   size_t tsize = 0, usize = 0, csize = 0;
-  size_t f[2] = {0, 0}, u = 0, lam = 0, irho = 0, src = 0, rec_ptr = 0, rec_xy = 0,
+  size_t f[2] = {0, 0}, u = 0, lam = 0, irho = 0, src = 0, srcb = 0, rec_ptr = 0, rec_xy = 0,
          rec_id = 0, traces = 0, partials = 0, flags = 0, stage = 0, total = 0;
   int rec_tiles_x = 0, rec_tiles = 0, stage_rows = 0;
   size_t done = 0;                // persistent two-step form: per-tile phase counters

@@ -71,6 +71,10 @@ struct StepParams {
   int mat_per_cell;
   const SourceDev *src;
   int nsrc;
+  // (xc, yc, rb, 0) of every source, packed: the per-block and per-cell
+  // source tests read one 16-byte entry per source (one coalesced load per
+  // warp) instead of three fields of each full record
+  const int4 *srcb;
   long long n;       // index of this step (force time t = n)
   int trace_slot;    // >= 0: record receivers into this slot
   int trace_end;     // two-step launches: trace slots below this exist
@@ -101,6 +105,9 @@ struct StepParams {
   int row0, nrows;
   double *out[8];           // ux uy vx vy rho pxx pxy pyy, [nrows][nx] each
 };
+
+// (xc, yc, rb) of source s in x, y, z.
+__device__ __forceinline__ int4 src_bound(const StepParams &p, int s) { return p.srcb[s]; }
 
 // ------------------------------------------------------------ lattice
 
@@ -548,8 +555,8 @@ __device__ void body_force(const StepParams &p, int x, int y, C &Fx, C &Fy) {
     bool hit = false;
     const int s = s0 + lane;
     if (s < p.nsrc) {
-      const SourceDev &q = p.src[s];
-      int dy = y - q.yc, dx = xmid - q.xc;
+      const int4 qb = src_bound(p, s);
+      int dy = y - qb.y, dx = xmid - qb.x;
       if (p.bc_top == BC_PERIODIC) {
         if (dy > p.ny / 2) dy -= p.ny;
         else if (dy < -(p.ny / 2)) dy += p.ny;
@@ -558,7 +565,7 @@ __device__ void body_force(const StepParams &p, int x, int y, C &Fx, C &Fy) {
         if (dx > p.nx / 2) dx -= p.nx;
         else if (dx < -(p.nx / 2)) dx += p.nx;
       }
-      hit = abs(dy) <= q.rb && abs(dx) <= q.rb + 17;
+      hit = abs(dy) <= qb.z && abs(dx) <= qb.z + 17;
     }
     unsigned mask = __ballot_sync(0xffffffffu, hit);
     while (mask) {
@@ -582,8 +589,8 @@ __device__ __forceinline__ unsigned source_mask(const StepParams &p, int cx, int
   if (p.nsrc > 32) return 0xffffffffu;
   bool hit = false;
   if ((int)threadIdx.x < p.nsrc) {
-    const SourceDev &q = p.src[threadIdx.x];
-    int dx = cx - q.xc, dy = cy - q.yc;
+    const int4 qb = src_bound(p, threadIdx.x);
+    int dx = cx - qb.x, dy = cy - qb.y;
     if (p.bc_left == BC_PERIODIC) {
       if (dx > p.nx / 2) dx -= p.nx;
       else if (dx < -(p.nx / 2)) dx += p.nx;
@@ -592,7 +599,7 @@ __device__ __forceinline__ unsigned source_mask(const StepParams &p, int cx, int
       if (dy > p.ny / 2) dy -= p.ny;
       else if (dy < -(p.ny / 2)) dy += p.ny;
     }
-    hit = abs(dx) <= q.rb + hx && abs(dy) <= q.rb + hy;
+    hit = abs(dx) <= qb.z + hx && abs(dy) <= qb.z + hy;
   }
   return __ballot_sync(0xffffffffu, hit);
 }
@@ -602,8 +609,8 @@ __device__ __forceinline__ unsigned source_mask(const StepParams &p, int cx, int
 template <class C>
 __device__ __forceinline__ void add_source(const StepParams &p, int s, int x, int y, long long n,
                                            C &Fx, C &Fy) {
-  const SourceDev &q = p.src[s];
-  int dy = y - q.yc, dx = x - q.xc;
+  const int4 qb = src_bound(p, s);
+  int dy = y - qb.y, dx = x - qb.x;
   if (p.bc_top == BC_PERIODIC) {
     if (dy > p.ny / 2) dy -= p.ny;
     else if (dy < -(p.ny / 2)) dy += p.ny;
@@ -612,8 +619,8 @@ __device__ __forceinline__ void add_source(const StepParams &p, int s, int x, in
     if (dx > p.nx / 2) dx -= p.nx;
     else if (dx < -(p.nx / 2)) dx += p.nx;
   }
-  if (abs(dy) <= q.rb && abs(dx) <= q.rb) {
-    const auto F = source_term(q, x, y, n, p.nx, p.ny, p.bc_left == BC_PERIODIC,
+  if (abs(dy) <= qb.z && abs(dx) <= qb.z) {
+    const auto F = source_term(p.src[s], x, y, n, p.nx, p.ny, p.bc_left == BC_PERIODIC,
                                p.bc_top == BC_PERIODIC, C(0));
     Fx += C(F.x);
     Fy += C(F.y);
@@ -871,8 +878,8 @@ __device__ __forceinline__ bool block_is_special(const StepParams &p, int x0, in
   const int lane = threadIdx.x & 31;
   bool hit = false;
   if (near_src && lane < p.nsrc) {
-    const SourceDev &q = p.src[lane];
-    int dx = x0 + W / 2 - q.xc, dy = y0 + h / 2 - q.yc;
+    const int4 qb = src_bound(p, lane);
+    int dx = x0 + W / 2 - qb.x, dy = y0 + h / 2 - qb.y;
     if (p.bc_left == BC_PERIODIC) {
       if (dx > p.nx / 2) dx -= p.nx;
       else if (dx < -(p.nx / 2)) dx += p.nx;
@@ -881,7 +888,7 @@ __device__ __forceinline__ bool block_is_special(const StepParams &p, int x0, in
       if (dy > p.ny / 2) dy -= p.ny;
       else if (dy < -(p.ny / 2)) dy += p.ny;
     }
-    hit = abs(dx) <= q.rb + W / 2 + 1 + halo && abs(dy) <= q.rb + h / 2 + 1 + halo;
+    hit = abs(dx) <= qb.z + W / 2 + 1 + halo && abs(dy) <= qb.z + h / 2 + 1 + halo;
   }
   if (near_rec && lane >= 30) {
     // receiver tiles are 64 x 4; this block spans one tile column, and rows

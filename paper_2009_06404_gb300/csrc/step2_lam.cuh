@@ -74,8 +74,8 @@ __device__ __forceinline__ bool lam_tile_special(const StepParams &p, int x0, in
   bool hit = false;
   if (near_src && lane < p.nsrc) {
     // W2 cells lie within W/2 + 2 columns and H/2 + 2 rows of the centre
-    const SourceDev &q = p.src[lane];
-    int dx = x0 + W / 2 - q.xc, dy = y0 + H / 2 - q.yc;
+    const int4 qb = src_bound(p, lane);
+    int dx = x0 + W / 2 - qb.x, dy = y0 + H / 2 - qb.y;
     if (p.bc_left == BC_PERIODIC) {
       if (dx > p.nx / 2) dx -= p.nx;
       else if (dx < -(p.nx / 2)) dx += p.nx;
@@ -84,7 +84,7 @@ __device__ __forceinline__ bool lam_tile_special(const StepParams &p, int x0, in
       if (dy > p.ny / 2) dy -= p.ny;
       else if (dy < -(p.ny / 2)) dy += p.ny;
     }
-    hit = abs(dx) <= q.rb + W / 2 + 3 && abs(dy) <= q.rb + H / 2 + 3;
+    hit = abs(dx) <= qb.z + W / 2 + 3 && abs(dy) <= qb.z + H / 2 + 3;
   }
   if (near_rec) {
     const int tx0 = x0 / kRecTileX, tx1 = min((x0 + W - 1) / kRecTileX, p.rec_tiles_x - 1);

@@ -278,8 +278,8 @@ __device__ __forceinline__ int tile_kind(const StepParams &p, int x0, int y0, in
   bool hit_src = near_src && p.nsrc > 32;
   if (near_src && p.nsrc <= 32 && lane < p.nsrc) {
     // window cells lie within W/2 + 1 columns and H/2 + 1 rows of the centre
-    const SourceDev &q = p.src[lane];
-    int dx = x0 + W / 2 - q.xc, dy = y0 + H / 2 - q.yc;
+    const int4 qb = src_bound(p, lane);
+    int dx = x0 + W / 2 - qb.x, dy = y0 + H / 2 - qb.y;
     if (p.bc_left == BC_PERIODIC) {
       if (dx > p.nx / 2) dx -= p.nx;
       else if (dx < -(p.nx / 2)) dx += p.nx;
@@ -288,7 +288,7 @@ __device__ __forceinline__ int tile_kind(const StepParams &p, int x0, int y0, in
       if (dy > p.ny / 2) dy -= p.ny;
       else if (dy < -(p.ny / 2)) dy += p.ny;
     }
-    hit_src = abs(dx) <= q.rb + W / 2 + 2 && abs(dy) <= q.rb + H / 2 + 2;
+    hit_src = abs(dx) <= qb.z + W / 2 + 2 && abs(dy) <= qb.z + H / 2 + 2;
   }
   bool hit_rec = false;
   if (near_rec) {
