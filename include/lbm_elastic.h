@@ -166,32 +166,17 @@ lbm_status lbm_elastic_reset(lbm_elastic_t *h);
  * have been recorded since the last reset / set_receivers / set_state. */
 lbm_status lbm_elastic_step(lbm_elastic_t *h, int nsteps);
 
-/* Time steps per kernel launch in lbm_elastic_step: 1; 2, which advances
+/* Time steps per kernel launch in lbm_elastic_step: 1, or 2, which advances
  * two steps per launch with the intermediate populations kept in on-chip
- * shared memory (each population then crosses HBM once per two steps); or
- * 0, the persistent form of the two-step update: all steps of one
- * lbm_elastic_step call in one cooperative launch, tiles of the next pair of
- * steps starting as soon as their neighbours finish the previous pair (no
- * grid-wide barrier between pairs).  Until set, the handle chooses: 2 for
- * FP32, and for 16-bit storage when every Lambda is zero; 1 for FP64
- * (bound by the FP64 arithmetic rather than by memory) and for 16-bit
- * storage with the density-gradient force (issue-bound, where the larger
- * two-step window costs more than the bytes it saves).  The persistent
- * form needs every Lambda zero and grid sizes that leave no tile one cell wide or high
- * (nx mod 30 != 1, ny mod 14 != 1), else it takes two-step launches; an
- * odd remainder takes a one-step launch.  All settings give bit-identical
- * states and traces.  Returns LBM_ERR_ARG for any other value. */
+ * shared memory (each population then crosses HBM once per two steps).
+ * Until set, the handle chooses: 2 for FP32, and for 16-bit storage when
+ * every Lambda is zero; 1 for FP64 (bound by the FP64 arithmetic rather
+ * than by memory) and for 16-bit storage with the density-gradient force
+ * (issue-bound, where the larger two-step window costs more than the bytes
+ * it saves).  An odd remainder takes a one-step launch.  Both settings give
+ * bit-identical states and traces.  Returns LBM_ERR_ARG for any other
+ * value. */
 lbm_status lbm_elastic_set_steps_per_launch(lbm_elastic_t *h, int steps);
-
-/* Persistent form (steps_per_launch = 0): a tile waits at most wait_cycles
- * SM clock cycles for its neighbours (0: the default, about 2 s); past it
- * the launch stops and the next synchronising call returns
- * LBM_ERR_TIMEOUT.  hold_tile >= 0 (for tests of that path) keeps tile
- * hold_tile (row-major over 30 x 14 tiles) from publishing its progress in
- * the next persistent launch, so that its neighbours time out; -1: none.
- * Returns LBM_ERR_ARG for wait_cycles < 0 or a tile out of range. */
-lbm_status lbm_elastic_set_persistent_wait(lbm_elastic_t *h, long long wait_cycles,
-                                           int hold_tile);
 
 /* Index n of the next step (number of steps taken since reset or the step
  * given to set_state). */

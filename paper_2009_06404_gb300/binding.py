@@ -30,7 +30,7 @@ SYMBOLS = [
     "lbm_elastic_workspace_bytes", "lbm_elastic_create", "lbm_elastic_set_material",
     "lbm_elastic_set_sources", "lbm_elastic_set_receivers", "lbm_elastic_set_sponges",
     "lbm_elastic_reset", "lbm_elastic_step", "lbm_elastic_set_steps_per_launch",
-    "lbm_elastic_set_persistent_wait", "lbm_elastic_step_index", "lbm_elastic_read_fields",
+    "lbm_elastic_step_index", "lbm_elastic_read_fields",
     "lbm_elastic_traces_recorded", "lbm_elastic_read_traces", "lbm_elastic_set_state",
     "lbm_elastic_get_state", "lbm_elastic_checkpoint_bytes", "lbm_elastic_save",
     "lbm_elastic_load", "lbm_elastic_moment_sums", "lbm_elastic_sync",
@@ -124,7 +124,6 @@ def load_library(build_if_missing: bool = False):
             "lbm_elastic_reset": (ip, [vp]),
             "lbm_elastic_step": (ip, [vp, ip]),
             "lbm_elastic_set_steps_per_launch": (ip, [vp, ip]),
-            "lbm_elastic_set_persistent_wait": (ip, [vp, ctypes.c_longlong, ip]),
             "lbm_elastic_step_index": (ctypes.c_longlong, [vp]),
             "lbm_elastic_read_fields": (ip, [vp] + [vp] * 8 + [ip]),
             "lbm_elastic_traces_recorded": (ip, [vp]),
@@ -308,16 +307,9 @@ class ElasticLBM:
         return self._check(self.L.lbm_elastic_step(self.h, int(nsteps)))
 
     def set_steps_per_launch(self, steps: int):
-        """1; 2: two time steps per kernel launch where the grid allows it;
-        0: all steps of a call in one persistent launch, two at a time (same
-        results bit for bit)."""
+        """1, or 2: two time steps per kernel launch (same results bit for
+        bit)."""
         return self._check(self.L.lbm_elastic_set_steps_per_launch(self.h, int(steps)))
-
-    def set_persistent_wait(self, wait_cycles: int = 0, hold_tile: int = -1):
-        """Wait limit of the persistent form (SM cycles, 0: default) and, for
-        tests, a tile that does not publish its progress in the next run."""
-        return self._check(self.L.lbm_elastic_set_persistent_wait(self.h, int(wait_cycles),
-                                                                   int(hold_tile)))
 
     @property
     def step_index(self) -> int:

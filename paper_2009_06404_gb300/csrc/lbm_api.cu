@@ -103,10 +103,7 @@ Layout make_layout(const lbm_elastic_config *c) {
   L.traces = take((size_t)c->max_steps_traced * c->max_receivers * 4 * sizeof(double) + 8);
   L.partials = take((size_t)(kRedBlocks + 1) * 8 * sizeof(double));
   L.flags = take(64);
-  L.tiles2x = (c->nx + kF2Cols - 1) / kF2Cols;
-  L.tiles2y = (c->ny + kF2Rows - 1) / kF2Rows;
-  L.done = take((size_t)L.tiles2x * L.tiles2y * sizeof(unsigned));
-  L.ntiles2 = (long long)L.tiles2x * L.tiles2y;
+  L.ntiles2 = (long long)((c->nx + kF2Cols - 1) / kF2Cols) * ((c->ny + kF2Rows - 1) / kF2Rows);
   L.ntiles2l = (long long)((c->nx + kL2Cols - 1) / kL2Cols) * ((c->ny + kL2Rows - 1) / kL2Rows);
   L.order2 = take((size_t)L.ntiles2 * sizeof(int2));
   L.order2l = take((size_t)L.ntiles2l * sizeof(int2));
@@ -607,66 +604,6 @@ static lbm_status handle_step2(lbm_elastic_t *h) {
   return LBM_OK;
 }
 
-// Wait limit of the persistent two-step form (SM cycles, about 2 s).
-constexpr long long kPersistWaitCycles = 4000000000LL;
-
-// Whether the persistent two-step form can run this handle: the two-step
-// conditions, and no tile one cell wide or high (a tile's pulls then reach
-// only its eight neighbours).
-static bool persistent_ok(const lbm_elastic_t *h) {
-  return !h->lambda_nonzero && h->cfg.nx % kF2Cols != 1 &&
-         h->cfg.ny % kF2Rows != 1;
-}
-
-// nphase two-step phases (steps n .. n + 2 nphase - 1) in one cooperative
-// launch of the persistent kernel.
-static lbm_status handle_step2_run(lbm_elastic_t *h, int nphase) {
-  const lbm_elastic_config &c = h->cfg;
-  const bool u64 = c.u_fp64 != 0;
-  if (h->persist_blocks < 0) {
-    int dev = 0;
-    if (h->nsm <= 0 && (cudaGetDevice(&dev) != cudaSuccess ||
-                        cudaDeviceGetAttribute(&h->nsm, cudaDevAttrMultiProcessorCount, dev) !=
-                            cudaSuccess))
-      return cuda_fail(h, cudaGetLastError(), "device query");
-    h->persist_blocks = c.storage == LBM_F64   ? step2_run_blocks_f64()
-                        : c.storage == LBM_F32 ? step2_run_blocks_f32(u64)
-                                               : step2_run_blocks_16(c.storage == LBM_BF16, u64);
-  }
-  if (h->persist_blocks <= 0) return fail(h, LBM_ERR_CUDA, "persistent kernel cannot be resident");
-  Step2Run r;
-  memset(&r, 0, sizeof(r));
-  r.p = base_params(h);
-  r.p.reverse = 0;
-  if (h->nrec > 0 && h->traced < c.max_steps_traced) r.p.trace_slot = h->traced;
-  r.nphase = nphase;
-  r.ntx = h->L.tiles2x;
-  r.nty = h->L.tiles2y;
-  r.done = at<unsigned>(h, h->L.done);
-  r.wait_cycles = h->persist_wait > 0 ? h->persist_wait : kPersistWaitCycles;
-  r.hold_tile = h->persist_hold;
-  const long long ntiles = (long long)r.ntx * r.nty;
-  LBM_CUDA(h, cudaMemsetAsync(r.done, 0, (size_t)ntiles * sizeof(unsigned), h->stream));
-  const int grid = (int)std::min<long long>((long long)nphase * ntiles,
-                                            (long long)h->persist_blocks * h->nsm);
-  cudaError_t e;
-  if (c.storage == LBM_F64)
-    e = launch_step2_run_f64(r, grid, h->stream);
-  else if (c.storage == LBM_F32)
-    e = launch_step2_run_f32(r, u64, grid, h->stream);
-  else
-    e = launch_step2_run_16(r, c.storage == LBM_BF16, u64, grid, h->stream);
-  if (e != cudaSuccess) return cuda_fail(h, e, "persistent two-step kernel launch");
-  if (lbm_status st = check_launch(h, "persistent two-step kernel launch")) return st;
-  if (h->nrec > 0)
-    h->traced += (int)std::max<long long>(
-        0, std::min<long long>(2LL * nphase, (long long)c.max_steps_traced - h->traced));
-  h->persist_hold = -1;
-  h->cur ^= nphase & 1;
-  h->step += 2LL * nphase;
-  return LBM_OK;
-}
-
 extern "C" {
 
 size_t lbm_elastic_workspace_bytes(const lbm_elastic_config *cfg) {
@@ -925,13 +862,9 @@ lbm_status lbm_elastic_step(lbm_elastic_t *h, int nsteps) {
     spl = (h->cfg.storage == LBM_F64 || (b16 && h->lambda_nonzero)) ? 1 : 2;
   }
   int s = 0;
-  if (spl == 0 && persistent_ok(h) && nsteps >= 2) {
-    if (lbm_status st = handle_step2_run(h, nsteps / 2)) return st;
-    s = nsteps / 2 * 2;
-  } else if (spl != 1) {
+  if (spl == 2)
     for (; s + 2 <= nsteps; s += 2)
       if (lbm_status st = handle_step2(h)) return st;
-  }
   for (; s < nsteps; ++s)
     if (lbm_status st = handle_step(h, nullptr)) return st;
   return LBM_OK;
@@ -939,19 +872,8 @@ lbm_status lbm_elastic_step(lbm_elastic_t *h, int nsteps) {
 
 lbm_status lbm_elastic_set_steps_per_launch(lbm_elastic_t *h, int steps) {
   if (!h) return LBM_ERR_ARG;
-  if (steps < 0 || steps > 2) return fail(h, LBM_ERR_ARG, "steps per launch must be 0, 1 or 2");
+  if (steps < 1 || steps > 2) return fail(h, LBM_ERR_ARG, "steps per launch must be 1 or 2");
   h->steps_per_launch = steps;
-  return LBM_OK;
-}
-
-lbm_status lbm_elastic_set_persistent_wait(lbm_elastic_t *h, long long wait_cycles,
-                                           int hold_tile) {
-  if (!h) return LBM_ERR_ARG;
-  if (wait_cycles < 0) return fail(h, LBM_ERR_ARG, "wait_cycles < 0");
-  if (hold_tile < -1 || hold_tile >= h->L.tiles2x * h->L.tiles2y)
-    return fail(h, LBM_ERR_ARG, "hold_tile out of range");
-  h->persist_wait = wait_cycles;
-  h->persist_hold = hold_tile;
   return LBM_OK;
 }
 

@@ -20,8 +20,6 @@ struct Layout {
   size_t f[2] = {0, 0}, u = 0, lam = 0, irho = 0, src = 0, srcb = 0, rec_ptr = 0, rec_xy = 0,
          rec_id = 0, traces = 0, partials = 0, flags = 0, stage = 0, total = 0;
   int rec_tiles_x = 0, rec_tiles = 0, stage_rows = 0;
-  size_t done = 0;                // persistent two-step form: per-tile phase counters
-  int tiles2x = 0, tiles2y = 0;   // its tiles per row and per column
   size_t order2 = 0, order2l = 0; // two-step tiles in launch order (int2), both geometries
   long long ntiles2 = 0, ntiles2l = 0;
   long long mat_count = 0;
@@ -41,10 +39,7 @@ struct lbm_elastic {
   int traced = 0;
   int nsrc = 0, nrec = 0;
   bool lambda_nonzero = false;
-  int steps_per_launch = -1;   // lbm_elastic_step: 1, 2, 0 (persistent two-step form), -1 auto
-  long long persist_wait = 0;  // persistent form: wait limit in SM cycles (0: default)
-  int persist_hold = -1;       // persistent form, tests: tile that never publishes
-  int persist_blocks = -1;     // resident blocks per SM of the persistent kernel (-1: unknown)
+  int steps_per_launch = -1;   // lbm_elastic_step: 1, 2, -1 auto
   long long launches = 0;
   std::vector<lbm::SourceDev> src_host;
   std::vector<int> rec_host;        // receivers (x, y), as set

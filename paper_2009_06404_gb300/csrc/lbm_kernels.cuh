@@ -151,7 +151,7 @@ template <> __device__ __forceinline__ void st<__nv_bfloat16, float>(__nv_bfloat
 // Global loads of populations and displacements go to L2 directly (ld.cg):
 // within a step no cell's value is loaded twice by one block, and a kernel
 // that advances several steps with blocks waiting on one another (the
-// persistent two-step kernel) must not read a stale line from the SM's L1.
+// persistent batched kernel) must not read a stale line from the SM's L1.
 template <class T, class C> __device__ __forceinline__ C ldg(const T *p) { return C(__ldcg(p)); }
 template <> __device__ __forceinline__ float ldg<__half, float>(const __half *p) {
   return __half2float(__ldcg(p));

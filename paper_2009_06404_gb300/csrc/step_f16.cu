@@ -34,22 +34,6 @@ static void launch2(const StepParams &p, cudaStream_t s) {
   launch_pdl(step2_kernel<T, float, U>, step2_grid(p.nx, p.ny), step2_block(), s, p);
 }
 
-cudaError_t launch_step2_run_16(const Step2Run &r, bool bf16, bool u64, int grid,
-                                cudaStream_t s) {
-  if (bf16)
-    return u64 ? launch_step2_run_t<__nv_bfloat16, float, double>(r, grid, s)
-               : launch_step2_run_t<__nv_bfloat16, float, float>(r, grid, s);
-  return u64 ? launch_step2_run_t<__half, float, double>(r, grid, s)
-             : launch_step2_run_t<__half, float, float>(r, grid, s);
-}
-int step2_run_blocks_16(bool bf16, bool u64) {
-  if (bf16)
-    return u64 ? step2_persistent_blocks_t<__nv_bfloat16, float, double>()
-               : step2_persistent_blocks_t<__nv_bfloat16, float, float>();
-  return u64 ? step2_persistent_blocks_t<__half, float, double>()
-             : step2_persistent_blocks_t<__half, float, float>();
-}
-
 template <class T, class U>
 static void launch2l(const StepParams &p, cudaStream_t s) {
   launch_pdl(step2_lam_kernel<T, float, U>, step2_lam_grid(p.nx, p.ny), step2_lam_block(), s, p);

@@ -30,19 +30,10 @@ void launch_step2_f32(const StepParams &p, bool u64, cudaStream_t s) {
   else launch_pdl(step2_kernel<float, float, float>, grid, block, s, p);
 }
 
-cudaError_t launch_step2_run_f32(const Step2Run &r, bool u64, int grid, cudaStream_t s) {
-  return u64 ? launch_step2_run_t<float, float, double>(r, grid, s)
-             : launch_step2_run_t<float, float, float>(r, grid, s);
-}
 void launch_step2_lam_f32(const StepParams &p, bool u64, cudaStream_t s) {
   const dim3 grid = step2_lam_grid(p.nx, p.ny), block = step2_lam_block();
   if (u64) launch_pdl(step2_lam_kernel<float, float, double>, grid, block, s, p);
   else launch_pdl(step2_lam_kernel<float, float, float>, grid, block, s, p);
-}
-
-int step2_run_blocks_f32(bool u64) {
-  return u64 ? step2_persistent_blocks_t<float, float, double>()
-             : step2_persistent_blocks_t<float, float, float>();
 }
 
 }  // namespace lbm

@@ -20,11 +20,6 @@ void launch_step2_f64(const StepParams &p, cudaStream_t s) {
   launch_pdl(step2_kernel<double, double, double>, step2_grid(p.nx, p.ny), step2_block(), s, p);
 }
 
-cudaError_t launch_step2_run_f64(const Step2Run &r, int grid, cudaStream_t s) {
-  return launch_step2_run_t<double, double, double>(r, grid, s);
-}
-int step2_run_blocks_f64() { return step2_persistent_blocks_t<double, double, double>(); }
-
 void launch_step2_lam_f64(const StepParams &p, cudaStream_t s) {
   launch_pdl(step2_lam_kernel<double, double, double>, step2_lam_grid(p.nx, p.ny),
              step2_lam_block(), s, p);

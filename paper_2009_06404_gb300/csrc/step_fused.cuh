@@ -204,9 +204,10 @@ constexpr int f2_buf() {
              : 9 * kF2H * kF2W;
 }
 
-// What changes from one two-step phase to the next: phase k of a run reads
-// what phase k - 1 wrote (the two buffers alternate), advances steps
-// n + 2k and n + 2k + 1, and records into trace slots trace_slot + 2k and
+// What changes from one two-step phase to the next: phase k after the one
+// the parameters describe (every launch passes k = 0) reads what phase
+// k - 1 wrote (the two buffers alternate), advances steps n + 2k and
+// n + 2k + 1, and records into trace slots trace_slot + 2k and
 // trace_slot + 2k + 1 while they exist.  The rest of the step's parameters
 // stay in the kernel's parameter space.
 struct Phase2 {
@@ -625,99 +626,6 @@ __global__ void __launch_bounds__(32 * kF2Warps, LBM_STEP2_MIN_BLOCKS)
   step2_tile<T, C, U>(p, t.x, t.y, tile, 0);
 }
 
-// ------------------------------------------------------------ persistent form
-//
-// Many two-step phases in one launch, without a grid-wide barrier between
-// them.  The (phase, tile) pairs are numbered phase by phase, tiles row by
-// row, and block b takes pairs b, b + grid, b + 2 grid, ...  Tile t of phase
-// k reads what the tiles around it (itself and its eight neighbours, which
-// hold every cell within two of its cells) wrote in phase k - 1, and
-// overwrites cells those tiles read in phase k - 1; so it waits until each
-// of them has published the completion of phase k - 1 (done[] counts
-// completed phases; release store after the tile's writes, acquire load
-// before its reads).  Every pair it waits for has a smaller number, and the
-// smallest unfinished pair waits for nothing, so with all blocks resident
-// (cooperative launch) the run cannot deadlock.  Each wait is bounded: past
-// wait_cycles, or once another wait has given up, bit 1 of *p.err is set
-// and the block stops.  The tail of one phase overlaps the start of the
-// next, which a launch per phase cannot do.
-
-struct Step2Run {
-  StepParams p;         // phase 0 (p.fin, p.fout, p.n, p.trace_slot, p.trace_end)
-  int nphase;           // phases (two steps each) of this launch
-  int ntx, nty;         // tiles per row and per column
-  unsigned *done;       // per tile: phases completed (zero at launch)
-  long long wait_cycles;
-  int hold_tile;        // for tests: this tile never publishes (-1: none)
-};
-
-__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned *p) {
-  unsigned v;
-  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-  return v;
-}
-__device__ __forceinline__ void st_release_u32(unsigned *p, unsigned v) {
-  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
-}
-__device__ __forceinline__ int ld_volatile_int(const int *p) {
-  return *(const volatile int *)p;
-}
-
-template <class T, class C, class U>
-__global__ void __launch_bounds__(32 * kF2Warps, LBM_STEP2_MIN_BLOCKS)
-    step2_persistent_kernel(const Step2Run r) {
-  __shared__ __align__(16) T tile[f2_buf<T>()];
-  __shared__ int stop;
-  const int t = threadIdx.y * 32 + threadIdx.x;
-  const int ntiles = r.ntx * r.nty;
-  const long long total = (long long)r.nphase * ntiles;
-  for (long long j = blockIdx.x; j < total; j += gridDim.x) {
-    const int k = (int)(j / ntiles), ti = (int)(j - (long long)k * ntiles);
-    const int by = ti / r.ntx, bx = ti - by * r.ntx;
-    if (threadIdx.y == 0) {
-      // lanes 0..8: the tile and its neighbours (wrapped on periodic axes,
-      // absent beyond a wall) must have completed phase k - 1
-      bool gave_up = false;
-      if (threadIdx.x < 9) {
-        int nbx = bx + (int)threadIdx.x % 3 - 1, nby = by + (int)threadIdx.x / 3 - 1;
-        bool need = true;
-        if (nbx < 0 || nbx >= r.ntx) {
-          if (r.p.bc_left == BC_PERIODIC) nbx = (nbx + r.ntx) % r.ntx;
-          else need = false;
-        }
-        if (nby < 0 || nby >= r.nty) {
-          if (r.p.bc_top == BC_PERIODIC) nby = (nby + r.nty) % r.nty;
-          else need = false;
-        }
-        if (need) {
-          const unsigned *d = r.done + (nby * r.ntx + nbx);
-          const long long t0 = clock64();
-          while (ld_acquire_u32(d) < (unsigned)k) {
-            if (clock64() - t0 > r.wait_cycles || (ld_volatile_int(r.p.err) & 2)) {
-              gave_up = true;
-              break;
-            }
-            __nanosleep(64);
-          }
-        }
-      }
-      const bool any = __ballot_sync(0xffffffffu, gave_up) != 0u;
-      if (threadIdx.x == 0) {
-        if (any) atomicOr(r.p.err, 2);
-        stop = any;
-      }
-    }
-    __syncthreads();
-    if (stop) break;
-    step2_tile<T, C, U>(r.p, bx, by, tile, k);
-    __syncthreads();  // every write of the tile is done, and the window is free
-    if (t == 0 && ti != r.hold_tile) {
-      __threadfence();
-      st_release_u32(r.done + ti, (unsigned)k + 1u);
-    }
-  }
-}
-
 // Launch configuration of the two-step kernel for an nx x ny grid: one
 // block per tile.
 inline dim3 step2_grid(int nx, int ny) {
@@ -729,30 +637,5 @@ inline dim3 step2_block() { return dim3(32, kF2Warps, 1); }
 void launch_step2_f64(const StepParams &p, cudaStream_t s);
 void launch_step2_f32(const StepParams &p, bool u64, cudaStream_t s);
 void launch_step2_16(const StepParams &p, bool bf16, bool u64, cudaStream_t s);
-
-// The persistent form: a cooperative launch of `grid` blocks (at most the
-// resident blocks: the blocks-per-SM value below times the SM count).
-cudaError_t launch_step2_run_f64(const Step2Run &r, int grid, cudaStream_t s);
-cudaError_t launch_step2_run_f32(const Step2Run &r, bool u64, int grid, cudaStream_t s);
-cudaError_t launch_step2_run_16(const Step2Run &r, bool bf16, bool u64, int grid,
-                                cudaStream_t s);
-int step2_run_blocks_f64();
-int step2_run_blocks_f32(bool u64);
-int step2_run_blocks_16(bool bf16, bool u64);
-
-template <class T, class C, class U>
-cudaError_t launch_step2_run_t(const Step2Run &r, int grid, cudaStream_t s) {
-  void *args[] = {(void *)&r};
-  return cudaLaunchCooperativeKernel((const void *)step2_persistent_kernel<T, C, U>, dim3(grid),
-                                     step2_block(), args, 0, s);
-}
-template <class T, class C, class U>
-int step2_persistent_blocks_t() {
-  int n = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, step2_persistent_kernel<T, C, U>,
-                                                    32 * kF2Warps, 0) != cudaSuccess)
-    return 0;
-  return n;
-}
 
 }  // namespace lbm

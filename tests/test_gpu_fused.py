@@ -85,18 +85,17 @@ def _run(w, spl, u_fp64=False, k=0, nsteps=None, max_traced=None, seed=5):
     return sim, fs, u, sim.read_traces(), launches
 
 
-@pytest.mark.parametrize("spl", [2, 0])
 @pytest.mark.parametrize("storage,u64,k", STORAGES)
 @pytest.mark.parametrize("bcname", sorted(BCS))
 @pytest.mark.parametrize("nx,ny", [(3, 3), (13, 7), (33, 17), (70, 45), (300, 37)])
-def test_two_step_equals_one_step_bitwise(spl, storage, u64, k, bcname, nx, ny):
-    """Seven steps (three two-step launches, or one persistent launch of three
-    two-step phases, and one one-step launch) from a random state; the trace
-    buffer holds six steps, so the last pair records its first step only."""
+def test_two_step_equals_one_step_bitwise(storage, u64, k, bcname, nx, ny):
+    """Seven steps (three two-step launches and one one-step launch) from a
+    random state; the trace buffer holds six steps, so the last pair records
+    its first step only."""
     w = _case(nx, ny, bcname, storage)
     s1, fs1, u1, tr1, l1 = _run(w, 1, u64, k, max_traced=6)
-    s2, fs2, u2, tr2, l2 = _run(w, spl, u64, k, max_traced=6)
-    assert (l1, l2) == (7, 4 if spl == 2 else 2)
+    s2, fs2, u2, tr2, l2 = _run(w, 2, u64, k, max_traced=6)
+    assert (l1, l2) == (7, 4)
     assert s1.step_index == s2.step_index == 10
     assert np.array_equal(fs1, fs2)
     assert np.array_equal(u1, u2)
@@ -104,26 +103,24 @@ def test_two_step_equals_one_step_bitwise(spl, storage, u64, k, bcname, nx, ny):
     assert np.array_equal(tr1, tr2)
 
 
-@pytest.mark.parametrize("spl", [2, 0])
 @pytest.mark.parametrize("fs_order", [0, 1])
 @pytest.mark.parametrize("bcname", ["halfspace_sponges", "free_box", "free_tb_rigid_lr"])
-def test_two_step_free_surface_orders_bitwise(spl, fs_order, bcname):
+def test_two_step_free_surface_orders_bitwise(fs_order, bcname):
     """Both free-surface extrapolation orders, per-cell material."""
     w = _case(70, 45, bcname, "f64", fs_order=fs_order, per_cell=True)
     _, fs1, u1, tr1, _ = _run(w, 1)
-    _, fs2, u2, tr2, _ = _run(w, spl)
+    _, fs2, u2, tr2, _ = _run(w, 2)
     assert np.array_equal(fs1, fs2) and np.array_equal(u1, u2) and np.array_equal(tr1, tr2)
 
 
-@pytest.mark.parametrize("spl", [2, 0])
 @pytest.mark.parametrize("storage,tol", [("f64", 1e-12), ("f32", 1e-5)])
 @pytest.mark.parametrize("bcname", ["halfspace_sponges", "free_tb_rigid_lr", "periodic"])
-def test_two_step_matches_oracle(spl, storage, tol, bcname):
-    """Six steps (three two-step launches, or one persistent launch) from a
-    random state equal the oracle's element by element."""
+def test_two_step_matches_oracle(storage, tol, bcname):
+    """Six steps (three two-step launches) from a random state equal the
+    oracle's element by element."""
     w = _case(70, 45, bcname, storage, fs_order=1).with_(nsteps=6)
-    _, fs, u, tr, launches = _run(w, spl)
-    assert launches == (3 if spl == 2 else 1)
+    _, fs, u, tr, launches = _run(w, 2)
+    assert launches == 3
     prob = oracle_problem(w)
     fs0, u0 = _wl().random_state(w.nx, w.ny, seed=5)
     st, tro = oracle.run(prob, 6, oracle.State(prob, fs=fs0, u=u0, n=3))
@@ -132,20 +129,20 @@ def test_two_step_matches_oracle(spl, storage, tol, bcname):
     assert max_rel(tr, tro) <= tol
 
 
-@pytest.mark.parametrize("spl,nsteps", [(2, 2), (0, 4)])
+@pytest.mark.parametrize("nsteps", [2, 4])
 @pytest.mark.parametrize("storage", ["f64", "f32"])
-def test_two_step_full_size_halfspace(storage, spl, nsteps):
+def test_two_step_full_size_halfspace(storage, nsteps):
     """The bench's workload (2048 x 1024 half-space, free top, 64-cell layers)
-    from a random state, two steps in one launch or four steps in one
-    persistent launch: every cell equals the oracle's steps."""
+    from a random state, two or four steps in two-step launches: every cell
+    equals the oracle's steps."""
     w = _wl().halfspace(nsteps=nsteps, storage=storage)
     fs0, u0 = _wl().random_state(w.nx, w.ny, seed=21)
     sim = _pkg().from_workload(w)
-    sim.set_steps_per_launch(spl)  # (the FP64 default is one step per launch)
+    sim.set_steps_per_launch(2)  # (the FP64 default is one step per launch)
     sim.set_state(fs0, u0, step=40)
     n0 = sim.kernel_launches
     sim.step(nsteps)
-    assert sim.kernel_launches - n0 == 1
+    assert sim.kernel_launches - n0 == nsteps // 2
     fs, u = sim.get_state()
     prob = oracle_problem(w)
     st, _ = oracle.run(prob, nsteps, oracle.State(prob, fs=fs0, u=u0, n=40), traces=False)
@@ -161,7 +158,7 @@ def test_two_step_many_sources_bitwise():
     w = wl.periodic_layered_multisource(n=256, nsteps=20, seed=5, storage="f32")
     w = w.with_(lam=w.mu.copy())  # Lambda = 0 in every layer
     outs = []
-    for spl in (1, 2, 0):
+    for spl in (1, 2):
         sim = _pkg().from_workload(w, kernel="simple")
         sim.set_steps_per_launch(spl)
         sim.step(w.nsteps)
@@ -241,18 +238,8 @@ def test_two_step_gradient_force_layered_run_bitwise():
     assert rel_l2(ta, np.zeros_like(ta)) > 0
 
 
-def test_persistent_form_needs_lambda_zero():
-    """The persistent form applies to Lambda = 0 only; with the gradient
-    force steps_per_launch = 0 takes two-step launches (same results)."""
-    w = _case_lam(70, 45, "halfspace_sponges", "f32")
-    _, fs1, u1, _, l1 = _run(w, 1)
-    _, fs0, u0, _, l0 = _run(w, 0)
-    assert (l1, l0) == (7, 4)
-    assert np.array_equal(fs1, fs0) and np.array_equal(u1, u0)
-
-
 def test_steps_per_launch_argument_and_defaults():
-    """0, 1 and 2 are accepted; until set, FP32 handles take two steps per
+    """1 and 2 are accepted; until set, FP32 handles take two steps per
     launch, 16-bit handles two without and one with the gradient force, FP64
     handles one."""
     for storage, k, lam, per_launch in (("f32", 0, False, 2), ("f16", 10, False, 2),
@@ -263,49 +250,11 @@ def test_steps_per_launch_argument_and_defaults():
         n0 = sim.kernel_launches
         sim.step(4)
         assert sim.kernel_launches - n0 == 4 // per_launch, storage
-        for bad in (3, -1):
+        for bad in (3, 0, -1):
             with pytest.raises(_pkg().LBMError):
                 sim.set_steps_per_launch(bad)
-        for good in (0, 1, 2):
+        for good in (1, 2):
             sim.set_steps_per_launch(good)
-        with pytest.raises(_pkg().LBMError):
-            sim.set_persistent_wait(-1)
-        with pytest.raises(_pkg().LBMError):
-            sim.set_persistent_wait(0, hold_tile=10 ** 6)
-
-
-@pytest.mark.parametrize("nx,ny", [(61, 45), (70, 29)])
-def test_persistent_form_falls_back_on_one_cell_tiles(nx, ny):
-    """Grid sizes that leave a tile one cell wide (nx mod 30 = 1) or high
-    (ny mod 14 = 1) take two-step launches instead of the persistent form,
-    with the same results."""
-    w = _case(nx, ny, "periodic", "f32")
-    _, fs1, u1, tr1, l1 = _run(w, 1)
-    _, fs0, u0, tr0, l0 = _run(w, 0)
-    assert (l1, l0) == (7, 4)
-    assert np.array_equal(fs1, fs0) and np.array_equal(u1, u0) and np.array_equal(tr1, tr0)
-
-
-def test_persistent_wait_times_out_and_recovers():
-    """A tile that never publishes its progress makes its neighbours' bounded
-    waits run out: the launch stops, the next synchronising call reports the
-    time-out, and after a reset the handle steps normally again."""
-    w = _case(300, 37, "periodic", "f32")
-    sim = _pkg().from_workload(w, kernel="simple")
-    sim.set_steps_per_launch(0)
-    sim.set_persistent_wait(2_000_000, hold_tile=3)
-    sim.step(6)
-    with pytest.raises(_pkg().LBMError) as e:
-        sim.sync()
-    assert e.value.status == -6  # LBM_ERR_TIMEOUT
-    sim.reset()
-    sim.set_persistent_wait(0, -1)
-    fs0, u0 = _wl().random_state(w.nx, w.ny, seed=5)
-    sim.set_state(fs0, u0, step=3)
-    sim.step(7)
-    fs, u = sim.get_state()
-    _, fs1, u1, _, _ = _run(w, 1)
-    assert np.array_equal(fs, fs1) and np.array_equal(u, u1)
 
 
 def test_two_step_long_run_matches_one_step_f32():
@@ -315,7 +264,7 @@ def test_two_step_long_run_matches_one_step_f32():
     w = wl.layered_halfspace(256, 96, 400, seed=4, sponge=16, nrec=32, storage="f32")
     w = w.with_(lam=w.mu.copy())
     res = []
-    for spl in (1, 2, 0):
+    for spl in (1, 2):
         sim = _pkg().from_workload(w, kernel="simple")
         sim.set_steps_per_launch(spl)
         sim.step(w.nsteps)
