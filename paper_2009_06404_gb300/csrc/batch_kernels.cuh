@@ -135,7 +135,7 @@ __device__ __forceinline__ void batch_tile2(const StepParams &sp, int lam, int b
     step2_lam_tile<T, C, U>(sp, bx, by, win,
                             (C(*)[kL2RW])(smem + Batch2Smem<T, C>::kWin * sizeof(T)));
   else
-    step2_tile<T, C, U>(sp, bx, by, win, 0);
+    step2_tile<T, C, U>(sp, bx, by, win);
 }
 
 // Resident blocks per SM the register budget of a tile kind is set for.

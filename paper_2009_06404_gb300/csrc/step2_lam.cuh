@@ -374,7 +374,7 @@ __device__ __noinline__ void lam_general(const StepParams &p, const Phase2 &ph, 
 template <class T, class C, class U>
 __device__ __forceinline__ void step2_lam_tile(const StepParams &p, int bx, int by, T *tile,
                                                C (*rho_s)[kL2RW]) {
-  const Phase2 ph = phase2(p, 0);
+  const Phase2 ph = phase2(p);
   const int x0 = bx * kL2Cols, y0 = by * kL2Rows;
   if (lam_tile_special(p, x0, y0, ph.slot_a)) {
     lam_general<T, C, U>(p, ph, x0, y0, tile, rho_s);

@@ -204,27 +204,23 @@ constexpr int f2_buf() {
              : 9 * kF2H * kF2W;
 }
 
-// What changes from one two-step phase to the next: phase k after the one
-// the parameters describe (every launch passes k = 0) reads what phase
-// k - 1 wrote (the two buffers alternate), advances steps n + 2k and
-// n + 2k + 1, and records into trace slots trace_slot + 2k and
-// trace_slot + 2k + 1 while they exist.  The rest of the step's parameters
-// stay in the kernel's parameter space.
+// The two steps of a launch: steps n = p.n and n + 1 read p.fin and write
+// p.fout; they record into trace slots trace_slot and trace_slot + 1 while
+// those exist (below trace_end).
 struct Phase2 {
   const void *fin;
   void *fout;
   long long n;
   int slot_a, slot_b;
 };
-__device__ __forceinline__ Phase2 phase2(const StepParams &p, int k) {
+__device__ __forceinline__ Phase2 phase2(const StepParams &p) {
   Phase2 q;
-  const bool odd = k & 1;
-  q.fin = odd ? (const void *)p.fout : p.fin;
-  q.fout = odd ? (void *)p.fin : p.fout;
-  q.n = p.n + 2LL * k;
-  const int s = p.trace_slot + 2 * k;
-  q.slot_a = (p.trace_slot >= 0 && s < p.trace_end) ? s : -1;
-  q.slot_b = (p.trace_slot >= 0 && s + 1 < p.trace_end) ? s + 1 : -1;
+  q.fin = p.fin;
+  q.fout = p.fout;
+  q.n = p.n;
+  const int s = p.trace_slot;
+  q.slot_a = (s >= 0 && s < p.trace_end) ? s : -1;
+  q.slot_b = (s >= 0 && s + 1 < p.trace_end) ? s + 1 : -1;
   return q;
 }
 
@@ -321,7 +317,7 @@ __device__ __forceinline__ int tile_kind(const StepParams &p, int x0, int y0, in
 // after step n goes through global memory (u + v^n stored, reloaded for
 // + v^{n+1}: the same two roundings).
 template <class T, class C, class U>
-__device__ __noinline__ void step2_general(const StepParams &p, int x0, int y0, T *tile, int k) {
+__device__ __noinline__ void step2_general(const StepParams &p, int x0, int y0, T *tile) {
   // window cells lie within kF2Cols/2 + 1 columns and kF2Rows/2 + 1 rows of
   // the centre
   const unsigned smask = source_mask(p, x0 + kF2Cols / 2, y0 + kF2Rows / 2, kF2Cols / 2 + 2,
@@ -331,7 +327,7 @@ __device__ __noinline__ void step2_general(const StepParams &p, int x0, int y0, 
   constexpr int SW = f2_stage_w<T>();
   const int sox = stage_origin<T>(x0, 2);
   if constexpr (stages<T>()) {
-    stage_rows<T, SW, kF2SH, 32 * kF2Warps>(p, (const T *)phase2(p, k).fin, sox, y0 - 2, tile);
+    stage_rows<T, SW, kF2SH, 32 * kF2Warps>(p, (const T *)phase2(p).fin, sox, y0 - 2, tile);
     stage_wait();
   }
   __syncthreads();
@@ -353,7 +349,7 @@ __device__ __noinline__ void step2_general(const StepParams &p, int x0, int y0, 
       else valid = false;
     }
     if (valid) {
-      const Phase2 ph = phase2(p, k);
+      const Phase2 ph = phase2(p);
       C Fx, Fy;
       body_force_cell<C>(p, wx, wy, ph.n, Fx, Fy, smask);
       C f[9];
@@ -394,7 +390,7 @@ __device__ __noinline__ void step2_general(const StepParams &p, int x0, int y0, 
   const int x = x0 - 1 + ex, y = y0 - 1 + ey;
   if (!(core && x < p.nx && y < p.ny)) return;
   // step n + 1 of the tile's cell (x, y)
-  const Phase2 ph = phase2(p, k);
+  const Phase2 ph = phase2(p);
   C Fx, Fy;
   body_force_cell<C>(p, x, y, ph.n + 1, Fx, Fy, smask);
   C f[9];
@@ -436,8 +432,8 @@ __device__ __forceinline__ int wrap1(int v, int n) { return v < 0 ? v + n : (v >
 // carries none of its registers.  Every thread calls it (one barrier).
 template <class T, class C, class U, bool SRC>
 __device__ __noinline__ void step2_featured(const StepParams &p, int x0, int y0, int kind,
-                                            T *tile, int k) {
-  const Phase2 ph = phase2(p, k);
+                                            T *tile) {
+  const Phase2 ph = phase2(p);
   const int lane = threadIdx.x, w = threadIdx.y;
   int ex, ey;
   bool core;
@@ -527,24 +523,24 @@ __device__ __noinline__ void step2_featured(const StepParams &p, int x0, int y0,
     record_receiver<U>(p, ph.slot_b, x, y, ux, uy, vx, vy);
 }
 
-// Phase k (steps p.n + 2k and p.n + 2k + 1) of the tile (bx, by), by the
-// 32 x kF2Warps threads of the block (tile: the block's shared-memory
-// window).  Every thread calls it; it holds one block barrier.
+// Steps p.n and p.n + 1 of the tile (bx, by), by the 32 x kF2Warps threads
+// of the block (tile: the block's shared-memory window).  Every thread
+// calls it; it holds one block barrier (three on the general path).
 template <class T, class C, class U>
-__device__ __forceinline__ void step2_tile(const StepParams &p, int bx, int by, T *tile, int k) {
-  const Phase2 ph = phase2(p, k);
+__device__ __forceinline__ void step2_tile(const StepParams &p, int bx, int by, T *tile) {
+  const Phase2 ph = phase2(p);
   const int x0 = bx * kF2Cols, y0 = by * kF2Rows;
   const int kind = tile_kind(p, x0, y0, ph.slot_a);
   if (kind & kTileGeneral) {
-    step2_general<T, C, U>(p, x0, y0, tile, k);
+    step2_general<T, C, U>(p, x0, y0, tile);
     return;
   }
   if (kind & kTileSrc) {
-    step2_featured<T, C, U, true>(p, x0, y0, kind, tile, k);
+    step2_featured<T, C, U, true>(p, x0, y0, kind, tile);
     return;
   }
   if (kind) {
-    step2_featured<T, C, U, false>(p, x0, y0, kind, tile, k);
+    step2_featured<T, C, U, false>(p, x0, y0, kind, tile);
     return;
   }
   const int lane = threadIdx.x, w = threadIdx.y;
@@ -623,7 +619,7 @@ __global__ void __launch_bounds__(32 * kF2Warps, LBM_STEP2_MIN_BLOCKS)
 #endif
   __shared__ __align__(16) T tile[f2_buf<T>()];
   const int2 t = tile_of_block(p.tiles2, p.tiles2_first, gridDim.x, blockIdx.x, p.reverse);
-  step2_tile<T, C, U>(p, t.x, t.y, tile, 0);
+  step2_tile<T, C, U>(p, t.x, t.y, tile);
 }
 
 // Launch configuration of the two-step kernel for an nx x ny grid: one
