@@ -53,6 +53,19 @@ struct BatchArgs {
   long long barrier_cycles;
 };
 
+// Whether 32-bit word w of StepParams belongs to a field that changes from
+// phase to phase (buffers, step index, trace slot and its end), which
+// load_shot2 writes itself.
+__device__ __forceinline__ bool per_step_word(int w) {
+  constexpr int fin = (int)(offsetof(StepParams, fin) / 4);
+  constexpr int fout = (int)(offsetof(StepParams, fout) / 4);
+  constexpr int n = (int)(offsetof(StepParams, n) / 4);
+  constexpr int ts = (int)(offsetof(StepParams, trace_slot) / 4);
+  constexpr int te = (int)(offsetof(StepParams, trace_end) / 4);
+  return w == fin || w == fin + 1 || w == fout || w == fout + 1 || w == n || w == n + 1 ||
+         w == ts || w == te;
+}
+
 // Stages the parameters of shot s for step hdr->kbase + k of this call in
 // shared memory (every thread of the block calls it).
 template <int NT>
@@ -80,26 +93,33 @@ __device__ __forceinline__ void load_shot(const BatchArgs &a, int s, int k, Step
 
 // Stages the parameters of shot s for the two steps of phase hdr->kbase + k
 // of this call (steps n0 + 2 phase and n0 + 2 phase + 1; one buffer swap per
-// phase) in shared memory (every thread of the block calls it).
+// phase) in shared memory (every thread of the block calls it): the threads
+// copy the step-independent words while thread 0 forms the per-step fields,
+// so the staging costs one memory round trip and one barrier (for the
+// two-step tiles 5 % faster than copying first and patching after a
+// barrier; the short one-step tiles measured 1 % slower that way, and keep
+// the two barriers).
 template <int NT>
 __device__ __forceinline__ void load_shot2(const BatchArgs &a, int s, int k, StepParams &sp,
                                            int &lam) {
   const int t = threadIdx.y * 32 + threadIdx.x;
-  const int *src = (const int *)&a.shots[s].p;
+  const BatchShot &b = a.shots[s];
+  const int *src = (const int *)&b.p;
   int *dst = (int *)&sp;
-  for (int w = t; w < (int)(sizeof(StepParams) / 4); w += NT) dst[w] = src[w];
-  __syncthreads();
+  for (int w = t; w < (int)(sizeof(StepParams) / 4); w += NT)
+    if (!per_step_word(w)) dst[w] = src[w];
   if (t == 0) {
-    const BatchShot &b = a.shots[s];
+    // every load issued before any is used (one round trip)
     const BatchDyn d = a.dyn[s];
     const long long ph = a.hdr->kbase + k;
+    const void *f0 = b.f[0], *f1 = b.f[1];
     const int cur = (int)((d.cur0 + ph) & 1);
-    sp.fin = b.f[cur];
-    sp.fout = (void *)b.f[cur ^ 1];
+    sp.fin = cur ? f1 : f0;
+    sp.fout = (void *)(cur ? f0 : f1);
     sp.n = d.n0 + 2 * ph;
     const long long slot = d.traced0 + 2 * ph;
     // phase2() checks each of the two slots against trace_end
-    sp.trace_slot = (sp.nrec > 0 && slot < b.trace_max) ? (int)slot : -1;
+    sp.trace_slot = (b.p.nrec > 0 && slot < b.trace_max) ? (int)slot : -1;
     sp.trace_end = b.trace_max;
     lam = b.lam;
   }
