@@ -72,126 +72,6 @@ struct TilePops {
 };
 
 
-// The input populations around a general tile, staged in shared memory by
-// one pass of copies so that the general rules (wrapped pulls, wall rules,
-// ring densities) read them from there instead of making a round trip to
-// memory per branch.  Layout [SH][9][SW], the global row-interleaved order:
-// element (0, 0) of plane i is grid cell (ox, oy); cells beyond a periodic
-// seam hold the image's populations at their unwrapped coordinates, cells
-// beyond a non-periodic edge are not copied (the wall rules never read
-// them).
-template <class T, int SW, int SH>
-struct StagePops {
-  const T *f;
-  int ox, oy;
-  static constexpr bool kWrap = false;
-  __device__ __forceinline__ const T *at(int i, int x, int y) const {
-    return f + (((y - oy) * 9 + i) * SW + (x - ox));
-  }
-  template <class C>
-  __device__ __forceinline__ C load(int i, int x, int y) const {
-    return ld<T, C>(at(i, x, y));
-  }
-};
-
-// 16-byte chunks of the staged rows: elements per chunk, the columns a
-// region of width w with margin m needs (its origin rounded down to a
-// chunk), rounded up to whole chunks.
-template <class T>
-constexpr int stage_chunk() { return 16 / (int)sizeof(T); }
-template <class T>
-constexpr int stage_width(int w, int m) {
-  return (w + 2 * m + stage_chunk<T>() - 1 + stage_chunk<T>() - 1) / stage_chunk<T>() *
-         stage_chunk<T>();
-}
-// The origin column of a staged region: x0 - m rounded down to a chunk
-// (floor for negative values too).
-template <class T>
-__device__ __forceinline__ int stage_origin(int x0, int m) {
-  constexpr int E = stage_chunk<T>();
-  const int v = x0 - m;
-  return v >= 0 ? v / E * E : -((-v + E - 1) / E * E);
-}
-
-// Stages SH grid rows from oy (each with its nine planes) of SW columns from
-// ox (a multiple of the chunk) of fin into st (16-byte aligned), by every
-// thread of an NT-thread block: whole chunks inside the grid by 16-byte
-// asynchronous copies to shared memory through L2 (cp.async.cg, no
-// registers held), chunks across an edge element by element (wrapped on a
-// periodic axis, skipped beyond a non-periodic one).  The caller waits with
-// stage_wait() and a block barrier.  With a layout other than the row
-// interleaved one, every chunk goes element by element.
-template <class T, int SW, int SH, int NT>
-__device__ __forceinline__ void stage_rows(const StepParams &p, const T *fin, int ox, int oy,
-                                           T *st) {
-  constexpr int E = stage_chunk<T>(), NC = SW / E, N = SH * 9 * NC;
-  static_assert(SW % E == 0, "whole chunks per staged row");
-  const bool inter = p.frow == 9 * p.fplane;
-  for (int q = threadIdx.y * 32 + threadIdx.x; q < N; q += NT) {
-    const int R = q / NC, c = q - R * NC;
-    const int r = R / 9, i = R - 9 * r;
-    int gy = oy + r;
-    if (gy < 0 || gy >= p.ny) {
-      if (p.bc_top != BC_PERIODIC) continue;
-      gy = wrap_any(gy, p.ny);
-    }
-    const int gx = ox + c * E;
-    T *dst = st + (R * SW + c * E);
-    const T *src = fin + ((long long)gy * p.frow + (long long)i * p.fplane);
-    // a chunk wholly beyond a periodic seam is copied from its image (whole
-    // and aligned when nx is a multiple of the chunk)
-    int wx = gx;
-    if ((wx < 0 || wx >= p.nx) && p.bc_left == BC_PERIODIC) wx = wrap_any(wx, p.nx);
-    if (inter && wx >= 0 && wx + E <= p.nx && wx % E == 0) {
-      const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
-      asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(src + wx)
-                   : "memory");
-    } else {
-      // across an edge or seam: element by element, every load issued
-      // before the first shared store
-      T v[E];
-      unsigned okm = 0u;
-#pragma unroll
-      for (int e = 0; e < E; ++e) {
-        int x = gx + e;
-        if (x < 0 || x >= p.nx) {
-          if (p.bc_left != BC_PERIODIC) continue;
-          x = wrap_any(x, p.nx);
-        }
-        v[e] = __ldcg(src + x);
-        okm |= 1u << e;
-      }
-#pragma unroll
-      for (int e = 0; e < E; ++e)
-        if (okm & (1u << e)) dst[e] = v[e];
-    }
-  }
-  asm volatile("cp.async.commit_group;" ::: "memory");
-}
-__device__ __forceinline__ void stage_wait() {
-  asm volatile("cp.async.wait_group 0;" ::: "memory");
-}
-
-// All nine streamed populations of the in-grid cell (x, y) (unwrapped on
-// periodic axes) from a staged region: plain pulls off the walls, the wall
-// rules otherwise (the values of gather, bit for bit).
-template <class T, class C, class A>
-__device__ __forceinline__ void pull_staged(const StepParams &p, const A &a, int x, int y,
-                                            C *f) {
-  if (off_walls(p, x, y)) {
-#pragma unroll
-    for (int i = 0; i < 9; ++i) f[i] = a.template load<C>(i, x - cxd(i), y - cyd(i));
-  } else {
-    pull_cell<T, C>(p, a, x, y, f);
-  }
-}
-
-// Whether the general tiles of storage type T stage their inputs (the
-// staged region of 8-byte populations would pass the 48 KB of static shared
-// memory; FP64 keeps per-cell global pulls).
-template <class T>
-constexpr bool stages() { return sizeof(T) <= 4; }
-
 // Staged region of a Lambda = 0 general tile: the tile widened by two cells
 // (the window's pulls), aliasing the window buffer until step n's stores.
 template <class T>
