@@ -187,10 +187,10 @@ __device__ __forceinline__ int tile_kind(const StepParams &p, int x0, int y0, in
 // the general rules.  Step n is evaluated at each window cell (cells beyond
 // a non-periodic edge are never read: the wall rules replace them), its
 // pulls read from the input populations of the tile widened by two cells,
-// staged in the window buffer by one pass of loads; step n + 1 at the
-// tile's cells.  Out of line so the bulk path carries none of its
-// registers.  Every thread calls it (three barriers: staged, staged region
-// read, window written).
+// staged in the window buffer by one pass of copies (FP64: per-cell global
+// pulls); step n + 1 at the tile's cells.  Out of line so the bulk path
+// carries none of its registers.  Every thread calls it (three barriers:
+// inputs staged, staged region read, window written).
 //
 // Register budget: the body force of each step is summed (out of line, in
 // the sources' bounding box) before that step's pulls, and the displacement
