@@ -4,9 +4,12 @@ against one step per launch and against the FP64 oracle.
 The two-step kernel runs every cell update with the one-step arithmetic, so
 states, displacements and traces must agree bit for bit with one-step
 launches, for every storage type, boundary kind, grid shape (partial tiles,
-grids narrower than a tile), source placement (across seams and corners),
-trace-buffer end (the second step of a launch past the last slot) and odd
-step count (a one-step launch at the end)."""
+grids narrower than a tile, widths that are and are not a multiple of the
+16-byte chunks in which general tiles stage their inputs, so that chunks
+beyond a periodic seam are copied from their image or element by element),
+source placement (across seams and corners), trace-buffer end (the second
+step of a launch past the last slot) and odd step count (a one-step launch
+at the end)."""
 import numpy as np
 import pytest
 
@@ -87,7 +90,7 @@ def _run(w, spl, u_fp64=False, k=0, nsteps=None, max_traced=None, seed=5):
 
 @pytest.mark.parametrize("storage,u64,k", STORAGES)
 @pytest.mark.parametrize("bcname", sorted(BCS))
-@pytest.mark.parametrize("nx,ny", [(3, 3), (13, 7), (33, 17), (70, 45), (300, 37)])
+@pytest.mark.parametrize("nx,ny", [(3, 3), (13, 7), (33, 17), (70, 45), (96, 40), (300, 37)])
 def test_two_step_equals_one_step_bitwise(storage, u64, k, bcname, nx, ny):
     """Seven steps (three two-step launches and one one-step launch) from a
     random state; the trace buffer holds six steps, so the last pair records
@@ -181,7 +184,7 @@ def _case_lam(nx, ny, bcname, storage, fs_order=0, per_cell=False, seed=3):
 
 @pytest.mark.parametrize("storage,u64,k", STORAGES)
 @pytest.mark.parametrize("bcname", sorted(BCS))
-@pytest.mark.parametrize("nx,ny", [(3, 3), (13, 7), (40, 21), (70, 45), (300, 37)])
+@pytest.mark.parametrize("nx,ny", [(3, 3), (13, 7), (40, 21), (70, 45), (96, 40), (300, 37)])
 def test_two_step_gradient_force_equals_one_step_bitwise(storage, u64, k, bcname, nx, ny):
     """With the density-gradient force (step n on the tile widened by two
     cells, densities on the tile widened by three): seven steps, three
