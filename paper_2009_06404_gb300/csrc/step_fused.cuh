@@ -122,26 +122,39 @@ __device__ __forceinline__ void window_cell(int lane, int w, int &ex, int &ey, b
   }
 }
 
-// Kinds of tile, from its position only (every lane of every warp gets the
-// same answer).  kTileGeneral: the general rules -- a non-periodic edge
-// within two cells (step n reaches one cell beyond the tile and pulls from
-// one more), a partial tile, or a periodic axis shorter than two tiles.
-// Otherwise any of: kTileWrap, the window or its pulls cross a periodic
-// seam; kTileSrc, a source reaches the window; kTileRec, a receiver is
-// among the tile's cells (when recording).  0: the plain bulk update.
+// Origin along one axis of the cells a tile computes.  A partial tile (the
+// last along an axis of n cells that is not a multiple of the tile size T)
+// on a periodic axis at least two tiles long computes the full tile that
+// ends at the seam, n - T, and stores only its own cells (from t0 on): the
+// cells below t0 are the previous tile's, computed again the same way.
+__device__ __forceinline__ int tile_origin(int t0, int T, int n, bool periodic) {
+  return periodic && t0 + T > n && n >= 2 * T ? n - T : t0;
+}
+
+// Kinds of tile (origin x0, y0), from its position only (every lane of
+// every warp gets the same answer).  kTileGeneral: the general rules -- a
+// non-periodic edge within two cells (step n reaches one cell beyond the
+// tile and pulls from one more), a partial tile on a non-periodic axis, or
+// a periodic axis shorter than two tiles.  Otherwise any of: kTileWrap, the
+// window or its pulls cross a periodic seam (every partial tile on a
+// periodic axis, whose cells are computed from tile_origin); kTileSrc, a
+// source reaches the window; kTileRec, a receiver is among the cells
+// computed (when recording).  0: the plain bulk update.
 enum { kTileGeneral = 1, kTileWrap = 2, kTileSrc = 4, kTileRec = 8 };
 
 __device__ __forceinline__ int tile_kind(const StepParams &p, int x0, int y0, int slot_a) {
   constexpr int W = kF2Cols, H = kF2Rows;
   int kind = 0;
   if (p.bc_left == BC_PERIODIC) {
-    if (x0 + W > p.nx || p.nx < 2 * W) return kTileGeneral;
+    if (p.nx < 2 * W) return kTileGeneral;
+    if (x0 + W > p.nx) x0 = p.nx - W;
     if (x0 < 2 || x0 + W > p.nx - 2) kind |= kTileWrap;
   } else if (x0 < 2 || x0 + W > p.nx - 2) {
     return kTileGeneral;
   }
   if (p.bc_top == BC_PERIODIC) {
-    if (y0 + H > p.ny || p.ny < 2 * H) return kTileGeneral;
+    if (p.ny < 2 * H) return kTileGeneral;
+    if (y0 + H > p.ny) y0 = p.ny - H;
     if (y0 < 2 || y0 + H > p.ny - 2) kind |= kTileWrap;
   } else if (y0 < 2 || y0 + H > p.ny - 2) {
     return kTileGeneral;
@@ -310,15 +323,18 @@ __device__ __forceinline__ int wrap1(int v, int n) { return v < 0 ? v + n : (v >
 // with the window's cells and pulls wrapped, the body force where a source
 // reaches, and the receivers recorded.  Out of line, so the plain bulk path
 // carries none of its registers.  Every thread calls it (one barrier).
+// (x0, y0): the cells computed; only those from (xs, ys) on are stored (a
+// partial tile on a periodic axis, tile_origin).
 template <class T, class C, class U, bool SRC>
-__device__ __noinline__ void step2_featured(const StepParams &p, int x0, int y0, int kind,
-                                            T *tile) {
+__device__ __noinline__ void step2_featured(const StepParams &p, int x0, int y0, int xs, int ys,
+                                            int kind, T *tile) {
   const Phase2 ph = phase2(p);
   const int lane = threadIdx.x, w = threadIdx.y;
   int ex, ey;
   bool core;
   window_cell(lane, w, ex, ey, core);
   const int x = x0 - 1 + ex, y = y0 - 1 + ey;  // tile cells: inside the grid
+  core = core && x >= xs && y >= ys;           // the cells this tile stores
   const int wx = wrap1(x, p.nx), wy = wrap1(y, p.ny);
   constexpr bool src = SRC;  // kind & kTileSrc
   const bool spg = (kind & kTileWrap) || x0 - 1 < p.sp_left || x0 + kF2Cols + 1 > p.nx - p.sp_right ||
@@ -415,12 +431,11 @@ __device__ __forceinline__ void step2_tile(const StepParams &p, int bx, int by, 
     step2_general<T, C, U>(p, x0, y0, tile);
     return;
   }
-  if (kind & kTileSrc) {
-    step2_featured<T, C, U, true>(p, x0, y0, kind, tile);
-    return;
-  }
   if (kind) {
-    step2_featured<T, C, U, false>(p, x0, y0, kind, tile);
+    const int cx = tile_origin(x0, kF2Cols, p.nx, p.bc_left == BC_PERIODIC);
+    const int cy = tile_origin(y0, kF2Rows, p.ny, p.bc_top == BC_PERIODIC);
+    if (kind & kTileSrc) step2_featured<T, C, U, true>(p, cx, cy, x0, y0, kind, tile);
+    else step2_featured<T, C, U, false>(p, cx, cy, x0, y0, kind, tile);
     return;
   }
   const int lane = threadIdx.x, w = threadIdx.y;
