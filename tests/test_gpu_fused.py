@@ -172,6 +172,35 @@ def test_two_step_many_sources_bitwise():
     assert np.abs(outs[0][1]).max() > 0
 
 
+@pytest.mark.parametrize("storage,u64,k", [("f32", False, 0), ("f16", False, 10)])
+@pytest.mark.parametrize("bcname", ["periodic", "halfspace_sponges", "periodic_y_rigid_x"])
+@pytest.mark.parametrize("nx,ny", [(61, 29), (89, 41)])
+def test_two_step_periodic_partial_tile_overlap_bitwise(storage, u64, k, bcname, nx, ny):
+    """A partial tile on a periodic axis computes the full tile that ends at
+    the seam and stores only its own cells: receivers and a source inside
+    the cells it computes again (its neighbour's), and a partial tile one
+    cell wide or tall (61 = 2 x 30 + 1, 29 = 2 x 14 + 1), leave every cell,
+    displacement and trace bit for bit as one step per launch."""
+    wl = _wl()
+    w = _case(nx, ny, bcname, storage)
+    # a cell of the last tile's overlap region: x in [nx - 30, 30 (nx // 30)),
+    # y in [ny - 14, 14 (ny // 14))
+    xo = (nx - 30 + 30 * (nx // 30)) // 2
+    yo = (ny - 14 + 14 * (ny // 14)) // 2
+    src = np.concatenate([w.sources, wl.source(xo + 0.3, yo + 0.6, sigma=1.2, direction=(0.0, 1.0),
+                                               f_peak=0.25, t0=1.5, r_cut=4.0)[None]])
+    rec = np.array([[xo, yo], [xo - 5, 3], [4, yo + 2], [nx - 1, ny - 1], [nx - 2, 0]], np.int32)
+    w = w.with_(sources=src, receivers=rec)
+    s1, fs1, u1, tr1, l1 = _run(w, 1, u64, k, max_traced=6)
+    s2, fs2, u2, tr2, l2 = _run(w, 2, u64, k, max_traced=6)
+    assert (l1, l2) == (7, 4)
+    assert np.array_equal(fs1, fs2)
+    assert np.array_equal(u1, u2)
+    assert tr1.shape == tr2.shape == (6, 5, 4)
+    assert np.array_equal(tr1, tr2)
+    assert np.abs(tr1[:, 0]).max() > 0
+
+
 def _case_lam(nx, ny, bcname, storage, fs_order=0, per_cell=False, seed=3):
     """As _case, with a Poisson ratio per row (per cell with per_cell) in
     [0.15, 0.33]: Lambda != 0, the density-gradient force is on."""
