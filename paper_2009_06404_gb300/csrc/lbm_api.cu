@@ -314,8 +314,11 @@ double store_scale(const lbm_elastic_config &c) {
 // edge or seam within which a tile takes a slower path) in launch order:
 // the tiles near an edge or seam, that a source footprint reaches, or that
 // hold a receiver first, then the others, each group in row-major order.
-// Appends to out; returns the size of the first group.  Only the order of
-// the work depends on it, never a result.
+// Appends to out; returns the size of the first group.  The first group
+// holds every tile a source footprint (widened by m + 1) or a receiver can
+// reach: the single-grid kernels skip the source and receiver lookups of
+// the other tiles (their edge and seam tests stay in the kernel), so the
+// list is rebuilt whenever sources or receivers change.
 int order_tiles(const lbm_elastic_t *h, int W, int H, int m, std::vector<int2> &out) {
   const int nx = h->cfg.nx, ny = h->cfg.ny;
   const bool perx = h->cfg.bc_left == LBM_BC_PERIODIC, pery = h->cfg.bc_top == LBM_BC_PERIODIC;
@@ -326,23 +329,43 @@ int order_tiles(const lbm_elastic_t *h, int W, int H, int m, std::vector<int2> &
       const int x0 = bx * W, y0 = by * H;
       if (x0 < m || x0 + W > nx - m || y0 < m || y0 + H > ny - m) slow[(size_t)by * gx + bx] = 1;
     }
-  // tile indices along one axis whose cells, widened by m + 1, overlap
-  // [lo, hi] (wrapped on a periodic axis, each at most once)
-  auto span = [](long long lo, long long hi, int T, int g, bool per, std::vector<int> &v) {
+  // tile indices along one axis (n cells, tiles of T) holding a cell of
+  // [lo, hi], each at most once: cells wrapped on a periodic axis (the last
+  // tile may be partial, so a range across the seam continues at cell 0,
+  // not at a whole tile), dropped beyond a non-periodic edge.  The kernels
+  // take every tile after this list's first part to be out of every
+  // source's and receiver's reach.
+  auto span = [](long long lo, long long hi, int T, int n, bool per, std::vector<int> &v) {
     v.clear();
-    const long long a = lo >= 0 ? lo / T : -((-lo + T - 1) / T);
-    const long long b = hi >= 0 ? hi / T : -((-hi + T - 1) / T);
-    for (long long t = a; t <= b && (long long)v.size() < g; ++t) {
-      long long k = t;
-      if (per) k = ((k % g) + g) % g;
-      else if (k < 0 || k >= g) continue;
-      v.push_back((int)k);
+    auto add = [&](long long a, long long b) {  // cells a..b, 0 <= a <= b < n
+      for (long long k = a / T; k <= b / T; ++k) {
+        bool seen = false;
+        for (int e : v) seen |= e == (int)k;
+        if (!seen) v.push_back((int)k);
+      }
+    };
+    if (per) {
+      if (hi - lo + 1 >= n) {
+        add(0, n - 1);
+      } else {
+        const long long a = ((lo % n) + n) % n, b = a + (hi - lo);
+        if (b < n) {
+          add(a, b);
+        } else {
+          add(a, n - 1);
+          add(0, b - n);
+        }
+      }
+    } else {
+      lo = std::max(lo, 0LL);
+      hi = std::min(hi, (long long)n - 1);
+      if (lo <= hi) add(lo, hi);
     }
   };
   std::vector<int> xs, ys;
   for (const SourceDev &q : h->src_host) {
-    span((long long)q.xc - q.rb - m - 1, (long long)q.xc + q.rb + m + 1, W, gx, perx, xs);
-    span((long long)q.yc - q.rb - m - 1, (long long)q.yc + q.rb + m + 1, H, gy, pery, ys);
+    span((long long)q.xc - q.rb - m - 1, (long long)q.xc + q.rb + m + 1, W, nx, perx, xs);
+    span((long long)q.yc - q.rb - m - 1, (long long)q.yc + q.rb + m + 1, H, ny, pery, ys);
     for (int ty : ys)
       for (int tx : xs) slow[(size_t)ty * gx + tx] = 1;
   }

@@ -59,11 +59,14 @@ __device__ __forceinline__ void lam_ring_cell(int t, int &hx, int &hy) {
 
 // Whether a tile at (x0, y0) takes the general rules: an edge or seam of the
 // grid within four cells (W3's pulls), a source reaching W2, or a receiver
-// among the tile's cells when recording.  Warp-wide.
+// among the tile's cells when recording.  Warp-wide.  lookup = false skips
+// the source and receiver tests (a tile the host's launch order places
+// after every tile a source or receiver can reach).
 __device__ __forceinline__ bool lam_tile_special(const StepParams &p, int x0, int y0,
-                                                 int slot_a) {
+                                                 int slot_a, bool lookup = true) {
   constexpr int W = kL2Cols, H = kL2Rows;
   if (x0 < 4 || x0 + W > p.nx - 4 || y0 < 4 || y0 + H > p.ny - 4) return true;
+  if (!lookup) return false;
   const bool near_src = p.nsrc > 0 && x0 - 2 <= p.src_x1 && x0 + W + 1 >= p.src_x0 &&
                         y0 - 2 <= p.src_y1 && y0 + H + 1 >= p.src_y0;
   const bool near_rec = slot_a >= 0 && x0 <= p.rec_x1 && x0 + W - 1 >= p.rec_x0 &&
@@ -371,12 +374,13 @@ __device__ __noinline__ void lam_general(const StepParams &p, const Phase2 &ph, 
 // Steps n = p.n and n + 1 of the tile (bx, by) with the density-gradient
 // force, by the 32 x kL2H threads of a block (tile, rho_s: its shared
 // memory).  Every thread calls it; it holds three block barriers.
+// lookup: as for lam_tile_special.
 template <class T, class C, class U>
 __device__ __forceinline__ void step2_lam_tile(const StepParams &p, int bx, int by, T *tile,
-                                               C (*rho_s)[kL2RW]) {
+                                               C (*rho_s)[kL2RW], bool lookup = true) {
   const Phase2 ph = phase2(p);
   const int x0 = bx * kL2Cols, y0 = by * kL2Rows;
-  if (lam_tile_special(p, x0, y0, ph.slot_a)) {
+  if (lam_tile_special(p, x0, y0, ph.slot_a, lookup)) {
     lam_general<T, C, U>(p, ph, x0, y0, tile, rho_s);
     return;
   }
@@ -396,7 +400,9 @@ __global__ void __launch_bounds__(32 * kL2H, LBM_STEP2L_MIN_BLOCKS)
   __shared__ __align__(16) T tile[l2_buf<T>()];
   __shared__ C rho_s[kL2RH][kL2RW];
   const int2 t = tile_of_block(p.tiles2l, p.tiles2l_first, gridDim.x, blockIdx.x, p.reverse);
-  step2_lam_tile<T, C, U>(p, t.x, t.y, tile, rho_s);
+  // the tiles after the list's first part are out of every source's and
+  // receiver's reach (the edge and seam tests stay)
+  step2_lam_tile<T, C, U>(p, t.x, t.y, tile, rho_s, (int)blockIdx.x < p.tiles2l_first);
 }
 
 inline dim3 step2_lam_grid(int nx, int ny) {

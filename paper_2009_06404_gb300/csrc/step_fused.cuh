@@ -139,10 +139,13 @@ __device__ __forceinline__ int tile_origin(int t0, int T, int n, bool periodic) 
 // window or its pulls cross a periodic seam (every partial tile on a
 // periodic axis, whose cells are computed from tile_origin); kTileSrc, a
 // source reaches the window; kTileRec, a receiver is among the cells
-// computed (when recording).  0: the plain bulk update.
+// computed (when recording).  0: the plain bulk update.  lookup = false
+// skips the source and receiver tests (a tile the host's launch order
+// places after every tile a source or receiver can reach).
 enum { kTileGeneral = 1, kTileWrap = 2, kTileSrc = 4, kTileRec = 8 };
 
-__device__ __forceinline__ int tile_kind(const StepParams &p, int x0, int y0, int slot_a) {
+__device__ __forceinline__ int tile_kind(const StepParams &p, int x0, int y0, int slot_a,
+                                         bool lookup = true) {
   constexpr int W = kF2Cols, H = kF2Rows;
   int kind = 0;
   if (p.bc_left == BC_PERIODIC) {
@@ -159,6 +162,7 @@ __device__ __forceinline__ int tile_kind(const StepParams &p, int x0, int y0, in
   } else if (y0 < 2 || y0 + H > p.ny - 2) {
     return kTileGeneral;
   }
+  if (!lookup) return kind;
   const bool near_src = p.nsrc > 0 && x0 - 1 <= p.src_x1 && x0 + W >= p.src_x0 &&
                         y0 - 1 <= p.src_y1 && y0 + H >= p.src_y0;
   const bool near_rec = slot_a >= 0 && x0 <= p.rec_x1 && x0 + W - 1 >= p.rec_x0 &&
@@ -422,11 +426,13 @@ __device__ __noinline__ void step2_featured(const StepParams &p, int x0, int y0,
 // Steps p.n and p.n + 1 of the tile (bx, by), by the 32 x kF2Warps threads
 // of the block (tile: the block's shared-memory window).  Every thread
 // calls it; it holds one block barrier (three on the general path).
+// lookup: as for tile_kind.
 template <class T, class C, class U>
-__device__ __forceinline__ void step2_tile(const StepParams &p, int bx, int by, T *tile) {
+__device__ __forceinline__ void step2_tile(const StepParams &p, int bx, int by, T *tile,
+                                           bool lookup = true) {
   const Phase2 ph = phase2(p);
   const int x0 = bx * kF2Cols, y0 = by * kF2Rows;
-  const int kind = tile_kind(p, x0, y0, ph.slot_a);
+  const int kind = tile_kind(p, x0, y0, ph.slot_a, lookup);
   if (kind & kTileGeneral) {
     step2_general<T, C, U>(p, x0, y0, tile);
     return;
@@ -514,7 +520,9 @@ __global__ void __launch_bounds__(32 * kF2Warps, LBM_STEP2_MIN_BLOCKS)
 #endif
   __shared__ __align__(16) T tile[f2_buf<T>()];
   const int2 t = tile_of_block(p.tiles2, p.tiles2_first, gridDim.x, blockIdx.x, p.reverse);
-  step2_tile<T, C, U>(p, t.x, t.y, tile);
+  // the tiles after the list's first part are out of every source's and
+  // receiver's reach (the edge and seam tests stay)
+  step2_tile<T, C, U>(p, t.x, t.y, tile, (int)blockIdx.x < p.tiles2_first);
 }
 
 // Launch configuration of the two-step kernel for an nx x ny grid: one
