@@ -107,6 +107,8 @@ Layout make_layout(const lbm_elastic_config *c) {
   L.ntiles2l = (long long)((c->nx + kL2Cols - 1) / kL2Cols) * ((c->ny + kL2Rows - 1) / kL2Rows);
   L.order2 = take((size_t)L.ntiles2 * sizeof(int2));
   L.order2l = take((size_t)L.ntiles2l * sizeof(int2));
+  L.nblk1 = (long long)((c->nx + 31) / 32) * ((c->ny + 7) / 8);
+  L.blk1 = take((size_t)L.nblk1 + 16);
   size_t stage = (size_t)L.stage_rows * c->nx * 11 * sizeof(double);
   size_t mat_stage = (size_t)3 * c->ny * sizeof(double);
   L.stage = take(stage > mat_stage ? stage : mat_stage);
@@ -310,6 +312,38 @@ double store_scale(const lbm_elastic_config &c) {
                                                          : 1.0;
 }
 
+// The indices of the tiles (or blocks) of size T along one axis of n cells
+// that hold a cell of [lo, hi], each once: cells wrapped on a periodic axis
+// (the last tile may be partial, so a range across the seam continues at
+// cell 0, not at a whole tile), dropped beyond a non-periodic edge.
+static void tile_span(long long lo, long long hi, int T, int n, bool per, std::vector<int> &v) {
+  v.clear();
+  auto add = [&](long long a, long long b) {  // cells a..b, 0 <= a <= b < n
+    for (long long k = a / T; k <= b / T; ++k) {
+      bool seen = false;
+      for (int e : v) seen |= e == (int)k;
+      if (!seen) v.push_back((int)k);
+    }
+  };
+  if (per) {
+    if (hi - lo + 1 >= n) {
+      add(0, n - 1);
+    } else {
+      const long long a = ((lo % n) + n) % n, b = a + (hi - lo);
+      if (b < n) {
+        add(a, b);
+      } else {
+        add(a, n - 1);
+        add(0, b - n);
+      }
+    }
+  } else {
+    lo = std::max(lo, 0LL);
+    hi = std::min(hi, (long long)n - 1);
+    if (lo <= hi) add(lo, hi);
+  }
+}
+
 // The two-step tiles of one geometry (W x H cells; m: the distance to an
 // edge or seam within which a tile takes a slower path) in launch order:
 // the tiles near an edge or seam, that a source footprint reaches, or that
@@ -329,43 +363,10 @@ int order_tiles(const lbm_elastic_t *h, int W, int H, int m, std::vector<int2> &
       const int x0 = bx * W, y0 = by * H;
       if (x0 < m || x0 + W > nx - m || y0 < m || y0 + H > ny - m) slow[(size_t)by * gx + bx] = 1;
     }
-  // tile indices along one axis (n cells, tiles of T) holding a cell of
-  // [lo, hi], each at most once: cells wrapped on a periodic axis (the last
-  // tile may be partial, so a range across the seam continues at cell 0,
-  // not at a whole tile), dropped beyond a non-periodic edge.  The kernels
-  // take every tile after this list's first part to be out of every
-  // source's and receiver's reach.
-  auto span = [](long long lo, long long hi, int T, int n, bool per, std::vector<int> &v) {
-    v.clear();
-    auto add = [&](long long a, long long b) {  // cells a..b, 0 <= a <= b < n
-      for (long long k = a / T; k <= b / T; ++k) {
-        bool seen = false;
-        for (int e : v) seen |= e == (int)k;
-        if (!seen) v.push_back((int)k);
-      }
-    };
-    if (per) {
-      if (hi - lo + 1 >= n) {
-        add(0, n - 1);
-      } else {
-        const long long a = ((lo % n) + n) % n, b = a + (hi - lo);
-        if (b < n) {
-          add(a, b);
-        } else {
-          add(a, n - 1);
-          add(0, b - n);
-        }
-      }
-    } else {
-      lo = std::max(lo, 0LL);
-      hi = std::min(hi, (long long)n - 1);
-      if (lo <= hi) add(lo, hi);
-    }
-  };
   std::vector<int> xs, ys;
   for (const SourceDev &q : h->src_host) {
-    span((long long)q.xc - q.rb - m - 1, (long long)q.xc + q.rb + m + 1, W, nx, perx, xs);
-    span((long long)q.yc - q.rb - m - 1, (long long)q.yc + q.rb + m + 1, H, ny, pery, ys);
+    tile_span((long long)q.xc - q.rb - m - 1, (long long)q.xc + q.rb + m + 1, W, nx, perx, xs);
+    tile_span((long long)q.yc - q.rb - m - 1, (long long)q.yc + q.rb + m + 1, H, ny, pery, ys);
     for (int ty : ys)
       for (int tx : xs) slow[(size_t)ty * gx + tx] = 1;
   }
@@ -397,6 +398,23 @@ lbm_status upload_tile_order(lbm_elastic_t *h) {
   LBM_CUDA(h, cudaMemcpyAsync(h->ws + L.order2l, o.data() + L.ntiles2,
                               (size_t)L.ntiles2l * sizeof(int2), cudaMemcpyHostToDevice,
                               h->stream));
+  // one-step blocks (32 x 8) that a source footprint widened by three cells
+  // (the kernel's test reaches two) or a receiver can reach
+  const int nx = h->cfg.nx, ny = h->cfg.ny, gx = (nx + 31) / 32;
+  const bool perx = h->cfg.bc_left == LBM_BC_PERIODIC, pery = h->cfg.bc_top == LBM_BC_PERIODIC;
+  std::vector<unsigned char> near((size_t)L.nblk1, 0);
+  std::vector<int> xs, ys;
+  for (const SourceDev &q : h->src_host) {
+    tile_span((long long)q.xc - q.rb - 3, (long long)q.xc + q.rb + 3, 32, nx, perx, xs);
+    tile_span((long long)q.yc - q.rb - 3, (long long)q.yc + q.rb + 3, 8, ny, pery, ys);
+    for (int ty : ys)
+      for (int tx : xs) near[(size_t)ty * gx + tx] = 1;
+  }
+  for (size_t r = 0; 2 * r + 1 < h->rec_host.size(); ++r)
+    near[(size_t)(h->rec_host[2 * r + 1] / 8) * gx + h->rec_host[2 * r] / 32] = 1;
+  LBM_CUDA(h, cudaMemcpyAsync(h->ws + L.blk1, near.data(), near.size(), cudaMemcpyHostToDevice,
+                              h->stream));
+  // (pageable source: the copy has left the host buffer when the call returns)
   return LBM_OK;
 }
 
@@ -453,6 +471,7 @@ StepParams base_params(lbm_elastic_t *h) {
   p.tiles2l = at<int2>(h, L.order2l);
   p.tiles2_first = h->order2_first;
   p.tiles2l_first = h->order2l_first;
+  p.blk_near = at<unsigned char>(h, L.blk1);
   p.rec_tile_ptr = at<int>(h, L.rec_ptr);
   p.rec_xy = at<int>(h, L.rec_xy);
   p.rec_id = at<int>(h, L.rec_id);

@@ -239,6 +239,7 @@ lbm_status prepare_call(lbm_batch_t *b) {
     BatchShot &bs = b->shot_host[s];
     memset(&bs, 0, sizeof(bs));
     bs.p = handle_step_params(h);
+    bs.p.blk_near = nullptr;  // laid out for the shot's own one-step launches
     bs.f[0] = h->ws + h->L.f[0];
     bs.f[1] = h->ws + h->L.f[1];
     bs.lam = h->lambda_nonzero ? 1 : 0;

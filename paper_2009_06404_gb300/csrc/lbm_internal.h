@@ -22,6 +22,8 @@ struct Layout {
   int rec_tiles_x = 0, rec_tiles = 0, stage_rows = 0;
   size_t order2 = 0, order2l = 0; // two-step tiles in launch order (int2), both geometries
   long long ntiles2 = 0, ntiles2l = 0;
+  size_t blk1 = 0;                // one-step blocks (32 x 8) a source or receiver reaches (bytes)
+  long long nblk1 = 0;
   long long mat_count = 0;
 };
 

@@ -101,6 +101,10 @@ struct StepParams {
   // density-gradient force)
   const int2 *tiles2, *tiles2l;
   int tiles2_first, tiles2l_first;
+  // one-step launches of the single grid: per 32 x 8 block (row-major), 0
+  // when no source footprint and no receiver can reach the block, so that
+  // its source and receiver lookups are skipped; null: every block looks
+  const unsigned char *blk_near;
   // fields mode only
   int row0, nrows;
   double *out[8];           // ux uy vx vy rho pxx pxy pyy, [nrows][nx] each
@@ -983,10 +987,12 @@ __device__ __noinline__ void boundary_cell(const StepParams &p, C Fx, C Fy, int 
 // beyond the bulk update: a wall or periodic seam within m cells, a source
 // reaching the block widened by `halo` cells on every side, or (when
 // recording) a receiver in the block.  Warp-wide (all 32 lanes call it);
-// every lane gets the same answer.
+// every lane gets the same answer.  near (optional): the host's flag of the
+// block (StepParams::blk_near); 0 skips the source and receiver lookups.
 template <int W = 32>
 __device__ __forceinline__ bool block_is_special(const StepParams &p, int x0, int y0, int h,
-                                                 int m, int halo = 0) {
+                                                 int m, int halo = 0,
+                                                 const unsigned char *near = nullptr) {
   static_assert(W == 32 || W == kRecTileX, "a block spans one receiver tile column");
   if (x0 < m || x0 + W > p.nx - m || y0 < m || y0 + h > p.ny - m) return true;
   const bool near_src = p.nsrc > 0 && x0 - halo <= p.src_x1 && x0 + W - 1 + halo >= p.src_x0 &&
@@ -994,6 +1000,7 @@ __device__ __forceinline__ bool block_is_special(const StepParams &p, int x0, in
   const bool near_rec = p.trace_slot >= 0 && x0 <= p.rec_x1 && x0 + W - 1 >= p.rec_x0 &&
                         y0 <= p.rec_y1 && y0 + h - 1 >= p.rec_y0;
   if (!near_src && !near_rec) return false;
+  if (near != nullptr && *near == 0) return false;
   if (p.nsrc > 32) return true;
   const int lane = threadIdx.x & 31;
   bool hit = false;
@@ -1224,7 +1231,14 @@ __device__ __forceinline__ void step_block(const StepParams &p, int bx, int by) 
   const int y = y0 + threadIdx.y;
   const int yend = MODE == 1 ? p.row0 + p.nrows : p.ny;
   const int m = LAM ? 2 : 1;
-  if (MODE == 1 || block_is_special(p, x0, y0, R, m)) {
+  // the host's per-block flags are laid out for the single grid's 32 x 8
+  // blocks of one-step launches; taken with the gradient force only (with
+  // Lambda = 0 the flag's load made the 8192^2 step 8 % slower, with it the
+  // 16-bit step 4 % faster)
+  const unsigned char *near = (LAM && MODE == 0 && R == 8 && p.blk_near != nullptr)
+                                  ? p.blk_near + (by * ((p.nx + 31) >> 5) + bx)
+                                  : nullptr;
+  if (MODE == 1 || block_is_special(p, x0, y0, R, m, 0, near)) {
     // the same for every thread of the block (block_is_special depends on
     // the block's position only)
     if (LAM) general_block_lam<T, C, U, MODE, R>(p, x0, y0, yend);
