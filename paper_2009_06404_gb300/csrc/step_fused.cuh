@@ -514,12 +514,14 @@ __device__ __forceinline__ int2 tile_of_block(const int2 *list, int first, int n
 template <class T, class C, class U>
 __global__ void __launch_bounds__(32 * kF2Warps, LBM_STEP2_MIN_BLOCKS)
     step2_kernel(const StepParams p) {
+  // the tile list is written only by host copies ordered before the
+  // previous launch, so its entry is read before the wait for that launch
+  const int2 t = tile_of_block(p.tiles2, p.tiles2_first, gridDim.x, blockIdx.x, p.reverse);
 #if LBM_PDL
   asm volatile("griddepcontrol.wait;" ::: "memory");
   asm volatile("griddepcontrol.launch_dependents;");
 #endif
   __shared__ __align__(16) T tile[f2_buf<T>()];
-  const int2 t = tile_of_block(p.tiles2, p.tiles2_first, gridDim.x, blockIdx.x, p.reverse);
   // the tiles after the list's first part are out of every source's and
   // receiver's reach (the edge and seam tests stay)
   step2_tile<T, C, U>(p, t.x, t.y, tile, (int)blockIdx.x < p.tiles2_first);
